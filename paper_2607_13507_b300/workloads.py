@@ -1,0 +1,248 @@
+"""Seeded synthetic inputs for the PIC hot path.
+
+This module only draws initial conditions (particle cells, in-cell offsets,
+momenta, weights, ids) and describes the workloads.  It holds none of the
+method's arithmetic (no push, gather, deposit or field update) and is the one
+piece shared by the CUDA path and the CPU oracle used by the tests.
+
+Every random number comes from numpy's Philox4x32-10 counter-based generator
+(Salmon et al., SC'11) keyed by an explicit seed.  Offsets, momenta and
+weights are rounded to float32-representable values, so the FP32 path, the
+FP64 path and the oracle all start from bit-identical states.
+
+Units are normalised (c = eps0 = 1, |e| = m_e = 1).  The thermal workloads use
+c/omega_p and 1/omega_p with n0 = 1; the laser workloads use c/omega_0 and
+1/omega_0 (lambda = 2 pi) with the critical density n_c = 1.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 20261202
+
+
+def generator(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+def _f32_unit(a: np.ndarray) -> np.ndarray:
+    """Round to float32 and keep the value inside [0, 1)."""
+    a = a.astype(np.float32)
+    a = np.minimum(a, np.nextafter(np.float32(1.0), np.float32(0.0)))
+    a = np.maximum(a, np.float32(0.0))
+    return a.astype(np.float64)
+
+
+@dataclass
+class Particles:
+    """Initial state of one species.
+
+    cell: (dim, n) int64 cell coordinates; off: (dim, n) in-cell offsets in
+    [0, 1) (cell units); u: (3, n) momenta u = gamma v; w: (n,) weights;
+    id: (n,) int32 particle ids (0..n-1).
+    """
+    q: float
+    m: float
+    cell: np.ndarray
+    off: np.ndarray
+    u: np.ndarray
+    w: np.ndarray
+    id: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.w.shape[0])
+
+
+@dataclass
+class SpeciesSpec:
+    q: float
+    m: float
+    ppc: int
+    vth: float                      # per-component momentum spread (u ~ N(0, vth^2))
+    density: float = 1.0            # peak density
+    profile: str = "uniform"        # "uniform" | "slab"
+    slab: tuple = ()                # (ramp_start, ramp_end, plateau_end) in x, physical units
+    same_positions_as: int = -1     # load at the positions of an earlier species
+
+
+@dataclass
+class LaserSpec:
+    a0: float
+    w0: float
+    tau: float                      # full sin^2 envelope duration
+    omega: float = 1.0
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    n: tuple
+    h: tuple
+    dt: float
+    order: int                      # 1 = CIC, 2 = TSC
+    absorb_x: bool
+    species: list
+    steps: int
+    laser: LaserSpec | None = None
+    precision: str = "fp32"         # "fp64" | "fp32"
+    seed: int = SEED_BASE
+    notes: str = ""
+
+    @property
+    def cells(self) -> int:
+        return int(np.prod(self.n))
+
+    @property
+    def dV(self) -> float:
+        return float(np.prod(self.h))
+
+    def laser_center(self):
+        return tuple(0.5 * self.n[d] * self.h[d] for d in range(1, self.dim))
+
+
+def cfl_dt(h, eta=0.95) -> float:
+    """dt = eta / (c sqrt(sum h^-2)) (Sec. 3.2)."""
+    return eta / math.sqrt(sum(1.0 / x ** 2 for x in h))
+
+
+def _density(spec: SpeciesSpec, xc: np.ndarray) -> np.ndarray:
+    if spec.profile == "uniform":
+        return np.full(xc.shape, spec.density)
+    r0, r1, p1 = spec.slab
+    n = np.zeros(xc.shape)
+    ramp = (xc >= r0) & (xc < r1)
+    n[ramp] = spec.density * (xc[ramp] - r0) / (r1 - r0)
+    n[(xc >= r1) & (xc < p1)] = spec.density
+    return n
+
+
+def load_species(wl: Workload, sid: int, previous: list | None = None,
+                 cells: tuple | None = None) -> Particles:
+    """Exactly ``ppc`` particles per loaded cell, uniform in the cell, with
+    momenta u_i ~ N(0, vth^2) and weight w = n(x_cell) dV / ppc.  Cells of zero
+    density get no particles.  ``cells`` restricts loading to a box of cells
+    ((lo, hi) per dimension) for sampled runs."""
+    spec = wl.species[sid]
+    g = generator(wl.seed + 1000 * sid)
+    dim = wl.dim
+    axes = []
+    for d in range(dim):
+        lo, hi = (0, wl.n[d]) if cells is None else cells[d]
+        axes.append(np.arange(lo, hi, dtype=np.int64))
+    # cell coordinates, x fastest
+    mesh = np.meshgrid(*axes[::-1], indexing="ij")
+    cc = [m.reshape(-1) for m in mesh[::-1]]            # cc[0] = x index, ...
+    xc = (cc[0] + 0.5) * wl.h[0]
+    dens = _density(spec, xc)
+    keep = dens > 0.0
+    cc = [c[keep] for c in cc]
+    dens = dens[keep]
+    ncell = dens.shape[0]
+    ppc = spec.ppc
+    n = ncell * ppc
+    cell = np.stack([np.repeat(c, ppc) for c in cc]) if dim else np.zeros((0, n), np.int64)
+    if spec.same_positions_as >= 0 and previous is not None:
+        src = previous[spec.same_positions_as]
+        assert src.n == n
+        cell = src.cell.copy()
+        off = src.off.copy()
+    else:
+        off = _f32_unit(g.random((dim, n)))
+    u = (g.standard_normal((3, n)) * spec.vth).astype(np.float32).astype(np.float64)
+    w = (np.repeat(dens, ppc) * wl.dV / ppc).astype(np.float32).astype(np.float64)
+    ids = np.arange(n, dtype=np.int32)
+    return Particles(spec.q, spec.m, cell, off, u, w, ids)
+
+
+def load_all(wl: Workload, cells: tuple | None = None) -> list:
+    out = []
+    for s in range(len(wl.species)):
+        out.append(load_species(wl, s, out, cells))
+    return out
+
+
+# --------------------------------------------------------------- workloads
+ELECTRON = dict(q=-1.0, m=1.0)
+PROTON = dict(q=1.0, m=1836.0)
+LAMBDA = 2.0 * math.pi
+
+
+def thermal2d(n=64, ppc=16, vth=0.01, order=1, steps=200, precision="fp64", seed=None) -> Workload:
+    """2D3V periodic thermal plasma, dx = dy = 0.1 c/omega_p, dt = 0.95 CFL, one
+    electron species with a fixed (not deposited) ion background."""
+    h = (0.1, 0.1)
+    return Workload(f"thermal2d_{n}x{n}_ppc{ppc}", 2, (n, n), h, cfl_dt(h), order, False,
+                    [SpeciesSpec(**ELECTRON, ppc=ppc, vth=vth)], steps,
+                    precision=precision, seed=SEED_BASE + 1000 * 1 if seed is None else seed)
+
+
+def laser2d(nx=2048, ny=1024, ppc=32, order=2, steps=1600, precision="fp32", seed=None) -> Workload:
+    """2D3V laser-plasma: dx = lambda/32, a0 = 10 laser (waist 4 lambda, 8-cycle
+    sin^2 envelope) entering at x-min through an absorbing edge; electron +
+    proton slab at 10 n_c with a 2 lambda linear ramp; absorbing x, periodic y.
+    The slab sits at the same fractions of the box when nx is scaled down."""
+    dx = LAMBDA / 32.0
+    h = (dx, dx)
+    Lx = nx * dx
+    r0, r1, p1 = (16.0 / 64.0) * Lx, (18.0 / 64.0) * Lx, (48.0 / 64.0) * Lx
+    sp = [SpeciesSpec(**ELECTRON, ppc=ppc, vth=0.01, density=10.0, profile="slab", slab=(r0, r1, p1)),
+          SpeciesSpec(**PROTON, ppc=ppc, vth=0.0, density=10.0, profile="slab", slab=(r0, r1, p1),
+                      same_positions_as=0)]
+    return Workload(f"laser2d_{nx}x{ny}", 2, (nx, ny), h, cfl_dt(h), order, True, sp, steps,
+                    laser=LaserSpec(a0=10.0, w0=4.0 * LAMBDA, tau=8.0 * LAMBDA),
+                    precision=precision, seed=SEED_BASE + 1000 * 2 if seed is None else seed)
+
+
+def thermal3d(n=256, ppc=8, vth=0.05, order=2, steps=100, precision="fp32", seed=None) -> Workload:
+    """3D3V periodic thermal plasma, dx = 0.1 c/omega_p, dt = 0.95 CFL, electrons
+    with a fixed ion background (the roofline run at n = 256, ppc = 8)."""
+    h = (0.1, 0.1, 0.1)
+    return Workload(f"thermal3d_{n}^3_ppc{ppc}", 3, (n, n, n), h, cfl_dt(h), order, False,
+                    [SpeciesSpec(**ELECTRON, ppc=ppc, vth=vth)], steps,
+                    precision=precision, seed=SEED_BASE + 1000 * 3 if seed is None else seed)
+
+
+def laser3d(nx=512, ny=256, nz=256, ppc=16, order=1, steps=500, precision="fp32", seed=None) -> Workload:
+    """3D3V laser-target: dx = lambda/32, a0 = 20 laser (waist 2 lambda, 8-cycle
+    envelope) on a 30 n_c slab 2 lambda thick at x in [4, 6] lambda (scaled with
+    nx), electrons + protons, absorbing x, periodic y and z."""
+    dx = LAMBDA / 32.0
+    h = (dx, dx, dx)
+    Lx = nx * dx
+    r0 = (4.0 / 16.0) * Lx
+    r1 = r0 + 1e-9
+    p1 = (6.0 / 16.0) * Lx
+    sp = [SpeciesSpec(**ELECTRON, ppc=ppc, vth=0.01, density=30.0, profile="slab", slab=(r0, r1, p1)),
+          SpeciesSpec(**PROTON, ppc=ppc, vth=0.0, density=30.0, profile="slab", slab=(r0, r1, p1),
+                      same_positions_as=0)]
+    return Workload(f"laser3d_{nx}x{ny}x{nz}", 3, (nx, ny, nz), h, cfl_dt(h), order, True, sp, steps,
+                    laser=LaserSpec(a0=20.0, w0=2.0 * LAMBDA, tau=8.0 * LAMBDA),
+                    precision=precision, seed=SEED_BASE + 1000 * 5 if seed is None else seed)
+
+
+@dataclass
+class EnsembleMember:
+    n: tuple
+    ppc: int
+    vth: float
+
+
+def ensemble(count=96, lo=128, hi=768, seed=None) -> list:
+    """Batched ensemble: independent 2D3V periodic plasmas with sides drawn
+    uniformly from [lo, hi], 4..64 particles per cell and v_th in [0.005, 0.1]."""
+    g = generator(SEED_BASE + 1000 * 4 if seed is None else seed)
+    out = []
+    for i in range(count):
+        nx, ny = (int(v) for v in g.integers(lo, hi + 1, size=2))
+        ppc = int(g.integers(4, 65))
+        vth = float(g.uniform(0.005, 0.1))
+        out.append(thermal2d(n=nx, ppc=ppc, vth=vth, order=1, steps=100, precision="fp32",
+                             seed=SEED_BASE + 1000 * 4 + 1 + i))
+        out[-1].n = (nx, ny)
+        out[-1].name = f"ens{i}_{nx}x{ny}_ppc{ppc}"
+    return out
