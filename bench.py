@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""Throughput of the explicit electromagnetic PIC hot path on one B300.
+
+One step = the whole hot path for every species: Maxwell half step (E, B,
+absorbing edges, laser), current zeroing, sort by tile, the fused gather /
+Boris / Esirkepov kernel, Maxwell half step.  The metric is particle-steps
+per second of the whole job (alive particles x steps / seconds, summed over
+ranks).  The dominant kernel (the fused particle kernel) is also timed by
+itself with CUDA events on its own stream, and reported against the measured
+HBM copy bandwidth as the roofline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+Under torchrun each rank runs an independent replica of the workload (the
+problems do not exchange data; "scaling": "weak").  --impl reference times
+the FP64 CPU oracle on a bounded sample of the same workload on the host.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (description, pre-steps before warm-up)
+    "laser2d": ("2D3V laser-plasma 2048x1024, dx=lambda/32, a0=10 w0=4lambda 8-cycle laser "
+                "through an absorbing x-min edge, e-+p slab 10 n_c with 2 lambda ramp, "
+                "32+32 particles/cell, TSC, FP32 push + int64 fixed-point deposit", 800),
+    "thermal3d": ("3D3V periodic thermal plasma 256^3, 8 electrons/cell (134M), v_th=0.05c, TSC, "
+                  "FP32 cell+offset positions, int64 fixed-point deposit", 0),
+    "thermal2d": ("2D3V periodic thermal plasma 64x64, 16 electrons/cell, v_th=0.01c, CIC", 0),
+}
+
+
+def make_workload(name, precision, seed_offset=0, ny=None):
+    from paper_2607_13507_b300 import workloads as W
+    if name == "laser2d":
+        wl = W.laser2d(precision=precision, ny=ny or 1024)
+    elif name == "thermal3d":
+        wl = W.thermal3d(precision=precision)
+    elif name == "thermal2d":
+        wl = W.thermal2d(precision=precision)
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    wl.seed += seed_offset
+    return wl
+
+
+def algorithmic_bytes(wl, n_particles, loaded_cells, precision):
+    """Bytes the fused kernel must move for one species launch: each particle
+    read once and written once, the E/B of the loaded cells read once and the
+    current of those cells written once (int64 J, 3 components)."""
+    d = wl.dim
+    if precision == "fp32":
+        rd = 4 + 4 * d + 12 + 4          # cell, offsets, u, w
+        wr = 4 + 4 * d + 12              # cell, offsets, u
+        grid = 24 + 24                   # E/B float32 read, J int64 written
+    else:
+        rd = 8 * d + 24 + 8
+        wr = 8 * d + 24
+        grid = 48 + 24
+    return n_particles * (rd + wr) + loaded_cells * grid, rd + wr, grid
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2607_13507_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(workload)
+    except Exception:
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+# ------------------------------------------------------------------ the GPU arm
+def run_b300(args, rank, world, local_rank):
+    import torch
+    from paper_2607_13507_b300 import build, lpic
+    from paper_2607_13507_b300 import workloads as W
+
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
+
+    wl = make_workload(args.workload, args.precision, seed_offset=rank, ny=args.ny)
+    prec = lpic.FP32_FIXED if args.precision == "fp32" else lpic.FP64
+    parts = W.load_all(wl)
+    G = lpic.grid_for(wl, prec, device=dev)
+    for p in parts:
+        G.add_species(p, stream=stream)
+    loaded = [p.n // wl.species[i].ppc for i, p in enumerate(parts)]
+    del parts
+    dt = G.dt
+    pre = WORKLOADS[args.workload][1] if args.pre_steps is None else args.pre_steps
+
+    def one_step(t, evs=None):
+        G.maxwell_half(0, t, stream)
+        G.zero_current(stream)
+        for sp in G.species:
+            if prec == lpic.FP32_FIXED:
+                G.sort(sp.id, stream)
+            if evs is not None:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                G.gather_push_deposit(sp.id, stream)
+                b.record(stream)
+                evs.append((sp.id, a, b))
+            else:
+                G.gather_push_deposit(sp.id, stream)
+        G.maxwell_half(1, t + 0.5 * dt, stream)
+
+    step = 0
+    with torch.cuda.stream(stream):
+        for _ in range(pre):
+            one_step(step * dt)
+            step += 1
+        for _ in range(args.warmup):
+            one_step(step * dt)
+            step += 1
+    stream.synchronize()
+    if G.check_status(stream) != 0:
+        raise SystemExit("device status bits set during warm-up")
+    counts0 = [sp.query(stream)[1] for sp in G.species]
+
+    if world > 1:
+        torch.distributed.barrier()
+    clock = ClockSampler(local_rank)
+    clock.start()
+    time.sleep(0.3)
+    launches0 = G.info().launches
+    evs = []
+    t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    t_start.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            one_step(step * dt, evs)
+            step += 1
+    t_stop.record(stream)
+    torch.cuda.synchronize(dev)
+    elapsed = t_start.elapsed_time(t_stop) / 1e3
+    launches = G.info().launches - launches0
+    clocks = clock.stop()
+    if G.check_status(stream) != 0:
+        raise SystemExit("device status bits set during the timed steps")
+    counts1 = [sp.query(stream)[1] for sp in G.species]
+    psteps = sum(0.5 * (a + b) for a, b in zip(counts0, counts1)) * args.steps
+
+    # dominant kernel: per-launch times and algorithmic bytes
+    kt = {}
+    for sid, a, b in evs:
+        kt.setdefault(sid, []).append(a.elapsed_time(b) / 1e3)
+    gpd_time = sum(sum(v) for v in kt.values())
+    algo_bytes_step = 0
+    for i, sp in enumerate(G.species):
+        n_mean = 0.5 * (counts0[i] + counts1[i])
+        algo_bytes_step += algorithmic_bytes(wl, n_mean, loaded[i], args.precision)[0]
+    launch_bytes = algo_bytes_step / len(G.species)
+    launch_time = gpd_time / max(1, sum(len(v) for v in kt.values()))
+
+    if world > 1:
+        t = torch.tensor([elapsed, psteps], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        elapsed, psteps = float(mx[0]), float(t[1])
+
+    result = None
+    if rank == 0:
+        peaks, which = measured_peaks()
+        peak = float(peaks["hbm_gbs"])
+        achieved = launch_bytes / launch_time / 1e9
+        per_ps = algorithmic_bytes(wl, 1, 0, args.precision)[1]
+        result = {
+            "metric": "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)",
+            "value": psteps / elapsed,
+            "unit": "particle-steps/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 (int64 fixed-point current)" if args.precision == "fp32" else "f64",
+            "data": "synthetic (seeded Philox initial conditions)",
+            "config": {
+                "workload": WORKLOADS[args.workload][0],
+                "grid": list(wl.n), "species": len(wl.species),
+                "particles": int(sum(counts0)), "pre_steps": pre,
+                "l2": "inputs larger than L2 (particle state %.1f GB)" % (
+                    sum(counts0) * algorithmic_bytes(wl, 1, 0, args.precision)[1] / 2 / 1e9),
+                "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            },
+            "gpd_particle_steps_per_s": psteps / max(gpd_time, 1e-12) / world if world == 1 else None,
+            "roofline": {
+                "bound": "hbm", "kernel": "k_gpd32" if args.precision == "fp32" else "k_gpd64",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{which} hbm_gbs",
+                "bytes_per_particle_step": per_ps,
+                "algorithmic_bytes_per_launch": launch_bytes,
+                "launch_ms": 1e3 * launch_time,
+                "traffic": ncu_traffic(args.workload),
+            },
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+    state = dict(G=G, stream=stream, dev=dev, step=step, counts=counts1, wl=wl)
+    return result, state
+
+
+def run_e2e(args, st):
+    """Same metric through host buffers: every step copies the state (particle
+    buffers and fields) from pinned host memory to the device, runs the step,
+    and copies the state back to pinned host memory."""
+    import torch
+    G, stream, dev = st["G"], st["stream"], st["dev"]
+    dt = G.dt
+    cur = [sp.query(stream)[0] for sp in G.species]
+    host_p = [torch.empty(sp.buffers[0].shape, dtype=sp.buffers[0].dtype, pin_memory=True)
+              for sp in G.species]
+    for h, sp, c in zip(host_p, G.species, cur):
+        h.copy_(sp.buffers[c])
+    fields = G.E + G.B + G.J
+    host_f = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in fields]
+    for h, f in zip(host_f, fields):
+        h.copy_(f)
+    nbytes = sum(h.numel() * h.element_size() for h in host_p + host_f)
+    steps = max(1, min(args.steps, args.e2e_steps))
+    step = st["step"]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    psteps = 0
+    with torch.cuda.stream(stream):
+        for _ in range(steps):
+            for h, sp, c in zip(host_p, G.species, cur):
+                sp.buffers[c].copy_(h, non_blocking=True)
+            for h, f in zip(host_f, fields):
+                f.copy_(h, non_blocking=True)
+            G.step(step * dt, stream)
+            step += 1
+            for i, sp in enumerate(G.species):
+                cur[i], n = sp.query(stream)
+                psteps += n
+                host_p[i].copy_(sp.buffers[cur[i]], non_blocking=True)
+            for h, f in zip(host_f, fields):
+                h.copy_(f, non_blocking=True)
+            stream.synchronize()
+    el = time.perf_counter() - t0
+    return {"value": psteps / el, "unit": "particle-steps/s", "h2d_bytes_per_step": int(nbytes),
+            "d2h_bytes_per_step": int(nbytes), "steps": steps}
+
+
+# ------------------------------------------------------------------ the oracle
+def oracle_sample(args, budget_s, max_steps):
+    """Time the FP64 CPU oracle, as it stands (one thread), on a bounded
+    sample of the workload: the full x extent with the first 16 rows (2D) or
+    a 32^3 box (3D), same cell size, density profile and particles per cell."""
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2607_13507_b300 import workloads as W
+    wl = make_workload(args.workload, "fp64")
+    if wl.dim == 2:
+        sample = dict(n=(wl.n[0], min(16, wl.n[1])))
+    else:
+        sample = dict(n=(32, 32, 32))
+    wl.n = sample["n"]
+    parts = W.load_all(wl)
+    laser = None
+    if wl.laser is not None:
+        c = wl.laser_center()
+        laser = O.Laser(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega, c[0],
+                        c[1] if wl.dim == 3 else 0.0)
+    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x, laser=laser)
+    h = np.array(wl.h)[:, None]
+    sps = [O.Species(p.q, p.m, (p.cell + p.off) * h, p.u, p.w) for p in parts]
+    npart = sum(p.n for p in parts)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps and (time.perf_counter() - t0) < budget_s:
+        O.step(g, sps, steps * wl.dt)
+        steps += 1
+    el = time.perf_counter() - t0
+    desc = (f"{'x'.join(str(v) for v in wl.n)} cells of the workload (same dx, profile, ppc), "
+            f"{npart} particles, {steps} steps, FP64 oracle, 1 thread")
+    return npart * steps / el, desc, steps, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    val, desc, steps, el = oracle_sample(args, budget_s=max(10.0, 0.5 * (args.steps + args.warmup)),
+                                         max_steps=args.steps + args.warmup)
+    return {
+        "metric": "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)",
+        "value": val, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
+        "warmup": 0, "ms_per_step": 1e3 * el / max(steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Philox initial conditions)",
+        "config": {"workload": WORKLOADS[args.workload][0], "sample": desc},
+        "impl": "reference",
+        "cpu_baseline": {"value": val, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": val, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="laser2d")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--pre-steps", type=int, default=None,
+                    help="untimed steps before warm-up (default: bring the laser onto the target)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ny", type=int, default=None,
+                    help="transverse cells of the 2D laser workload (smaller cases for profiling)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    res, state = run_b300(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_e2e:
+            res["e2e"] = run_e2e(args, state)
+        if world == 1 and not args.no_cpu_baseline:
+            val, desc, steps, el = oracle_sample(args, args.cpu_budget, 60)
+            res["cpu_baseline"] = {"value": val, "unit": "particle-steps/s", "cores": 1,
+                                   "kind": "oracle", "sample": desc}
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

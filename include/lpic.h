@@ -1,0 +1,217 @@
+/*
+ * lpic.h -- C ABI of liblpic: the hot path of the explicit electromagnetic
+ * particle-in-cell timestep of lambdaPIC (Algorithm 1 without QED, load
+ * balancing or MPI) on one NVIDIA B300 (sm_103a).
+ *
+ * Per particle: field gather from the Yee grid (Sec. 3.1), relativistic Boris
+ * push (Sec. 3.1), Esirkepov charge-conserving current deposit (Sec. 3.1); per
+ * grid: the Yee FDTD update split in two dt/2 halves (Sec. 3.2 Eq. 1-4,
+ * Algorithm 1), with periodic or absorbing (first-order Mur) x edges and an
+ * incoming laser at x-min (Sec. 4.2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Units: normalised, c = eps0 = 1, charges in |e|, masses in m_e.
+ * Memory: every data pointer is a DEVICE pointer owned by the caller
+ *   (borrowed: it must stay valid until lpic_destroy_grid).  The library owns
+ *   only its scratch (sort keys, tile tables, status word), allocated in
+ *   lpic_create_grid / lpic_add_species and freed in lpic_destroy_grid.  No
+ *   call allocates after lpic_add_species.
+ * Streams: calls taking a cudaStream_t enqueue work on that stream and return
+ *   without synchronising, except where "synchronises" is stated.  The
+ *   non-synchronising calls are capturable in a CUDA graph.
+ * Errors: every call returns an lpic_status.  Argument errors are detected on
+ *   the host and returned at once (nothing is enqueued); CUDA launch errors
+ *   return LPIC_ECUDA.  Errors found by kernels (a particle that moved a full
+ *   cell, left its tile's halo or an absorbing edge region, a non-finite
+ *   momentum) set bits of a device status word that lpic_check_status
+ *   returns.  lpic_last_error() gives a message for the calling thread's last
+ *   failure.  No C++ exception crosses this interface.
+ *
+ * Field layout: each component is a dense row-major array [nz][ny][fx]
+ *   (nz = 1 in 2D), fx = nx for periodic x and nx + 1 for absorbing x.  Index
+ *   (i, j, k) of a component stands for its staggered Yee position:
+ *     E_x (i+1/2, j, k)   E_y (i, j+1/2, k)   E_z (i, j, k+1/2)
+ *     B_x (i, j+1/2, k+1/2)   B_y (i+1/2, j, k+1/2)   B_z (i+1/2, j+1/2, k)
+ *   and J is co-located with E.  In 2D the k offsets are dropped.  Element
+ *   types: LPIC_FP64 -> E, B, J double; LPIC_FP32_FIXED -> E, B float and J
+ *   int64 fixed point (J_c = J_int * lpic_grid_info.j_scale[c]).
+ *
+ * Particle layout: a species lives in two caller-owned device buffers (ping
+ *   and pong).  The sort moves particles from the current buffer to the other
+ *   one and flips them; lpic_species_query tells which one is current.  Each
+ *   buffer is a struct of arrays, every array `capacity` entries long, in
+ *   this order (capacity must be a multiple of 64, so every array starts on
+ *   a 256-byte boundary):
+ *     LPIC_FP32_FIXED: int32 cell, float off[dim], float u[3], float w, int32 id
+ *        cell = (k * ny + j) * nx + i of the particle's cell (-1 = removed),
+ *        off = in-cell offsets in [0, 1) (cell units).
+ *     LPIC_FP64:       double x[dim], double u[3], double w, int32 id
+ *        x = physical position, w = 0 marks a removed particle.
+ *   u = gamma v / c.  Particles are stored leapfrog-style: at the loop
+ *   boundary t_n the buffers hold x^{n+1/2} = x^n + (dt/2) v^n and u^n (the
+ *   second half push of one step and the first half push of the next, which
+ *   use the same velocity, are fused).  lpic_positions_at_step returns x^n.
+ */
+#ifndef LPIC_H
+#define LPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LPIC_OK = 0,
+    LPIC_EINVAL = 1,        /* bad argument or descriptor */
+    LPIC_ENOMEM = 2,        /* scratch allocation failed */
+    LPIC_ECUDA = 3,         /* a CUDA runtime call or launch failed */
+    LPIC_EDEVICE = 4,       /* lpic_check_status: a kernel set status bits */
+    LPIC_EUNSUPPORTED = 5   /* valid but not supported combination */
+} lpic_status;
+
+/* device status bits (lpic_check_status) */
+#define LPIC_ST_CFL       0x1u  /* a particle moved >= 1 cell in a step */
+#define LPIC_ST_HALO      0x2u  /* a particle left its tile's halo (sort too rare) */
+#define LPIC_ST_NAN       0x4u  /* non-finite momentum */
+#define LPIC_ST_OUTSIDE   0x8u  /* a deposit or gather reached past an absorbing edge */
+#define LPIC_ST_OVERFLOW  0x10u /* a fixed-point value exceeded its bound */
+#define LPIC_ST_TIMEOUT   0x20u /* a bounded device wait gave up */
+
+enum { LPIC_FP64 = 0, LPIC_FP32_FIXED = 1 };
+
+typedef struct lpic_grid *lpic_grid_t;    /* opaque, owned by the library */
+
+/* Incoming laser at x-min (Sec. 4.2): E_y polarised,
+ * E_inc(x, y, z, t) = a0 sin^2(pi s / tau) exp(-r^2 / w0^2) sin(omega s),
+ * s = t - x in (0, tau), r^2 = (y - yc)^2 + (z - zc)^2 (no z term in 2D). */
+typedef struct {
+    double a0, w0, tau, omega, yc, zc;
+} lpic_laser_desc;
+
+typedef struct {
+    int dim;                    /* 2 (2D3V) or 3 (3D3V) */
+    int nx, ny, nz;             /* cells per dimension; nz ignored in 2D */
+    double dx, dy, dz, dt;      /* cell sizes and time step; dz ignored in 2D.
+                                   dt must satisfy the Courant limit of Sec. 3.2 */
+    int absorb_x;               /* 0: periodic x; 1: absorbing x edges */
+    int shape_order;            /* 1: cloud-in-cell, 2: quadratic spline (TSC) */
+    int precision;              /* LPIC_FP64 or LPIC_FP32_FIXED */
+    int tile[3];                /* cells per tile for the FP32 path; 0 = default */
+    void *E[3], *B[3], *J[3];   /* caller-owned device field arrays (see layout) */
+    const lpic_laser_desc *laser; /* NULL: no laser; copied at create (needs absorb_x) */
+} lpic_grid_desc;
+
+typedef struct {
+    double q, m;                /* charge (|e| units, signed) and mass (m_e units) */
+    long long count;            /* particles in buffers[0] at add time (first count entries) */
+    long long capacity;         /* entries per array, multiple of 64, >= count */
+    void *buffers[2];           /* two device buffers of lpic_species_bytes() bytes */
+    int staggered;              /* 0: buffers hold x^0, add_species advances them by dt/2;
+                                   1: they already hold x^{1/2} */
+} lpic_species_desc;
+
+typedef struct {
+    int fixed_shift;            /* F: FP32 path J_int unit is 2^-F charge */
+    double j_scale[3];          /* J_c = J_int * j_scale[c] (FP32 path) */
+    double rho_scale;           /* rho = rho_int * rho_scale (FP32 path) */
+    int tile[3];                /* tile shape in use */
+    long long ntiles;
+    int fx;                     /* stored x extent of the field arrays */
+    long long launches;         /* kernel launches issued so far by calls on this grid */
+} lpic_grid_info;
+
+typedef struct {
+    double kinetic;             /* sum_p w m (gamma - 1), gamma from u^n */
+    double field;               /* (1/2) sum (E^2 + B^2) dV over stored positions */
+    double charge;              /* sum_p q w */
+    long long particles;        /* alive particles, all species */
+} lpic_diag;
+
+/* Size in bytes of one species buffer (ping or pong). */
+size_t lpic_species_bytes(int dim, int precision, long long capacity);
+
+/* Create a grid from a descriptor (Sec. 3.2 grid; Sec. 2.1 Patches
+ * replaced by one guard-less global grid per instance).  Checks the
+ * descriptor (dimensions, Courant limit, shape order, laser needs absorbing
+ * x, tile shape) and allocates the library's scratch.  Synchronous. */
+lpic_status lpic_create_grid(const lpic_grid_desc *desc, lpic_grid_t *out);
+
+/* Free the library's scratch (not the caller's buffers).  Synchronises the
+ * device.  NULL is accepted. */
+lpic_status lpic_destroy_grid(lpic_grid_t grid);
+
+/* Register a species (Sec. 2.1 Species): checks the descriptor, allocates the
+ * per-species scratch, computes the fixed-point shift F from the bound
+ * sum_s capacity_s * max|q w|_s so that no int64 current can overflow, and,
+ * unless staggered, advances positions by dt/2.  Must be called before the
+ * first lpic_gather_push_deposit.  Synchronises `stream`. */
+lpic_status lpic_add_species(lpic_grid_t grid, const lpic_species_desc *desc,
+                             cudaStream_t stream, int *species_id);
+
+/* Which buffer is current (0 or 1) and how many particles it holds (alive
+ * particles first after a sort).  Synchronises `stream`. */
+lpic_status lpic_species_query(lpic_grid_t grid, int species_id, cudaStream_t stream,
+                               int *current_buffer, long long *count);
+
+/* Sort a species by cell tile (Algorithm 1 "sort particles by cell index"):
+ * counting sort (histogram, scan, scatter) from the current buffer into the
+ * other one, dropping removed particles; then the buffers flip.  Within a
+ * tile the order is not specified.  species_id -1 sorts every species. */
+lpic_status lpic_sort_particles(lpic_grid_t grid, int species_id, cudaStream_t stream);
+
+/* Zero the current array J (before the species loop of a step). */
+lpic_status lpic_zero_current(lpic_grid_t grid, cudaStream_t stream);
+
+/* The fused particle kernel (Sec. 2.3 "unified pusher", Algorithm 1 particle
+ * loop): for each particle of the species, gather E and B at x^{n+1/2}
+ * (Sec. 3.1), Boris u^n -> u^{n+1} (Sec. 3.1), advance the position by
+ * dt v^{n+1} to x^{n+3/2}, and add the Esirkepov current of that straight
+ * path (Sec. 3.1) to J.  FP64 path: one thread per particle, double atomics.
+ * FP32 path: needs the species sorted by tile since its last push (the sort
+ * of the same step); one thread block per tile with the tile's E/B halo and
+ * an int64 fixed-point J accumulator in shared memory, flushed once per tile
+ * with integer atomics (deterministic, bit-exact continuity). */
+lpic_status lpic_gather_push_deposit(lpic_grid_t grid, int species_id, cudaStream_t stream);
+
+/* One Maxwell half step (Sec. 3.2 Eq. 3-4, split as in Algorithm 1) from t to
+ * t + dt/2.  half = 0: E += (dt/2)(curl B - J), then B -= (dt/2) curl E;
+ * half = 1: B first, then E.  Absorbing x edges use first-order Mur on E_y,
+ * E_z with the laser (if any) entering at x-min. */
+lpic_status lpic_maxwell_half_step(lpic_grid_t grid, int half, double t, cudaStream_t stream);
+
+/* One full step t -> t + dt (Algorithm 1): Maxwell half 0, zero J, per
+ * species sort (FP32 path) and gather_push_deposit, Maxwell half 1. */
+lpic_status lpic_step(lpic_grid_t grid, double t, cudaStream_t stream);
+
+/* Charge density of the stored positions x^{n+1/2} (the charge the deposit
+ * conserves, Sec. 3.1), added into rho[nz][ny][fx]: FP64 path double
+ * q w S / dV; FP32 path int64 sum of rint(2^F q w S) with the same shape
+ * arithmetic as the deposit (rho = rho_int * rho_scale). */
+lpic_status lpic_deposit_charge(lpic_grid_t grid, int species_id, void *rho, cudaStream_t stream);
+
+/* Write x^n = x^{n+1/2} - (dt/2) v^n as doubles, out[d * capacity + p] for
+ * d < dim, in current-buffer order (removed particles give NaN). */
+lpic_status lpic_positions_at_step(lpic_grid_t grid, int species_id, double *out,
+                                   cudaStream_t stream);
+
+/* FP64 energy and charge reductions (Sec. 4.1 energy diagnostic).
+ * Synchronises `stream`. */
+lpic_status lpic_diagnostics(lpic_grid_t grid, lpic_diag *out, cudaStream_t stream);
+
+lpic_status lpic_grid_get_info(lpic_grid_t grid, lpic_grid_info *out);
+
+/* Synchronise `stream`, return the device status bits in *bits and clear
+ * them; returns LPIC_EDEVICE when any bit was set. */
+lpic_status lpic_check_status(lpic_grid_t grid, cudaStream_t stream, unsigned *bits);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char *lpic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPIC_H */

@@ -1,0 +1,635 @@
+// lpic_api.cu -- host side of liblpic: the C ABI declared in include/lpic.h.
+// Descriptor checks, scratch ownership, the fixed-point shift, and the
+// launches of the Maxwell, sort, particle and diagnostic kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lpic.h"
+#include "lpic_common.cuh"
+#include "lpic_diag.cuh"
+#include "lpic_field.cuh"
+#include "lpic_fp32.cuh"
+#include "lpic_fp64.cuh"
+#include "lpic_sort.cuh"
+
+using namespace lpic;
+
+namespace {
+
+thread_local std::string g_err;
+
+lpic_status fail(lpic_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define LPIC_CUDA(call)                                                                   \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) return fail(LPIC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// every kernel launch site has the grid `g` in scope and counts the launch
+#define LPIC_LAUNCHED(what)                                                               \
+    do {                                                                                  \
+        ++g->launches;                                                                    \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess) return fail(LPIC_ECUDA, "launch %s: %s", what, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct Species {
+    double q = 0, m = 1;
+    long long cap = 0;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    int* d_n = nullptr;          // particles in the current buffer
+    int* d_count = nullptr;      // ntiles + 1
+    int* d_start = nullptr;      // ntiles + 2
+    int* d_cursor = nullptr;     // ntiles + 1
+    double wmax = 0;
+    bool sorted = false;         // sorted since the last push (FP32 path needs it)
+};
+
+}  // namespace
+
+struct lpic_grid {
+    lpic_grid_desc d{};
+    Laser laser{};
+    Geo geo{};
+    int T[3] = {1, 1, 1}, nt[3] = {1, 1, 1};
+    long long ntiles = 1;
+    long long nfield = 0;        // fx * ny * nz
+    int F = 0;
+    double jscale[3] = {0, 0, 0}, rho_scale = 0;
+    std::vector<Species> sp;
+    unsigned* d_status = nullptr;
+    void* d_mur = nullptr;
+    double* d_acc = nullptr;
+    unsigned long long* d_cnt = nullptr;
+    bool started = false;
+    int nsm = 148;
+    size_t smem32 = 0;
+    long long launches = 0;
+};
+
+namespace {
+
+int grid_blocks(long long work, int nsm, int per_sm = 8) {
+    long long b = (work + 255) / 256;
+    long long cap = (long long)nsm * per_sm;
+    if (b > cap) b = cap;
+    return (int)(b < 1 ? 1 : b);
+}
+
+P32 view32(const lpic_grid* g, const Species& s, int b) {
+    char* base = static_cast<char*>(s.buf[b]);
+    const size_t a = (size_t)s.cap * 4;
+    const int dim = g->d.dim;
+    P32 p{};
+    p.cell = reinterpret_cast<int*>(base);
+    for (int d = 0; d < 3; ++d)
+        p.off[d] = reinterpret_cast<float*>(base + (1 + (d < dim ? d : dim - 1)) * a);
+    for (int c = 0; c < 3; ++c) p.u[c] = reinterpret_cast<float*>(base + (1 + dim + c) * a);
+    p.w = reinterpret_cast<float*>(base + (4 + dim) * a);
+    p.id = reinterpret_cast<int*>(base + (5 + dim) * a);
+    p.n = s.d_n;
+    return p;
+}
+
+P64 view64(const lpic_grid* g, const Species& s, int b) {
+    char* base = static_cast<char*>(s.buf[b]);
+    const size_t a = (size_t)s.cap * 8;
+    const int dim = g->d.dim;
+    P64 p{};
+    for (int d = 0; d < 3; ++d) p.x[d] = reinterpret_cast<double*>(base + (d < dim ? d : dim - 1) * a);
+    for (int c = 0; c < 3; ++c) p.u[c] = reinterpret_cast<double*>(base + (dim + c) * a);
+    p.w = reinterpret_cast<double*>(base + (dim + 3) * a);
+    p.id = reinterpret_cast<int*>(base + (dim + 4) * a);
+    p.n = s.d_n;
+    return p;
+}
+
+template <typename T>
+Ptr3<T> ptr3(void* const* v) {
+    Ptr3<T> p;
+    for (int c = 0; c < 3; ++c) p.p[c] = static_cast<T*>(v[c]);
+    return p;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+__global__ void k_absmax_f32(const float* w, const int* n, unsigned* out) {
+    unsigned m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < *n; i += gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(w[i])));
+    atomicMax(out, m);
+}
+
+__global__ void k_absmax_f64(const double* w, const int* n, unsigned long long* out) {
+    unsigned long long m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < *n; i += gridDim.x * blockDim.x)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(w[i])));
+    atomicMax(out, m);
+}
+
+// tile-kernel instance and its dynamic shared memory
+template <int DIM, int ORDER>
+lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st) {
+    const P32 p = view32(g, s, s.cur);
+    Tiles t{};
+    for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; }
+    t.start = s.d_start;
+    auto kern = k_gpd32<DIM, ORDER>;
+    LPIC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem32));
+    const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
+    const float sq = (float)std::ldexp(s.q, g->F);
+    kern<<<(unsigned)g->ntiles, 256, g->smem32, st>>>(
+        g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
+        p, t, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
+        (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status);
+    LPIC_LAUNCHED("k_gpd32");
+    return LPIC_OK;
+}
+
+template <int DIM, int ORDER>
+lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
+    const P64 p = view64(g, s, s.cur);
+    k_gpd64<DIM, ORDER><<<grid_blocks(s.cap, g->nsm, 16), 256, 0, st>>>(
+        g->geo, ptr3<const double>(g->d.E), ptr3<const double>(g->d.B), ptr3<double>(g->d.J), p,
+        s.q * g->d.dt / (2.0 * s.m), s.q, g->d_status);
+    LPIC_LAUNCHED("k_gpd64");
+    return LPIC_OK;
+}
+
+template <int DIM, typename R, typename JT>
+lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st) {
+    FieldArgs<R, JT> a{};
+    for (int c = 0; c < 3; ++c) {
+        a.E[c] = static_cast<R*>(g->d.E[c]);
+        a.B[c] = static_cast<R*>(g->d.B[c]);
+        a.J[c] = static_cast<const JT*>(g->d.J[c]);
+    }
+    const double tau = 0.5 * g->d.dt;
+    a.rdx = (R)(1.0 / g->d.dx);
+    a.rdy = (R)(1.0 / g->d.dy);
+    a.rdz = (R)(DIM == 3 ? 1.0 / g->d.dz : 0.0);
+    a.tau = (R)tau;
+    for (int c = 0; c < 3; ++c) a.jfac[c] = tau * (g->d.precision == LPIC_FP32_FIXED ? g->jscale[c] : 1.0);
+    const int nb = grid_blocks(g->nfield, g->nsm, 16);
+    const int plane = g->d.ny * (DIM == 3 ? g->d.nz : 1);
+    Ptr3<R> Ep;
+    for (int c = 0; c < 3; ++c) Ep.p[c] = a.E[c];
+    auto updE = [&]() -> lpic_status {
+        if (g->geo.absorb) {
+            k_mur_save<R><<<grid_blocks(8LL * plane, g->nsm), 256, 0, st>>>(g->geo, Ep, static_cast<R*>(g->d_mur));
+            LPIC_LAUNCHED("k_mur_save");
+        }
+        k_update_E<DIM, R, JT><<<nb, 256, 0, st>>>(g->geo, a);
+        LPIC_LAUNCHED("k_update_E");
+        if (g->geo.absorb) {
+            k_mur_apply<R><<<grid_blocks(2LL * plane, g->nsm), 256, 0, st>>>(
+                g->geo, Ep, static_cast<const R*>(g->d_mur), g->laser, t, tau);
+            LPIC_LAUNCHED("k_mur_apply");
+        }
+        return LPIC_OK;
+    };
+    auto updB = [&]() -> lpic_status {
+        k_update_B<DIM, R, JT><<<nb, 256, 0, st>>>(g->geo, a);
+        LPIC_LAUNCHED("k_update_B");
+        return LPIC_OK;
+    };
+    lpic_status r;
+    if (half == 0) {
+        if ((r = updE()) != LPIC_OK) return r;
+        if ((r = updB()) != LPIC_OK) return r;
+    } else {
+        if ((r = updB()) != LPIC_OK) return r;
+        if ((r = updE()) != LPIC_OK) return r;
+    }
+    return LPIC_OK;
+}
+
+lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st) {
+    const int other = 1 - s.cur;
+    const int nt = (int)g->ntiles;
+    LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (nt + 1), st));
+    LPIC_CUDA(cudaMemsetAsync(s.d_cursor, 0, sizeof(int) * (nt + 1), st));
+    const int nb = grid_blocks(s.cap, g->nsm, 16);
+    const int dim = g->d.dim;
+    if (g->d.precision == LPIC_FP32_FIXED) {
+        const P32 src = view32(g, s, s.cur), dst = view32(g, s, other);
+        KeyFP32 key{src.cell, g->d.nx, g->d.ny, g->T[0], g->T[1], g->T[2], g->nt[0], g->nt[1], nt, dim};
+        k_sort_count<<<nb, 256, 0, st>>>(key, s.d_n, s.d_count);
+        LPIC_LAUNCHED("k_sort_count");
+        k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt + 1);
+        LPIC_LAUNCHED("k_sort_scan");
+        k_sort_scatter<<<nb, 256, 0, st>>>(key, MoveFP32{src, dst, dim}, s.d_n, s.d_start, s.d_cursor, nt);
+        LPIC_LAUNCHED("k_sort_scatter");
+    } else {
+        const P64 src = view64(g, s, s.cur), dst = view64(g, s, other);
+        KeyFP64 key{{src.x[0], src.x[1], src.x[2]}, src.w, 1.0 / g->d.dx, 1.0 / g->d.dy,
+                    dim == 3 ? 1.0 / g->d.dz : 0.0, g->d.nx, g->d.ny, g->d.nz, g->T[0], g->T[1],
+                    g->T[2], g->nt[0], g->nt[1], nt, dim};
+        k_sort_count<<<nb, 256, 0, st>>>(key, s.d_n, s.d_count);
+        LPIC_LAUNCHED("k_sort_count");
+        k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt + 1);
+        LPIC_LAUNCHED("k_sort_scan");
+        k_sort_scatter<<<nb, 256, 0, st>>>(key, MoveFP64{src, dst, dim}, s.d_n, s.d_start, s.d_cursor, nt);
+        LPIC_LAUNCHED("k_sort_scatter");
+    }
+    k_sort_finalize<<<1, 32, 0, st>>>(s.d_start, nt, s.d_n);
+    LPIC_LAUNCHED("k_sort_finalize");
+    s.cur = other;
+    s.sorted = true;
+    return LPIC_OK;
+}
+
+lpic_status check_grid(lpic_grid_t g) {
+    if (!g) return fail(LPIC_EINVAL, "grid is NULL");
+    return LPIC_OK;
+}
+
+lpic_status check_species(lpic_grid_t g, int sid) {
+    if (!g) return fail(LPIC_EINVAL, "grid is NULL");
+    if (sid < 0 || sid >= (int)g->sp.size()) return fail(LPIC_EINVAL, "species id %d out of range", sid);
+    return LPIC_OK;
+}
+
+void recompute_shift(lpic_grid* g) {
+    double total = 0.0, mx = 0.0;
+    for (const auto& s : g->sp) {
+        const double b = std::fabs(s.q) * s.wmax;
+        total += (double)s.cap * b;
+        mx = std::max(mx, b);
+    }
+    if (mx <= 0.0) { g->F = 0; }
+    else {
+        const int f1 = (int)std::floor(29.0 - std::log2(mx));
+        const int f2 = (int)std::floor(61.0 - std::log2(total));
+        g->F = std::min(f1, f2);
+    }
+    const double u = std::ldexp(1.0, -g->F);
+    const lpic_grid_desc& d = g->d;
+    if (d.dim == 3) {
+        g->jscale[0] = u / (d.dt * d.dy * d.dz);
+        g->jscale[1] = u / (d.dt * d.dx * d.dz);
+        g->jscale[2] = u / (d.dt * d.dx * d.dy);
+        g->rho_scale = u / (d.dx * d.dy * d.dz);
+    } else {
+        g->jscale[0] = u / (d.dt * d.dy);
+        g->jscale[1] = u / (d.dt * d.dx);
+        g->jscale[2] = u / (d.dx * d.dy);
+        g->rho_scale = u / (d.dx * d.dy);
+    }
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+size_t lpic_species_bytes(int dim, int precision, long long capacity) {
+    if ((dim != 2 && dim != 3) || capacity < 0) return 0;
+    if (precision == LPIC_FP32_FIXED) return (size_t)(dim + 6) * 4 * (size_t)capacity;
+    if (precision == LPIC_FP64) return (size_t)(dim + 4) * 8 * (size_t)capacity + 4 * (size_t)capacity;
+    return 0;
+}
+
+const char* lpic_last_error(void) { return g_err.c_str(); }
+
+lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
+    if (!desc || !out) return fail(LPIC_EINVAL, "NULL descriptor or output");
+    *out = nullptr;
+    const lpic_grid_desc& d = *desc;
+    if (d.dim != 2 && d.dim != 3) return fail(LPIC_EINVAL, "dim must be 2 or 3 (got %d)", d.dim);
+    const int nz = (d.dim == 3) ? d.nz : 1;
+    if (d.nx < 4 || d.ny < 4 || nz < 1 || (d.dim == 3 && d.nz < 4))
+        return fail(LPIC_EINVAL, "grid too small (%d x %d x %d), need >= 4 cells per dimension", d.nx, d.ny, nz);
+    if ((long long)d.nx * d.ny * nz >= (1LL << 31)) return fail(LPIC_EINVAL, "more than 2^31 cells");
+    if (!(d.dx > 0) || !(d.dy > 0) || (d.dim == 3 && !(d.dz > 0)) || !(d.dt > 0))
+        return fail(LPIC_EINVAL, "cell sizes and dt must be positive");
+    double s2 = 1.0 / (d.dx * d.dx) + 1.0 / (d.dy * d.dy) + (d.dim == 3 ? 1.0 / (d.dz * d.dz) : 0.0);
+    if (!(d.dt * std::sqrt(s2) < 1.0))
+        return fail(LPIC_EINVAL, "dt = %g violates the Courant limit %g", d.dt, 1.0 / std::sqrt(s2));
+    if (d.shape_order != 1 && d.shape_order != 2) return fail(LPIC_EINVAL, "shape_order must be 1 or 2");
+    if (d.precision != LPIC_FP64 && d.precision != LPIC_FP32_FIXED) return fail(LPIC_EINVAL, "bad precision");
+    if (d.absorb_x != 0 && d.absorb_x != 1) return fail(LPIC_EINVAL, "absorb_x must be 0 or 1");
+    if (d.absorb_x && d.nx < 8) return fail(LPIC_EINVAL, "absorbing x needs nx >= 8");
+    if (d.laser && !d.absorb_x) return fail(LPIC_EINVAL, "a laser needs absorbing x edges");
+    for (int c = 0; c < 3; ++c)
+        if (!d.E[c] || !d.B[c] || !d.J[c]) return fail(LPIC_EINVAL, "field pointer %d is NULL", c);
+    auto* g = new (std::nothrow) lpic_grid;
+    if (!g) return fail(LPIC_ENOMEM, "host allocation failed");
+    g->d = d;
+    g->d.nz = nz;
+    if (d.dim == 2) g->d.dz = 1.0;
+    g->laser.on = d.laser ? 1 : 0;
+    if (d.laser) {
+        g->laser.a0 = d.laser->a0; g->laser.w0 = d.laser->w0; g->laser.tau = d.laser->tau;
+        g->laser.omega = d.laser->omega; g->laser.yc = d.laser->yc; g->laser.zc = d.laser->zc;
+        if (!(g->laser.w0 > 0) || !(g->laser.tau > 0)) { delete g; return fail(LPIC_EINVAL, "laser w0 and tau must be positive"); }
+    }
+    g->d.laser = nullptr;
+    const int fx = d.absorb_x ? d.nx + 1 : d.nx;
+    g->geo = Geo{d.dim, d.nx, d.ny, nz, fx, d.absorb_x, d.dx, d.dy, g->d.dz, d.dt};
+    g->nfield = (long long)fx * d.ny * nz;
+    const int defT[2][3] = {{16, 16, 1}, {8, 8, 8}};
+    const int n3[3] = {d.nx, d.ny, nz};
+    g->ntiles = 1;
+    for (int k = 0; k < 3; ++k) {
+        int T = (k < d.dim) ? (d.tile[k] > 0 ? d.tile[k] : defT[d.dim - 2][k]) : 1;
+        if (T > n3[k]) T = n3[k];
+        if (k < d.dim && (T < 1 || T > 64)) { delete g; return fail(LPIC_EINVAL, "tile[%d] = %d out of [1, 64]", k, T); }
+        g->T[k] = T;
+        g->nt[k] = (n3[k] + T - 1) / T;
+        g->ntiles *= g->nt[k];
+    }
+    if (d.dim == 2) { g->T[2] = 1; g->nt[2] = 1; }
+    {
+        const int D = d.dim;
+        long long G = 1, H = 1;
+        for (int k = 0; k < D; ++k) { G *= g->T[k] + 4; H *= g->T[k] + 5; }
+        g->smem32 = (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 8;
+        if (d.precision == LPIC_FP32_FIXED && g->smem32 > 227 * 1024) {
+            delete g;
+            return fail(LPIC_EINVAL, "tile needs %zu bytes of shared memory (> 227 KB)", g->smem32);
+        }
+    }
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+        g->nsm = prop.multiProcessorCount;
+    const size_t fbytes = d.precision == LPIC_FP64 ? 8 : 4;
+    const int plane = d.ny * nz;
+    if (cudaMalloc(&g->d_status, 64) != cudaSuccess ||
+        cudaMalloc(&g->d_acc, 64) != cudaSuccess ||
+        cudaMalloc(&g->d_cnt, 64) != cudaSuccess ||
+        (d.absorb_x && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess)) {
+        lpic_destroy_grid(g);
+        return fail(LPIC_ENOMEM, "scratch allocation failed");
+    }
+    if (cudaMemset(g->d_status, 0, 64) != cudaSuccess) { lpic_destroy_grid(g); return fail(LPIC_ECUDA, "memset failed"); }
+    recompute_shift(g);
+    *out = g;
+    return LPIC_OK;
+}
+
+lpic_status lpic_destroy_grid(lpic_grid_t g) {
+    if (!g) return LPIC_OK;
+    cudaDeviceSynchronize();
+    for (auto& s : g->sp) {
+        cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
+    }
+    cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur);
+    delete g;
+    return LPIC_OK;
+}
+
+lpic_status lpic_grid_get_info(lpic_grid_t g, lpic_grid_info* out) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (!out) return fail(LPIC_EINVAL, "NULL output");
+    out->fixed_shift = g->F;
+    for (int c = 0; c < 3; ++c) { out->j_scale[c] = g->jscale[c]; out->tile[c] = g->T[c]; }
+    out->rho_scale = g->rho_scale;
+    out->ntiles = g->ntiles;
+    out->fx = g->geo.fx;
+    out->launches = g->launches;
+    return LPIC_OK;
+}
+
+lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaStream_t st, int* sid) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (!desc || !sid) return fail(LPIC_EINVAL, "NULL descriptor or output");
+    if (g->started) return fail(LPIC_EUNSUPPORTED, "species must be added before the first push");
+    const lpic_species_desc& d = *desc;
+    if (!(d.m > 0) || !std::isfinite(d.q)) return fail(LPIC_EINVAL, "mass must be positive, charge finite");
+    if (d.capacity <= 0 || d.capacity % 64 != 0 || d.capacity >= (1LL << 31))
+        return fail(LPIC_EINVAL, "capacity %lld must be a positive multiple of 64 below 2^31", d.capacity);
+    if (d.count < 0 || d.count > d.capacity) return fail(LPIC_EINVAL, "count %lld outside [0, capacity]", d.count);
+    if (!d.buffers[0] || !d.buffers[1] || d.buffers[0] == d.buffers[1])
+        return fail(LPIC_EINVAL, "two distinct particle buffers are required");
+    if (!aligned(d.buffers[0], 256) || !aligned(d.buffers[1], 256))
+        return fail(LPIC_EINVAL, "particle buffers must be 256-byte aligned");
+    Species s;
+    s.q = d.q; s.m = d.m; s.cap = d.capacity;
+    s.buf[0] = d.buffers[0]; s.buf[1] = d.buffers[1];
+    const int nt = (int)g->ntiles;
+    if (cudaMalloc(&s.d_n, sizeof(int) * 4) != cudaSuccess ||
+        cudaMalloc(&s.d_count, sizeof(int) * (nt + 1)) != cudaSuccess ||
+        cudaMalloc(&s.d_start, sizeof(int) * (nt + 2)) != cudaSuccess ||
+        cudaMalloc(&s.d_cursor, sizeof(int) * (nt + 1)) != cudaSuccess) {
+        cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
+        return fail(LPIC_ENOMEM, "species scratch allocation failed");
+    }
+    const int n = (int)d.count;
+    LPIC_CUDA(cudaMemcpyAsync(s.d_n, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+    // largest |w|, for the fixed-point bound
+    if (g->d.precision == LPIC_FP32_FIXED) {
+        const P32 p = view32(g, s, 0);
+        unsigned bits = 0;
+        LPIC_CUDA(cudaMemsetAsync(g->d_cnt, 0, 8, st));
+        k_absmax_f32<<<grid_blocks(s.cap, g->nsm), 256, 0, st>>>(p.w, s.d_n, reinterpret_cast<unsigned*>(g->d_cnt));
+        LPIC_LAUNCHED("k_absmax_f32");
+        LPIC_CUDA(cudaMemcpyAsync(&bits, g->d_cnt, 4, cudaMemcpyDeviceToHost, st));
+        LPIC_CUDA(cudaStreamSynchronize(st));
+        float wm;
+        std::memcpy(&wm, &bits, 4);
+        s.wmax = wm;
+    } else {
+        const P64 p = view64(g, s, 0);
+        unsigned long long bits = 0;
+        LPIC_CUDA(cudaMemsetAsync(g->d_cnt, 0, 8, st));
+        k_absmax_f64<<<grid_blocks(s.cap, g->nsm), 256, 0, st>>>(p.w, s.d_n, g->d_cnt);
+        LPIC_LAUNCHED("k_absmax_f64");
+        LPIC_CUDA(cudaMemcpyAsync(&bits, g->d_cnt, 8, cudaMemcpyDeviceToHost, st));
+        LPIC_CUDA(cudaStreamSynchronize(st));
+        double wm;
+        std::memcpy(&wm, &bits, 8);
+        s.wmax = wm;
+    }
+    if (!std::isfinite(s.wmax)) return fail(LPIC_EINVAL, "non-finite particle weight");
+    // x^0 -> x^{1/2}
+    if (!d.staggered) {
+        const int nb = grid_blocks(s.cap, g->nsm);
+        if (g->d.precision == LPIC_FP32_FIXED) {
+            const P32 p = view32(g, s, 0);
+            const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
+                        c = (float)(g->d.dt / g->d.dz);
+            if (g->d.dim == 3) k_advance32<3><<<nb, 256, 0, st>>>(g->geo, p, 0.5f, a, b, c);
+            else               k_advance32<2><<<nb, 256, 0, st>>>(g->geo, p, 0.5f, a, b, c);
+        } else {
+            const P64 p = view64(g, s, 0);
+            if (g->d.dim == 3) k_advance64<3><<<nb, 256, 0, st>>>(g->geo, p, 0.5);
+            else               k_advance64<2><<<nb, 256, 0, st>>>(g->geo, p, 0.5);
+        }
+        LPIC_LAUNCHED("k_advance");
+        LPIC_CUDA(cudaStreamSynchronize(st));
+    }
+    g->sp.push_back(s);
+    recompute_shift(g);
+    *sid = (int)g->sp.size() - 1;
+    return LPIC_OK;
+}
+
+lpic_status lpic_species_query(lpic_grid_t g, int sid, cudaStream_t st, int* cur, long long* count) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    int n = 0;
+    LPIC_CUDA(cudaMemcpyAsync(&n, g->sp[sid].d_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    if (cur) *cur = g->sp[sid].cur;
+    if (count) *count = n;
+    return LPIC_OK;
+}
+
+lpic_status lpic_sort_particles(lpic_grid_t g, int sid, cudaStream_t st) {
+    if (sid == -1) {
+        if (lpic_status r = check_grid(g)) return r;
+        for (auto& s : g->sp)
+            if (lpic_status r = sort_one(g, s, st)) return r;
+        return LPIC_OK;
+    }
+    if (lpic_status r = check_species(g, sid)) return r;
+    return sort_one(g, g->sp[sid], st);
+}
+
+lpic_status lpic_zero_current(lpic_grid_t g, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    for (int c = 0; c < 3; ++c) LPIC_CUDA(cudaMemsetAsync(g->d.J[c], 0, 8 * (size_t)g->nfield, st));
+    return LPIC_OK;
+}
+
+lpic_status lpic_gather_push_deposit(lpic_grid_t g, int sid, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    Species& s = g->sp[sid];
+    g->started = true;
+    const int D = g->d.dim, O = g->d.shape_order;
+    lpic_status r;
+    if (g->d.precision == LPIC_FP32_FIXED) {
+        if (!s.sorted) return fail(LPIC_EINVAL, "species %d must be sorted by tile before each push", sid);
+        if (D == 2) r = (O == 1) ? launch_gpd32<2, 1>(g, s, st) : launch_gpd32<2, 2>(g, s, st);
+        else        r = (O == 1) ? launch_gpd32<3, 1>(g, s, st) : launch_gpd32<3, 2>(g, s, st);
+        s.sorted = false;
+    } else {
+        if (D == 2) r = (O == 1) ? launch_gpd64<2, 1>(g, s, st) : launch_gpd64<2, 2>(g, s, st);
+        else        r = (O == 1) ? launch_gpd64<3, 1>(g, s, st) : launch_gpd64<3, 2>(g, s, st);
+    }
+    return r;
+}
+
+lpic_status lpic_maxwell_half_step(lpic_grid_t g, int half, double t, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (half != 0 && half != 1) return fail(LPIC_EINVAL, "half must be 0 or 1");
+    if (g->d.precision == LPIC_FP32_FIXED)
+        return g->d.dim == 3 ? maxwell_impl<3, float, long long>(g, half, t, st)
+                             : maxwell_impl<2, float, long long>(g, half, t, st);
+    return g->d.dim == 3 ? maxwell_impl<3, double, double>(g, half, t, st)
+                         : maxwell_impl<2, double, double>(g, half, t, st);
+}
+
+lpic_status lpic_step(lpic_grid_t g, double t, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (lpic_status r = lpic_maxwell_half_step(g, 0, t, st)) return r;
+    if (lpic_status r = lpic_zero_current(g, st)) return r;
+    for (int s = 0; s < (int)g->sp.size(); ++s) {
+        if (g->d.precision == LPIC_FP32_FIXED)
+            if (lpic_status r = sort_one(g, g->sp[s], st)) return r;
+        if (lpic_status r = lpic_gather_push_deposit(g, s, st)) return r;
+    }
+    return lpic_maxwell_half_step(g, 1, t + 0.5 * g->d.dt, st);
+}
+
+lpic_status lpic_deposit_charge(lpic_grid_t g, int sid, void* rho, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (!rho) return fail(LPIC_EINVAL, "rho is NULL");
+    Species& s = g->sp[sid];
+    const int nb = grid_blocks(s.cap, g->nsm, 16);
+    const int D = g->d.dim, O = g->d.shape_order;
+    if (g->d.precision == LPIC_FP32_FIXED) {
+        const P32 p = view32(g, s, s.cur);
+        const float sq = (float)std::ldexp(s.q, g->F);
+        auto* r = static_cast<unsigned long long*>(rho);
+        if (D == 2) { if (O == 1) k_charge32<2, 1><<<nb, 256, 0, st>>>(g->geo, p, sq, r); else k_charge32<2, 2><<<nb, 256, 0, st>>>(g->geo, p, sq, r); }
+        else        { if (O == 1) k_charge32<3, 1><<<nb, 256, 0, st>>>(g->geo, p, sq, r); else k_charge32<3, 2><<<nb, 256, 0, st>>>(g->geo, p, sq, r); }
+    } else {
+        const P64 p = view64(g, s, s.cur);
+        auto* r = static_cast<double*>(rho);
+        if (D == 2) { if (O == 1) k_charge64<2, 1><<<nb, 256, 0, st>>>(g->geo, p, s.q, r); else k_charge64<2, 2><<<nb, 256, 0, st>>>(g->geo, p, s.q, r); }
+        else        { if (O == 1) k_charge64<3, 1><<<nb, 256, 0, st>>>(g->geo, p, s.q, r); else k_charge64<3, 2><<<nb, 256, 0, st>>>(g->geo, p, s.q, r); }
+    }
+    LPIC_LAUNCHED("k_charge");
+    return LPIC_OK;
+}
+
+lpic_status lpic_positions_at_step(lpic_grid_t g, int sid, double* out, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (!out) return fail(LPIC_EINVAL, "out is NULL");
+    Species& s = g->sp[sid];
+    const int nb = grid_blocks(s.cap, g->nsm, 16);
+    if (g->d.precision == LPIC_FP32_FIXED) {
+        const P32 p = view32(g, s, s.cur);
+        if (g->d.dim == 3) k_positions32<3><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
+        else               k_positions32<2><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
+    } else {
+        const P64 p = view64(g, s, s.cur);
+        if (g->d.dim == 3) k_positions64<3><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
+        else               k_positions64<2><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
+    }
+    LPIC_LAUNCHED("k_positions");
+    return LPIC_OK;
+}
+
+lpic_status lpic_diagnostics(lpic_grid_t g, lpic_diag* out, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (!out) return fail(LPIC_EINVAL, "out is NULL");
+    LPIC_CUDA(cudaMemsetAsync(g->d_acc, 0, 64, st));
+    LPIC_CUDA(cudaMemsetAsync(g->d_cnt, 0, 8, st));
+    for (auto& s : g->sp) {
+        const int nb = grid_blocks(s.cap, g->nsm, 8);
+        if (g->d.precision == LPIC_FP32_FIXED)
+            k_diag_p32<<<nb, 256, 0, st>>>(view32(g, s, s.cur), s.q, s.m, g->d_acc, g->d_cnt);
+        else
+            k_diag_p64<<<nb, 256, 0, st>>>(view64(g, s, s.cur), s.q, s.m, g->d_acc, g->d_cnt);
+        LPIC_LAUNCHED("k_diag_p");
+    }
+    const double dV = g->d.dx * g->d.dy * (g->d.dim == 3 ? g->d.dz : 1.0);
+    const int nb = grid_blocks(g->nfield, g->nsm, 8);
+    if (g->d.precision == LPIC_FP32_FIXED)
+        k_diag_field<float><<<nb, 256, 0, st>>>(ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), g->nfield, dV, g->d_acc);
+    else
+        k_diag_field<double><<<nb, 256, 0, st>>>(ptr3<const double>(g->d.E), ptr3<const double>(g->d.B), g->nfield, dV, g->d_acc);
+    LPIC_LAUNCHED("k_diag_field");
+    double acc[3];
+    unsigned long long cnt = 0;
+    LPIC_CUDA(cudaMemcpyAsync(acc, g->d_acc, sizeof acc, cudaMemcpyDeviceToHost, st));
+    LPIC_CUDA(cudaMemcpyAsync(&cnt, g->d_cnt, 8, cudaMemcpyDeviceToHost, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    out->kinetic = acc[0];
+    out->charge = acc[1];
+    out->field = acc[2];
+    out->particles = (long long)cnt;
+    return LPIC_OK;
+}
+
+lpic_status lpic_check_status(lpic_grid_t g, cudaStream_t st, unsigned* bits) {
+    if (lpic_status r = check_grid(g)) return r;
+    unsigned b = 0;
+    LPIC_CUDA(cudaMemcpyAsync(&b, g->d_status, 4, cudaMemcpyDeviceToHost, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    LPIC_CUDA(cudaMemsetAsync(g->d_status, 0, 4, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    if (bits) *bits = b;
+    if (b) return fail(LPIC_EDEVICE, "device status bits 0x%x", b);
+    return LPIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// lpic_common.cuh -- device helpers shared by the liblpic kernels:
+// index wrapping, particle shapes (Sec. 3.1), the relativistic Boris push
+// (Sec. 3.1), the incoming laser (Sec. 4.2) and the status word.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "lpic.h"
+
+namespace lpic {
+
+// ------------------------------------------------------------ geometry
+struct Geo {
+    int dim, nx, ny, nz, fx;      // cells; stored x extent of field arrays
+    int absorb;                    // absorbing x edges
+    double dx, dy, dz, dt;
+};
+
+// Wrap an index that is off by less than one period.
+__host__ __device__ inline int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// Wrap any index into [0, n).
+__host__ __device__ inline int wrapm(int i, int n) { i %= n; return i < 0 ? i + n : i; }
+
+// Linear field index of node (i, j, k); periodic dimensions wrap, an
+// absorbing x index outside [0, fx) yields -1.
+__device__ inline long long fidx(const Geo& g, int i, int j, int k) {
+    if (g.absorb) {
+        if (i < 0 || i >= g.fx) return -1;
+    } else {
+        i = wrapm(i, g.nx);
+    }
+    j = wrapm(j, g.ny);
+    k = (g.dim == 3) ? wrapm(k, g.nz) : 0;
+    return ((long long)k * g.ny + j) * g.fx + i;
+}
+
+template <typename T> struct Ptr3 { T* p[3]; };
+
+__device__ inline void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
+
+// ------------------------------------------------------------ shapes (Sec. 3.1)
+// Weights of a particle on the integer nodes of one dimension, from its cell
+// lc and in-cell offset f in [0, 1).  Order 1 (cloud-in-cell): nodes lc, lc+1.
+// Order 2 (quadratic spline): the three nodes around the nearest one.  The
+// arithmetic uses explicitly rounded intrinsics (no contraction), so the same
+// (cell, offset) pair always gives bit-identical weights -- the fixed-point
+// deposit relies on this to chain charge exactly from one step to the next.
+template <int ORDER> struct NodeW;
+
+template <> struct NodeW<1> {
+    int base; float w[2];
+    __device__ inline NodeW(int lc, float f) {
+        base = lc; w[0] = __fsub_rn(1.0f, f); w[1] = f;
+    }
+};
+
+template <> struct NodeW<2> {
+    int base; float w[3];
+    __device__ inline NodeW(int lc, float f) {
+        float d;
+        if (f < 0.5f) { base = lc - 1; d = f; }
+        else          { base = lc;     d = __fsub_rn(f, 1.0f); }   // exact for f in [0.5, 1)
+        const float a = __fsub_rn(0.5f, d), b = __fadd_rn(0.5f, d);
+        w[0] = __fmul_rn(0.5f, __fmul_rn(a, a));
+        w[1] = __fsub_rn(0.75f, __fmul_rn(d, d));
+        w[2] = __fmul_rn(0.5f, __fmul_rn(b, b));
+    }
+};
+
+// Weights on the half-integer nodes (index i stands for position i + 1/2).
+template <int ORDER> struct HalfW;
+
+template <> struct HalfW<1> {
+    int base; float w[2];
+    __device__ inline HalfW(int lc, float f) {
+        float t;
+        if (f >= 0.5f) { base = lc; t = f - 0.5f; } else { base = lc - 1; t = f + 0.5f; }
+        w[0] = 1.0f - t; w[1] = t;
+    }
+};
+
+template <> struct HalfW<2> {
+    int base; float w[3];
+    __device__ inline HalfW(int lc, float f) {
+        const float d = f - 0.5f;           // distance to half node lc (position lc + 1/2)
+        base = lc - 1;
+        const float a = 0.5f - d, b = 0.5f + d;
+        w[0] = 0.5f * a * a; w[1] = 0.75f - d * d; w[2] = 0.5f * b * b;
+    }
+};
+
+// Double-precision weights at an arbitrary coordinate xi (cell units).
+template <int ORDER> struct NodeWd;
+template <> struct NodeWd<1> {
+    int base; double w[2];
+    __device__ inline NodeWd(double xi) {
+        const double fl = floor(xi); base = (int)fl; const double f = xi - fl;
+        w[0] = 1.0 - f; w[1] = f;
+    }
+};
+template <> struct NodeWd<2> {
+    int base; double w[3];
+    __device__ inline NodeWd(double xi) {
+        const double n = floor(xi + 0.5); const double d = xi - n; base = (int)n - 1;
+        const double a = 0.5 - d, b = 0.5 + d;
+        w[0] = 0.5 * a * a; w[1] = 0.75 - d * d; w[2] = 0.5 * b * b;
+    }
+};
+
+// ------------------------------------------------------------ Boris (Sec. 3.1)
+// u = gamma v (c = 1); k = q dt / (2 m).  Half electric kick, rotation about
+// B with gamma taken after the first kick, half electric kick.
+template <typename R>
+__device__ inline void boris(R& ux, R& uy, R& uz, R k, R ex, R ey, R ez, R bx, R by, R bz) {
+    const R mx = ux + k * ex, my = uy + k * ey, mz = uz + k * ez;
+    const R g = sqrt(R(1) + mx * mx + my * my + mz * mz);
+    const R tx = k * bx / g, ty = k * by / g, tz = k * bz / g;
+    const R t2 = tx * tx + ty * ty + tz * tz;
+    const R f = R(2) / (R(1) + t2);
+    const R sx = f * tx, sy = f * ty, sz = f * tz;
+    const R px = mx + (my * tz - mz * ty);
+    const R py = my + (mz * tx - mx * tz);
+    const R pz = mz + (mx * ty - my * tx);
+    ux = mx + (py * sz - pz * sy) + k * ex;
+    uy = my + (pz * sx - px * sz) + k * ey;
+    uz = mz + (px * sy - py * sx) + k * ez;
+}
+
+// ------------------------------------------------------------ laser (Sec. 4.2)
+struct Laser {
+    int on; double a0, w0, tau, omega, yc, zc;
+};
+
+__device__ inline double laser_ey(const Laser& L, int dim, double x, double y, double z, double t) {
+    const double s = t - x;
+    if (!L.on || s <= 0.0 || s >= L.tau) return 0.0;
+    double env = sin(3.14159265358979323846 * s / L.tau);
+    env *= env;
+    double r2 = (y - L.yc) * (y - L.yc);
+    if (dim == 3) r2 += (z - L.zc) * (z - L.zc);
+    return L.a0 * env * exp(-r2 / (L.w0 * L.w0)) * sin(L.omega * s);
+}
+
+}  // namespace lpic

@@ -1,0 +1,134 @@
+// lpic_field.cuh -- Yee FDTD half-step kernels (Sec. 3.2 Eq. 1-4, split in
+// two dt/2 halves as in Algorithm 1) with periodic or absorbing x edges.
+//
+// E and B are updated in place, one thread per grid node, all three
+// components: the E update reads only B (and J), the B update only E, so no
+// thread reads a value another thread of the same launch writes.
+// Absorbing x edges: E_y and E_z on the edge planes i = 0 and i = nx follow
+// the first-order Mur condition for an outgoing wave (Mur 1981), written with
+// tau = dt/2 for each half-step; at x-min the incoming laser is added to the
+// wave that the condition lets through.
+#pragma once
+#include "lpic_common.cuh"
+
+namespace lpic {
+
+template <typename R, typename JT>
+struct FieldArgs {
+    R* E[3];
+    R* B[3];
+    const JT* J[3];
+    R rdx, rdy, rdz;      // 1 / h
+    R tau;                // dt / 2
+    double jfac[3];       // tau * (J units -> field units)
+};
+
+template <int DIM, typename R, typename JT>
+__global__ void k_update_E(Geo g, FieldArgs<R, JT> a) {
+    const long long total = (long long)g.fx * g.ny * (DIM == 3 ? g.nz : 1);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % g.fx);
+        const long long r = n / g.fx;
+        const int j = (int)(r % g.ny);
+        const int k = (int)(r / g.ny);
+        const long long nj = (j == 0) ? n + (long long)(g.ny - 1) * g.fx : n - g.fx;
+        long long nk = n;
+        if (DIM == 3) nk = (k == 0) ? n + (long long)(g.nz - 1) * g.ny * g.fx : n - (long long)g.ny * g.fx;
+        long long ni;
+        bool edge = false;
+        if (g.absorb) { ni = n - 1; edge = (i == 0 || i == g.nx); }
+        else          { ni = (i == 0) ? n + (g.nx - 1) : n - 1; }
+        // E_x at (i+1/2, j, k)
+        if (!(g.absorb && i == g.nx)) {
+            R cb = (a.B[2][n] - a.B[2][nj]) * a.rdy;
+            if (DIM == 3) cb -= (a.B[1][n] - a.B[1][nk]) * a.rdz;
+            a.E[0][n] += a.tau * cb - (R)((double)a.J[0][n] * a.jfac[0]);
+        }
+        if (!edge) {
+            // E_y at (i, j+1/2, k)
+            R cb = -(a.B[2][n] - a.B[2][ni]) * a.rdx;
+            if (DIM == 3) cb += (a.B[0][n] - a.B[0][nk]) * a.rdz;
+            a.E[1][n] += a.tau * cb - (R)((double)a.J[1][n] * a.jfac[1]);
+            // E_z at (i, j, k+1/2)
+            const R cz = (a.B[1][n] - a.B[1][ni]) * a.rdx - (a.B[0][n] - a.B[0][nj]) * a.rdy;
+            a.E[2][n] += a.tau * cz - (R)((double)a.J[2][n] * a.jfac[2]);
+        }
+    }
+}
+
+template <int DIM, typename R, typename JT>
+__global__ void k_update_B(Geo g, FieldArgs<R, JT> a) {
+    const long long total = (long long)g.fx * g.ny * (DIM == 3 ? g.nz : 1);
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(n % g.fx);
+        const long long r = n / g.fx;
+        const int j = (int)(r % g.ny);
+        const int k = (int)(r / g.ny);
+        const long long nj = (j == g.ny - 1) ? n - (long long)(g.ny - 1) * g.fx : n + g.fx;
+        long long nk = n;
+        if (DIM == 3)
+            nk = (k == g.nz - 1) ? n - (long long)(g.nz - 1) * g.ny * g.fx : n + (long long)g.ny * g.fx;
+        const bool last = g.absorb && i == g.nx;
+        const long long ni = (!g.absorb && i == g.nx - 1) ? n - (g.nx - 1) : n + 1;
+        // B_x at (i, j+1/2, k+1/2)
+        {
+            R ce = (a.E[2][nj] - a.E[2][n]) * a.rdy;
+            if (DIM == 3) ce -= (a.E[1][nk] - a.E[1][n]) * a.rdz;
+            a.B[0][n] -= a.tau * ce;
+        }
+        if (!last) {
+            // B_y at (i+1/2, j, k+1/2)
+            R ce = -(a.E[2][ni] - a.E[2][n]) * a.rdx;
+            if (DIM == 3) ce += (a.E[0][nk] - a.E[0][n]) * a.rdz;
+            a.B[1][n] -= a.tau * ce;
+            // B_z at (i+1/2, j+1/2, k)
+            const R cz = (a.E[1][ni] - a.E[1][n]) * a.rdx - (a.E[0][nj] - a.E[0][n]) * a.rdy;
+            a.B[2][n] -= a.tau * cz;
+        }
+    }
+}
+
+// Save E_y, E_z on planes i = 0, 1, nx-1, nx before the E update:
+// old[((c - 1) * 4 + p) * plane + q], q = k * ny + j.
+template <typename R>
+__global__ void k_mur_save(Geo g, Ptr3<R> E, R* old) {
+    const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
+    const int planes[4] = {0, 1, g.nx - 1, g.nx};
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * 4 * plane; t += gridDim.x * blockDim.x) {
+        const int q = t % plane;
+        const int p = (t / plane) % 4;
+        const int c = 1 + t / (4 * plane);
+        old[t] = E.p[c][(long long)q * g.fx + planes[p]];
+    }
+}
+
+template <typename R>
+__global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, double t_old, double tau) {
+    const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
+    const double c1 = (tau - g.dx) / (tau + g.dx);
+    const double t_new = t_old + tau;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * plane; t += gridDim.x * blockDim.x) {
+        const int q = t % plane;
+        const int c = 1 + t / plane;
+        const R* o = old + (c - 1) * 4 * plane;
+        const long long row = (long long)q * g.fx;
+        double i0o = 0, i1o = 0, i0n = 0, i1n = 0;
+        if (L.on && c == 1) {
+            const int j = q % g.ny, k = q / g.ny;
+            const double y = (j + 0.5) * g.dy, z = k * g.dz;
+            i0o = laser_ey(L, g.dim, 0.0, y, z, t_old);
+            i1o = laser_ey(L, g.dim, g.dx, y, z, t_old);
+            i0n = laser_ey(L, g.dim, 0.0, y, z, t_new);
+            i1n = laser_ey(L, g.dim, g.dx, y, z, t_new);
+        }
+        const double e1n = (double)E.p[c][row + 1];
+        E.p[c][row] = (R)(i0n + ((double)o[1 * plane + q] - i1o)
+                        + c1 * ((e1n - i1n) - ((double)o[0 * plane + q] - i0o)));
+        const double eMn = (double)E.p[c][row + g.nx - 1];
+        E.p[c][row + g.nx] = (R)((double)o[2 * plane + q] + c1 * (eMn - (double)o[3 * plane + q]));
+    }
+}
+
+}  // namespace lpic

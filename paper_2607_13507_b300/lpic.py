@@ -1,0 +1,325 @@
+"""Thin ctypes binding of liblpic (include/lpic.h).
+
+Argument marshalling only: PyTorch provides device memory and streams, every
+step of the PIC path runs in the CUDA kernels of ``csrc/``.  There is no CPU
+fallback: importing this module on a machine without the built library, or
+using it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "liblpic.so")
+
+FP64, FP32_FIXED = 0, 1
+ST_CFL, ST_HALO, ST_NAN, ST_OUTSIDE, ST_OVERFLOW, ST_TIMEOUT = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+
+STATUS = {0: "LPIC_OK", 1: "LPIC_EINVAL", 2: "LPIC_ENOMEM", 3: "LPIC_ECUDA", 4: "LPIC_EDEVICE",
+          5: "LPIC_EUNSUPPORTED"}
+
+EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_add_species",
+           "lpic_species_query", "lpic_sort_particles", "lpic_zero_current",
+           "lpic_gather_push_deposit", "lpic_maxwell_half_step", "lpic_step",
+           "lpic_deposit_charge", "lpic_positions_at_step", "lpic_diagnostics",
+           "lpic_grid_get_info", "lpic_check_status", "lpic_last_error"]
+
+
+class LpicError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class LaserDesc(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("a0", "w0", "tau", "omega", "yc", "zc")]
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("nz", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+                ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("absorb_x", ctypes.c_int),
+                ("shape_order", ctypes.c_int), ("precision", ctypes.c_int),
+                ("tile", ctypes.c_int * 3), ("E", ctypes.c_void_p * 3), ("B", ctypes.c_void_p * 3),
+                ("J", ctypes.c_void_p * 3), ("laser", ctypes.POINTER(LaserDesc))]
+
+
+class SpeciesDesc(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("count", ctypes.c_longlong),
+                ("capacity", ctypes.c_longlong), ("buffers", ctypes.c_void_p * 2),
+                ("staggered", ctypes.c_int)]
+
+
+class GridInfo(ctypes.Structure):
+    _fields_ = [("fixed_shift", ctypes.c_int), ("j_scale", ctypes.c_double * 3),
+                ("rho_scale", ctypes.c_double), ("tile", ctypes.c_int * 3),
+                ("ntiles", ctypes.c_longlong), ("fx", ctypes.c_int), ("launches", ctypes.c_longlong)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("kinetic", ctypes.c_double), ("field", ctypes.c_double),
+                ("charge", ctypes.c_double), ("particles", ctypes.c_longlong)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load liblpic.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"liblpic not built at {path}; run `python -m paper_2607_13507_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p
+    lib.lpic_species_bytes.restype = ctypes.c_size_t
+    lib.lpic_species_bytes.argtypes = [i, i, ctypes.c_longlong]
+    lib.lpic_create_grid.argtypes = [ctypes.POINTER(GridDesc), ctypes.POINTER(vp)]
+    lib.lpic_destroy_grid.argtypes = [vp]
+    lib.lpic_add_species.argtypes = [vp, ctypes.POINTER(SpeciesDesc), st, ctypes.POINTER(i)]
+    lib.lpic_species_query.argtypes = [vp, i, st, ctypes.POINTER(i), ctypes.POINTER(ctypes.c_longlong)]
+    lib.lpic_sort_particles.argtypes = [vp, i, st]
+    lib.lpic_zero_current.argtypes = [vp, st]
+    lib.lpic_gather_push_deposit.argtypes = [vp, i, st]
+    lib.lpic_maxwell_half_step.argtypes = [vp, i, ctypes.c_double, st]
+    lib.lpic_step.argtypes = [vp, ctypes.c_double, st]
+    lib.lpic_deposit_charge.argtypes = [vp, i, vp, st]
+    lib.lpic_positions_at_step.argtypes = [vp, i, vp, st]
+    lib.lpic_diagnostics.argtypes = [vp, ctypes.POINTER(Diag), st]
+    lib.lpic_grid_get_info.argtypes = [vp, ctypes.POINTER(GridInfo)]
+    lib.lpic_check_status.argtypes = [vp, st, ctypes.POINTER(ctypes.c_uint)]
+    lib.lpic_last_error.restype = ctypes.c_char_p
+    lib.lpic_last_error.argtypes = []
+    for name in EXPORTS:
+        if name != "lpic_species_bytes" and name != "lpic_last_error":
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise LpicError(rc, load().lpic_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def species_bytes(dim, precision, capacity) -> int:
+    return int(load().lpic_species_bytes(dim, precision, capacity))
+
+
+def _cap(n: int) -> int:
+    return max(64, (n + 63) // 64 * 64)
+
+
+class Species:
+    """Device buffers of one species (ping/pong, struct of arrays)."""
+
+    def __init__(self, grid: "Grid", q, m, capacity):
+        self.grid, self.q, self.m, self.cap = grid, float(q), float(m), int(capacity)
+        nbytes = species_bytes(grid.dim, grid.precision, self.cap)
+        self.buffers = [torch.empty(nbytes // 8 + 64, dtype=torch.int64, device=grid.device)
+                        for _ in range(2)]
+        self.id = -1
+
+    def ptr(self, b) -> int:
+        p = self.buffers[b].data_ptr()
+        return (p + 255) // 256 * 256
+
+    def _views(self, b):
+        """Typed views (cell, off, u, w, id) or (x, u, w, id) of buffer b."""
+        g, cap = self.grid, self.cap
+        raw = self.buffers[b].view(torch.uint8)
+        base = self.ptr(b) - self.buffers[b].data_ptr()
+        if g.precision == FP32_FIXED:
+            a = 4 * cap
+            seg = lambda k, dt: raw[base + k * a: base + (k + 1) * a].view(dt)
+            return dict(cell=seg(0, torch.int32),
+                        off=[seg(1 + d, torch.float32) for d in range(g.dim)],
+                        u=[seg(1 + g.dim + c, torch.float32) for c in range(3)],
+                        w=seg(4 + g.dim, torch.float32), id=seg(5 + g.dim, torch.int32))
+        a = 8 * cap
+        seg = lambda k, dt, sz=a: raw[base + k * a: base + k * a + sz].view(dt)
+        return dict(x=[seg(d, torch.float64) for d in range(g.dim)],
+                    u=[seg(g.dim + c, torch.float64) for c in range(3)],
+                    w=seg(g.dim + 3, torch.float64), id=seg(g.dim + 4, torch.int32, 4 * cap))
+
+    def upload(self, p, staggered=False, stream=None):
+        """Copy a workloads.Particles initial state into buffer 0 and register
+        the species with the grid."""
+        g = self.grid
+        n = p.n
+        assert n <= self.cap
+        v = self._views(0)
+        dev = g.device
+        if g.precision == FP32_FIXED:
+            nx, ny = g.n[0], g.n[1]
+            cell = p.cell[0] + nx * (p.cell[1] + (ny * p.cell[2] if g.dim == 3 else 0))
+            v["cell"].fill_(-1)
+            v["cell"][:n] = torch.from_numpy(cell.astype(np.int32)).to(dev)
+            for d in range(g.dim):
+                v["off"][d][:n] = torch.from_numpy(p.off[d].astype(np.float32)).to(dev)
+            for c in range(3):
+                v["u"][c][:n] = torch.from_numpy(p.u[c].astype(np.float32)).to(dev)
+            v["w"][:n] = torch.from_numpy(p.w.astype(np.float32)).to(dev)
+        else:
+            for d in range(g.dim):
+                v["x"][d][:n] = torch.from_numpy((p.cell[d] + p.off[d]) * g.h[d]).to(dev)
+            for c in range(3):
+                v["u"][c][:n] = torch.from_numpy(p.u[c]).to(dev)
+            v["w"].zero_()
+            v["w"][:n] = torch.from_numpy(p.w).to(dev)
+        v["id"][:n] = torch.from_numpy(p.id).to(dev)
+        desc = SpeciesDesc(self.q, self.m, n, self.cap, (ctypes.c_void_p * 2)(self.ptr(0), self.ptr(1)),
+                           int(staggered))
+        sid = ctypes.c_int(-1)
+        _check(load().lpic_add_species(g.h_, ctypes.byref(desc), _stream(stream), ctypes.byref(sid)))
+        self.id = sid.value
+        return self
+
+    def query(self, stream=None):
+        cur, cnt = ctypes.c_int(), ctypes.c_longlong()
+        _check(load().lpic_species_query(self.grid.h_, self.id, _stream(stream), ctypes.byref(cur),
+                                         ctypes.byref(cnt)))
+        return cur.value, cnt.value
+
+    def state(self, stream=None):
+        """Host copy of the current buffer's alive particles as numpy arrays."""
+        cur, cnt = self.query(stream)
+        v = self._views(cur)
+        out = {}
+        for k, val in v.items():
+            if isinstance(val, list):
+                out[k] = np.stack([t[:cnt].cpu().numpy() for t in val])
+            else:
+                out[k] = val[:cnt].cpu().numpy()
+        return out
+
+    def positions_at_step(self, stream=None) -> np.ndarray:
+        """x^n (physical, not wrapped) of the current buffer's first count entries."""
+        cur, cnt = self.query(stream)
+        out = torch.empty(3 * self.cap, dtype=torch.float64, device=self.grid.device)
+        _check(load().lpic_positions_at_step(self.grid.h_, self.id, out.data_ptr(), _stream(stream)))
+        o = out.view(3, self.cap)[: self.grid.dim, :cnt].cpu().numpy()
+        return o
+
+    def charge(self, stream=None) -> torch.Tensor:
+        """Charge density of the stored positions: float64 (FP64 path) or the
+        int64 fixed-point integer charge (FP32 path)."""
+        g = self.grid
+        dt = torch.float64 if g.precision == FP64 else torch.int64
+        rho = torch.zeros(g.field_shape, dtype=dt, device=g.device)
+        _check(load().lpic_deposit_charge(g.h_, self.id, rho.data_ptr(), _stream(stream)))
+        return rho
+
+
+class Grid:
+    """A grid with caller-owned (torch) field arrays and its species."""
+
+    def __init__(self, dim, n, h, dt, order, precision, absorb_x=False, laser=None, tile=None,
+                 device="cuda"):
+        load()
+        self.dim, self.precision, self.order = dim, precision, order
+        self.n = tuple(int(v) for v in n) + ((1,) if dim == 2 else ())
+        self.h = tuple(float(v) for v in h) + ((1.0,) if dim == 2 else ())
+        self.dt, self.absorb_x = float(dt), bool(absorb_x)
+        self.device = torch.device(device)
+        fx = self.n[0] + 1 if absorb_x else self.n[0]
+        nz = self.n[2] if dim == 3 else 1
+        self.field_shape = (nz, self.n[1], fx)
+        ft = torch.float64 if precision == FP64 else torch.float32
+        jt = torch.float64 if precision == FP64 else torch.int64
+        self.E = [torch.zeros(self.field_shape, dtype=ft, device=self.device) for _ in range(3)]
+        self.B = [torch.zeros(self.field_shape, dtype=ft, device=self.device) for _ in range(3)]
+        self.J = [torch.zeros(self.field_shape, dtype=jt, device=self.device) for _ in range(3)]
+        t = tile or (0, 0, 0)
+        self._laser = None
+        if laser is not None:
+            self._laser = LaserDesc(laser.a0, laser.w0, laser.tau, laser.omega, laser.yc, laser.zc)
+        desc = GridDesc(dim, self.n[0], self.n[1], nz, self.h[0], self.h[1], self.h[2], self.dt,
+                        int(absorb_x), order, precision, (ctypes.c_int * 3)(*t),
+                        (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.E]),
+                        (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.B]),
+                        (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.J]),
+                        ctypes.pointer(self._laser) if self._laser is not None else None)
+        h = ctypes.c_void_p()
+        _check(load().lpic_create_grid(ctypes.byref(desc), ctypes.byref(h)))
+        self.h_ = h
+        self.species: list[Species] = []
+
+    def close(self):
+        if getattr(self, "h_", None):
+            load().lpic_destroy_grid(self.h_)
+            self.h_ = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_species(self, p, capacity=None, staggered=False, stream=None) -> Species:
+        sp = Species(self, p.q, p.m, capacity or _cap(p.n))
+        sp.upload(p, staggered, stream)
+        self.species.append(sp)
+        return sp
+
+    def info(self) -> GridInfo:
+        out = GridInfo()
+        _check(load().lpic_grid_get_info(self.h_, ctypes.byref(out)))
+        return out
+
+    # -- the path
+    def maxwell_half(self, half, t=0.0, stream=None):
+        _check(load().lpic_maxwell_half_step(self.h_, half, t, _stream(stream)))
+
+    def zero_current(self, stream=None):
+        _check(load().lpic_zero_current(self.h_, _stream(stream)))
+
+    def sort(self, sid=-1, stream=None):
+        _check(load().lpic_sort_particles(self.h_, sid, _stream(stream)))
+
+    def gather_push_deposit(self, sid, stream=None):
+        _check(load().lpic_gather_push_deposit(self.h_, sid, _stream(stream)))
+
+    def step(self, t, stream=None):
+        _check(load().lpic_step(self.h_, t, _stream(stream)))
+
+    def diagnostics(self, stream=None) -> Diag:
+        out = Diag()
+        _check(load().lpic_diagnostics(self.h_, ctypes.byref(out), _stream(stream)))
+        return out
+
+    def check_status(self, stream=None) -> int:
+        bits = ctypes.c_uint()
+        rc = load().lpic_check_status(self.h_, _stream(stream), ctypes.byref(bits))
+        if rc not in (0, 4):
+            _check(rc)
+        return bits.value
+
+    def current(self) -> list:
+        """J as float64 in field units (FP32 path: J_int * j_scale)."""
+        if self.precision == FP64:
+            return [j.clone() for j in self.J]
+        inf = self.info()
+        return [self.J[c].to(torch.float64) * inf.j_scale[c] for c in range(3)]
+
+
+def grid_for(wl, precision=None, tile=None, device="cuda") -> Grid:
+    """A Grid for a workloads.Workload (laser centred transversally)."""
+    from . import workloads as W
+    prec = precision if precision is not None else (FP64 if wl.precision == "fp64" else FP32_FIXED)
+    laser = None
+    if wl.laser is not None:
+        c = wl.laser_center()
+        laser = W.LaserSpec(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega)
+        laser.yc, laser.zc = c[0], (c[1] if wl.dim == 3 else 0.0)
+    return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device)

@@ -1,0 +1,235 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+FP64 path: element-wise relative L2 <= 1e-11 on fields and on particles
+matched by id after 20 steps (chaotic growth of rounding differences stays
+far below that over 20 steps).  FP32 path: tolerances derived from float32
+rounding (unit roundoff 2^-24 = 6e-8): a particle's state carries O(10)
+roundings per step, so positions agree to ~1e-6 cell and momenta to ~1e-6
+relative per step; the deposited current to ~1e-6 relative; the bound used
+is 2e-5 per step on fields, 1e-5 per step on momenta.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_13507_b300 import workloads as W
+
+from pic_cases import gpu_case, match_particles, oracle_case, rel_l2, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_13507_b300 import build, lpic
+    build.build()
+    lpic.load()
+
+
+def _fp64_parity(wl, steps, tol):
+    from paper_2607_13507_b300 import lpic
+    parts = W.load_all(wl)
+    g, sps = oracle_case(wl, parts)
+    G = gpu_case(wl, parts, lpic.FP64)
+    run_oracle(g, sps, steps)
+    run_gpu(G, steps)
+    assert G.check_status() == 0
+    for c in range(3):
+        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < tol, ("E", c)
+        assert rel_l2(G.B[c].cpu().numpy(), g.B[c]) < tol, ("B", c)
+        assert rel_l2(G.J[c].cpu().numpy(), g.J[c]) < tol, ("J", c)
+    for sg, so in zip(G.species, sps):
+        xg, xo, ug, uo = match_particles(G, sg, so, wl)
+        assert rel_l2(xg, xo) < tol
+        assert rel_l2(ug, uo) < tol
+    return G, g
+
+
+def test_fp64_thermal2d_64x64_ppc16_20_steps():
+    """The small plain-FP64 thermal plasma (64 x 64, 16 per cell, CIC)."""
+    _fp64_parity(W.thermal2d(), 20, 1e-11)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_fp64_thermal3d_small(order):
+    _fp64_parity(W.thermal3d(n=12, ppc=2, order=order, precision="fp64"), 10, 1e-11)
+
+
+def test_fp64_laser2d_absorbing_small():
+    """Laser through the Mur edge onto a slab, absorbing x, TSC."""
+    wl = W.laser2d(nx=128, ny=64, ppc=2, precision="fp64")
+    _fp64_parity(wl, 80, 1e-10)
+
+
+def _fp32_case(wl, steps, tile=None):
+    from paper_2607_13507_b300 import lpic
+    parts = W.load_all(wl)
+    g, sps = oracle_case(wl, parts)
+    G = gpu_case(wl, parts, lpic.FP32_FIXED, tile)
+    run_oracle(g, sps, steps)
+    run_gpu(G, steps)
+    assert G.check_status() == 0
+    return G, g, sps
+
+
+@pytest.mark.parametrize("dim,order,tile", [(2, 1, None), (2, 2, None), (2, 2, (8, 4)),
+                                            (3, 1, None), (3, 2, None), (3, 2, (4, 8, 2))])
+def test_fp32_fixed_against_oracle(dim, order, tile):
+    if dim == 2:
+        wl = W.thermal2d(n=40, ppc=8, vth=0.05, order=order, precision="fp32")
+    else:
+        wl = W.thermal3d(n=12, ppc=4, vth=0.05, order=order, precision="fp32")
+    steps = 5
+    G, g, sps = _fp32_case(wl, steps, tile)
+    Jg = G.current()
+    for c in range(3):
+        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < 2e-5 * steps, ("E", c)
+        assert rel_l2(Jg[c].cpu().numpy(), g.J[c]) < 2e-5, ("J", c)
+        if np.linalg.norm(g.B[c]) > 0:
+            assert rel_l2(G.B[c].cpu().numpy(), g.B[c]) < 2e-5 * steps, ("B", c)
+    xg, xo, ug, uo = match_particles(G, G.species[0], sps[0], wl)
+    for d in range(wl.dim):
+        assert np.max(np.abs(xg[d] - xo[d])) / wl.h[d] < 1e-5
+    assert rel_l2(ug, uo) < 1e-5 * steps
+
+
+def test_fp32_laser2d_small_against_oracle():
+    wl = W.laser2d(nx=128, ny=64, ppc=2, precision="fp32")
+    steps = 80
+    G, g, sps = _fp32_case(wl, steps)
+    for c in range(3):
+        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < 1e-4, ("E", c)
+        assert rel_l2(G.B[c].cpu().numpy(), g.B[c]) < 1e-4, ("B", c)
+
+
+def _div_int(G):
+    """Integer divergence of the fixed-point current on the integer nodes:
+    sum_d J_d(i+1/2) - J_d(i-1/2) (periodic)."""
+    J = G.J
+    d = (J[0] - torch.roll(J[0], 1, 2)) + (J[1] - torch.roll(J[1], 1, 1))
+    if G.dim == 3:
+        d = d + (J[2] - torch.roll(J[2], 1, 0))
+    return d
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_fp32_exact_integer_continuity_over_steps(dim, order):
+    """rho_int(after) - rho_int(before) + div J_int = 0 exactly, every step,
+    and summed over many steps (the end of one path is bit-identical to the
+    start of the next)."""
+    from paper_2607_13507_b300 import lpic
+    if dim == 2:
+        wl = W.thermal2d(n=48, ppc=6, vth=0.2, order=order, precision="fp32")
+    else:
+        wl = W.thermal3d(n=16, ppc=3, vth=0.2, order=order, precision="fp32")
+    G = gpu_case(wl, W.load_all(wl), lpic.FP32_FIXED)
+    sp = G.species[0]
+    rho0 = sp.charge()
+    prev = rho0.clone()
+    total_div = torch.zeros_like(rho0)
+    for s in range(12):
+        G.step(s * G.dt)
+        rho = sp.charge()
+        dv = _div_int(G)
+        assert torch.equal(rho - prev + dv, torch.zeros_like(dv)), s
+        total_div += dv
+        prev = rho
+    assert torch.equal(prev - rho0 + total_div, torch.zeros_like(rho0))
+    assert G.check_status() == 0
+
+
+def test_fp32_deposit_is_deterministic_under_permutation():
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d(n=32, ppc=8, vth=0.1, order=2, precision="fp32")
+    parts = W.load_all(wl)
+    G1 = gpu_case(wl, parts, lpic.FP32_FIXED)
+    p = parts[0]
+    perm = np.random.Generator(np.random.Philox(3)).permutation(p.n)
+    q = W.Particles(p.q, p.m, p.cell[:, perm], p.off[:, perm], p.u[:, perm], p.w[perm], p.id[perm])
+    G2 = gpu_case(wl, [q], lpic.FP32_FIXED)
+    for s in range(3):
+        G1.step(s * G1.dt)
+        G2.step(s * G2.dt)
+        torch.cuda.synchronize()
+        for c in range(3):
+            assert torch.equal(G1.J[c], G2.J[c])
+            assert torch.equal(G1.E[c], G2.E[c])
+
+
+def test_sort_groups_by_tile_and_keeps_every_particle():
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d(n=40, ppc=5, vth=0.1, order=1, precision="fp32")
+    G = gpu_case(wl, W.load_all(wl), lpic.FP32_FIXED, tile=(8, 8))
+    sp = G.species[0]
+    before = sp.state()
+    G.sort()
+    after = sp.state()
+    assert sorted(after["id"].tolist()) == sorted(before["id"].tolist())
+    cell = after["cell"]
+    cx, cy = cell % 40, cell // 40
+    key = (cy // 8) * 5 + cx // 8
+    assert np.all(np.diff(key) >= 0)
+    # per-id state is carried unchanged
+    o = np.argsort(before["id"])
+    a = np.argsort(after["id"])
+    assert np.array_equal(before["cell"][o], after["cell"][a])
+    assert np.array_equal(before["u"][:, o], after["u"][:, a])
+
+
+def test_absorbing_edge_removes_particles_and_sort_compacts():
+    from paper_2607_13507_b300 import lpic
+    wl = W.laser2d(nx=64, ny=16, ppc=2, precision="fp32")
+    # a drifting slab that reaches the x-max edge
+    parts = W.load_all(wl)
+    for p in parts:
+        p.u[0] = np.float32(0.9 * 20.0)
+    G = gpu_case(wl, parts, lpic.FP32_FIXED)
+    n0 = sum(p.n for p in parts)
+    for s in range(60):
+        G.step(s * G.dt)
+    torch.cuda.synchronize()
+    left = sum(sp.query()[1] for sp in G.species)
+    assert 0 < left < n0
+    G.sort()
+    for sp in G.species:
+        st = sp.state()
+        assert np.all(st["cell"] >= 0)
+        cx = st["cell"] % 64
+        assert np.all((cx >= 2) & (cx < 62))
+    assert G.check_status() == 0
+
+
+def test_nonfinite_momentum_sets_status_and_removes_particle():
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d(n=16, ppc=1, vth=0.01, order=1, precision="fp32")
+    parts = W.load_all(wl)
+    parts[0].u[0, 3] = np.inf
+    G = gpu_case(wl, parts, lpic.FP32_FIXED)
+    G.step(0.0)
+    bits = G.check_status()
+    assert bits & lpic.ST_NAN
+    assert G.check_status() == 0          # cleared
+    G.sort()
+    assert G.species[0].query()[1] == parts[0].n - 1
+
+
+def test_diagnostics_match_oracle_energy():
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d(n=32, ppc=4, vth=0.05, order=1, precision="fp64")
+    parts = W.load_all(wl)
+    g, sps = oracle_case(wl, parts)
+    G = gpu_case(wl, parts, lpic.FP64)
+    run_oracle(g, sps, 5)
+    run_gpu(G, 5)
+    d = G.diagnostics()
+    ek, ef, qt = O.energy(g, sps)
+    assert abs(d.kinetic - ek) < 1e-11 * ek
+    assert abs(d.field - ef) < 1e-9 * ef
+    assert abs(d.charge - qt) < 1e-12 * abs(qt)
+    assert d.particles == parts[0].n
