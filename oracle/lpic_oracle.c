@@ -24,8 +24,9 @@
  *   - normalised units c = eps0 = 1;
  *   - absorbing x edges: first-order Mur condition on the tangential E at the
  *     edge nodes, applied in each half-step with tau = dt/2, with an incoming
- *     Gaussian/sin^2 laser in E_y at x-min; particles whose new position lies
- *     outside [2 dx, (nx-2) dx) deposit their last step and are removed.
+ *     Gaussian/sin^2 laser in E_y at x-min; particles whose deposit end point
+ *     x^{n+1/2} + dt v^{n+1} lies outside [2 dx, (nx-2) dx) deposit their
+ *     last step and are removed.
  *
  * Layout (shared with nothing, stated here for the Python wrapper): every
  * field array is [nz][ny][fx] row-major, fx = nx for periodic x and nx+1 for
@@ -505,7 +506,8 @@ void orc_maxwell_half(orc_grid *g, int which, double t)
  * x^{n+1/2} to x^{n+1/2} + dt v^{n+1} (whose end point is where the next
  * step's first half push will put the particle).  2D3V J_z uses v_z^{n+1}.
  * Periodic coordinates of x^{n+1} are wrapped; with absorbing x a particle
- * whose x^{n+1} leaves [2 dx, (nx-2) dx) is removed after its deposit. */
+ * whose deposit end point leaves [2 dx, (nx-2) dx) is removed after its
+ * deposit. */
 int orc_push_species(orc_grid *g, orc_species *sp)
 {
     const double dt = g->dt;
@@ -530,7 +532,7 @@ int orc_push_species(orc_grid *g, orc_species *sp)
             if (x1[d] >= L[d]) x1[d] -= L[d];
             else if (x1[d] < 0.0) x1[d] += L[d];
         }
-        if (g->absorb_x && (x1[0] < 2.0 * g->dx || x1[0] >= (g->nx - 2) * g->dx)) sp->alive[p] = 0;
+        if (g->absorb_x && (xe[0] < 2.0 * g->dx || xe[0] >= (g->nx - 2) * g->dx)) sp->alive[p] = 0;
         for (int d = 0; d < g->dim; ++d) sp->x[d][p] = x1[d];
         for (int c = 0; c < 3; ++c) sp->u[c][p] = u[c];
     }
