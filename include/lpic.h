@@ -101,6 +101,9 @@ typedef struct {
     int shape_order;            /* 1: cloud-in-cell, 2: quadratic spline (TSC) */
     int precision;              /* LPIC_FP64 or LPIC_FP32_FIXED */
     int tile[3];                /* cells per tile for the FP32 path; 0 = default */
+    int block_particles;        /* FP32 path: at most this many particles per thread block
+                                   (a crowded tile is split into several work items);
+                                   0 = default (4096), else in [256, 2^20] */
     void *E[3], *B[3], *J[3];   /* caller-owned device field arrays (see layout) */
     const lpic_laser_desc *laser; /* NULL: no laser; copied at create (needs absorb_x) */
 } lpic_grid_desc;
@@ -186,6 +189,18 @@ lpic_status lpic_maxwell_half_step(lpic_grid_t grid, int half, double t, cudaStr
 /* One full step t -> t + dt (Algorithm 1): Maxwell half 0, zero J, per
  * species sort (FP32 path) and gather_push_deposit, Maxwell half 1. */
 lpic_status lpic_step(lpic_grid_t grid, double t, cudaStream_t stream);
+
+/* Set the device clock that captured steps read the laser time from. */
+lpic_status lpic_set_clock(lpic_grid_t grid, double t, cudaStream_t stream);
+
+/* Run nsteps full steps (as lpic_step) by replaying CUDA graphs: the first
+ * call for a given buffer parity captures one step on `stream` (thread-local
+ * capture) and instantiates it; later calls only launch.  The laser time is
+ * the device clock (lpic_set_clock), which each replay advances by dt.  A
+ * graph holds the species buffer pointers of its parity, so adding species or
+ * changing buffers after the first capture is not supported.  `stream` must
+ * be a created stream (the legacy default stream cannot be captured). */
+lpic_status lpic_graph_steps(lpic_grid_t grid, int nsteps, cudaStream_t stream);
 
 /* Charge density of the stored positions x^{n+1/2} (the charge the deposit
  * conserves, Sec. 3.1), added into rho[nz][ny][fx]: FP64 path double

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -56,6 +57,10 @@ struct Species {
     int* d_count = nullptr;      // ntiles + 1
     int* d_start = nullptr;      // ntiles + 2
     int* d_cursor = nullptr;     // ntiles + 1
+    int* d_coff = nullptr;       // ntiles + 1 work-item offsets
+    int2* d_items = nullptr;     // work items (tile, chunk)
+    int* d_nitems = nullptr;
+    long long item_cap = 0;
     double wmax = 0;
     bool sorted = false;         // sorted since the last push (FP32 path needs it)
 };
@@ -80,6 +85,13 @@ struct lpic_grid {
     int nsm = 148;
     size_t smem32 = 0;
     long long launches = 0;
+    int P = 4096;                              // particles per work item (FP32 path)
+    CellDecode dec{};
+    FastDiv fT[3]{};
+    double* d_clock = nullptr;                 // device time for graph replays
+    std::map<unsigned, cudaGraphExec_t> graphs;  // captured steps keyed by buffer parity
+    std::map<unsigned, long long> graph_launches;
+    bool attrs_set = false;
 };
 
 namespace {
@@ -149,13 +161,15 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st) {
     Tiles t{};
     for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; }
     t.start = s.d_start;
+    t.items = s.d_items;
+    t.nitems = s.d_nitems;
+    t.P = g->P;
     auto kern = k_gpd32<DIM, ORDER>;
-    LPIC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem32));
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
-    kern<<<(unsigned)g->ntiles, 256, g->smem32, st>>>(
+    kern<<<(unsigned)s.item_cap, 256, g->smem32, st>>>(
         g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
-        p, t, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
+        p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
         (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status);
     LPIC_LAUNCHED("k_gpd32");
     return LPIC_OK;
@@ -171,8 +185,15 @@ lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
     return LPIC_OK;
 }
 
+template <int DIM, int ORDER>
+cudaError_t set_smem_attrs(size_t bytes) {
+    return cudaFuncSetAttribute(k_gpd32<DIM, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)bytes);
+}
+
+// clock != nullptr: the laser time is read from the device clock plus t.
 template <int DIM, typename R, typename JT>
-lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st) {
+lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st, const double* clock) {
     FieldArgs<R, JT> a{};
     for (int c = 0; c < 3; ++c) {
         a.E[c] = static_cast<R*>(g->d.E[c]);
@@ -198,7 +219,7 @@ lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st) {
         LPIC_LAUNCHED("k_update_E");
         if (g->geo.absorb) {
             k_mur_apply<R><<<grid_blocks(2LL * plane, g->nsm), 256, 0, st>>>(
-                g->geo, Ep, static_cast<const R*>(g->d_mur), g->laser, t, tau);
+                g->geo, Ep, static_cast<const R*>(g->d_mur), g->laser, t, clock, tau);
             LPIC_LAUNCHED("k_mur_apply");
         }
         return LPIC_OK;
@@ -228,11 +249,13 @@ lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st) {
     const int dim = g->d.dim;
     if (g->d.precision == LPIC_FP32_FIXED) {
         const P32 src = view32(g, s, s.cur), dst = view32(g, s, other);
-        KeyFP32 key{src.cell, g->d.nx, g->d.ny, g->T[0], g->T[1], g->T[2], g->nt[0], g->nt[1], nt, dim};
+        KeyFP32 key{src.cell, g->dec, g->fT[0], g->fT[1], g->fT[2], g->nt[0], g->nt[1], nt};
         k_sort_count<<<nb, 256, 0, st>>>(key, s.d_n, s.d_count);
         LPIC_LAUNCHED("k_sort_count");
-        k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt + 1);
+        k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt, g->P, s.d_coff);
         LPIC_LAUNCHED("k_sort_scan");
+        k_sort_items<<<grid_blocks(nt, g->nsm), 256, 0, st>>>(s.d_count, s.d_coff, nt, g->P, s.d_items, s.d_nitems);
+        LPIC_LAUNCHED("k_sort_items");
         k_sort_scatter<<<nb, 256, 0, st>>>(key, MoveFP32{src, dst, dim}, s.d_n, s.d_start, s.d_cursor, nt);
         LPIC_LAUNCHED("k_sort_scatter");
     } else {
@@ -242,7 +265,7 @@ lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st) {
                     g->T[2], g->nt[0], g->nt[1], nt, dim};
         k_sort_count<<<nb, 256, 0, st>>>(key, s.d_n, s.d_count);
         LPIC_LAUNCHED("k_sort_count");
-        k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt + 1);
+        k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt, g->P, s.d_coff);
         LPIC_LAUNCHED("k_sort_scan");
         k_sort_scatter<<<nb, 256, 0, st>>>(key, MoveFP64{src, dst, dim}, s.d_n, s.d_start, s.d_cursor, nt);
         LPIC_LAUNCHED("k_sort_scatter");
@@ -274,7 +297,7 @@ void recompute_shift(lpic_grid* g) {
     }
     if (mx <= 0.0) { g->F = 0; }
     else {
-        const int f1 = (int)std::floor(29.0 - std::log2(mx));
+        const int f1 = (int)std::floor(22.0 - std::log2(mx));
         const int f2 = (int)std::floor(61.0 - std::log2(total));
         g->F = std::min(f1, f2);
     }
@@ -326,6 +349,8 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     if (d.absorb_x != 0 && d.absorb_x != 1) return fail(LPIC_EINVAL, "absorb_x must be 0 or 1");
     if (d.absorb_x && d.nx < 8) return fail(LPIC_EINVAL, "absorbing x needs nx >= 8");
     if (d.laser && !d.absorb_x) return fail(LPIC_EINVAL, "a laser needs absorbing x edges");
+    if (d.block_particles != 0 && (d.block_particles < 256 || d.block_particles > (1 << 20)))
+        return fail(LPIC_EINVAL, "block_particles must be 0 or in [256, 2^20]");
     for (int c = 0; c < 3; ++c)
         if (!d.E[c] || !d.B[c] || !d.J[c]) return fail(LPIC_EINVAL, "field pointer %d is NULL", c);
     auto* g = new (std::nothrow) lpic_grid;
@@ -355,11 +380,14 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         g->ntiles *= g->nt[k];
     }
     if (d.dim == 2) { g->T[2] = 1; g->nt[2] = 1; }
+    for (int k = 0; k < 3; ++k) g->fT[k] = make_fastdiv((unsigned)g->T[k]);
+    g->dec = CellDecode{make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny)};
+    if (d.block_particles > 0) g->P = d.block_particles;
     {
         const int D = d.dim;
         long long G = 1, H = 1;
         for (int k = 0; k < D; ++k) { G *= g->T[k] + 4; H *= g->T[k] + 5; }
-        g->smem32 = (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 8;
+        g->smem32 = (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 12;
         if (d.precision == LPIC_FP32_FIXED && g->smem32 > 227 * 1024) {
             delete g;
             return fail(LPIC_EINVAL, "tile needs %zu bytes of shared memory (> 227 KB)", g->smem32);
@@ -372,13 +400,22 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     const size_t fbytes = d.precision == LPIC_FP64 ? 8 : 4;
     const int plane = d.ny * nz;
     if (cudaMalloc(&g->d_status, 64) != cudaSuccess ||
+        cudaMalloc(&g->d_clock, 64) != cudaSuccess ||
         cudaMalloc(&g->d_acc, 64) != cudaSuccess ||
         cudaMalloc(&g->d_cnt, 64) != cudaSuccess ||
         (d.absorb_x && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess)) {
         lpic_destroy_grid(g);
         return fail(LPIC_ENOMEM, "scratch allocation failed");
     }
-    if (cudaMemset(g->d_status, 0, 64) != cudaSuccess) { lpic_destroy_grid(g); return fail(LPIC_ECUDA, "memset failed"); }
+    if (cudaMemset(g->d_status, 0, 64) != cudaSuccess || cudaMemset(g->d_clock, 0, 64) != cudaSuccess) {
+        lpic_destroy_grid(g);
+        return fail(LPIC_ECUDA, "memset failed");
+    }
+    if (d.precision == LPIC_FP32_FIXED) {
+        cudaError_t e = d.dim == 2 ? (d.shape_order == 1 ? set_smem_attrs<2, 1>(g->smem32) : set_smem_attrs<2, 2>(g->smem32))
+                                   : (d.shape_order == 1 ? set_smem_attrs<3, 1>(g->smem32) : set_smem_attrs<3, 2>(g->smem32));
+        if (e != cudaSuccess) { lpic_destroy_grid(g); return fail(LPIC_ECUDA, "shared memory attribute: %s", cudaGetErrorString(e)); }
+    }
     recompute_shift(g);
     *out = g;
     return LPIC_OK;
@@ -389,8 +426,11 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     cudaDeviceSynchronize();
     for (auto& s : g->sp) {
         cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
+        cudaFree(s.d_coff); cudaFree(s.d_items); cudaFree(s.d_nitems);
     }
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
     cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur);
+    cudaFree(g->d_clock);
     delete g;
     return LPIC_OK;
 }
@@ -424,11 +464,16 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
     s.q = d.q; s.m = d.m; s.cap = d.capacity;
     s.buf[0] = d.buffers[0]; s.buf[1] = d.buffers[1];
     const int nt = (int)g->ntiles;
+    s.item_cap = nt + (d.capacity + g->P - 1) / g->P + 1;
     if (cudaMalloc(&s.d_n, sizeof(int) * 4) != cudaSuccess ||
         cudaMalloc(&s.d_count, sizeof(int) * (nt + 1)) != cudaSuccess ||
         cudaMalloc(&s.d_start, sizeof(int) * (nt + 2)) != cudaSuccess ||
-        cudaMalloc(&s.d_cursor, sizeof(int) * (nt + 1)) != cudaSuccess) {
+        cudaMalloc(&s.d_cursor, sizeof(int) * (nt + 1)) != cudaSuccess ||
+        cudaMalloc(&s.d_coff, sizeof(int) * (nt + 1)) != cudaSuccess ||
+        cudaMalloc(&s.d_items, sizeof(int2) * s.item_cap) != cudaSuccess ||
+        cudaMalloc(&s.d_nitems, sizeof(int) * 4) != cudaSuccess) {
         cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
+        cudaFree(s.d_coff); cudaFree(s.d_items); cudaFree(s.d_nitems);
         return fail(LPIC_ENOMEM, "species scratch allocation failed");
     }
     const int n = (int)d.count;
@@ -465,8 +510,8 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
             const P32 p = view32(g, s, 0);
             const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
                         c = (float)(g->d.dt / g->d.dz);
-            if (g->d.dim == 3) k_advance32<3><<<nb, 256, 0, st>>>(g->geo, p, 0.5f, a, b, c);
-            else               k_advance32<2><<<nb, 256, 0, st>>>(g->geo, p, 0.5f, a, b, c);
+            if (g->d.dim == 3) k_advance32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+            else               k_advance32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
         } else {
             const P64 p = view64(g, s, 0);
             if (g->d.dim == 3) k_advance64<3><<<nb, 256, 0, st>>>(g->geo, p, 0.5);
@@ -526,26 +571,90 @@ lpic_status lpic_gather_push_deposit(lpic_grid_t g, int sid, cudaStream_t st) {
     return r;
 }
 
+static lpic_status maxwell_any(lpic_grid_t g, int half, double t, cudaStream_t st, const double* clock) {
+    if (g->d.precision == LPIC_FP32_FIXED)
+        return g->d.dim == 3 ? maxwell_impl<3, float, long long>(g, half, t, st, clock)
+                             : maxwell_impl<2, float, long long>(g, half, t, st, clock);
+    return g->d.dim == 3 ? maxwell_impl<3, double, double>(g, half, t, st, clock)
+                         : maxwell_impl<2, double, double>(g, half, t, st, clock);
+}
+
 lpic_status lpic_maxwell_half_step(lpic_grid_t g, int half, double t, cudaStream_t st) {
     if (lpic_status r = check_grid(g)) return r;
     if (half != 0 && half != 1) return fail(LPIC_EINVAL, "half must be 0 or 1");
-    if (g->d.precision == LPIC_FP32_FIXED)
-        return g->d.dim == 3 ? maxwell_impl<3, float, long long>(g, half, t, st)
-                             : maxwell_impl<2, float, long long>(g, half, t, st);
-    return g->d.dim == 3 ? maxwell_impl<3, double, double>(g, half, t, st)
-                         : maxwell_impl<2, double, double>(g, half, t, st);
+    return maxwell_any(g, half, t, st, nullptr);
 }
 
-lpic_status lpic_step(lpic_grid_t g, double t, cudaStream_t st) {
-    if (lpic_status r = check_grid(g)) return r;
-    if (lpic_status r = lpic_maxwell_half_step(g, 0, t, st)) return r;
+// One step; with a device clock the laser time is *clock (+ dt/2 in the
+// second half) and the clock advances by dt at the end.
+static lpic_status step_impl(lpic_grid_t g, double t, cudaStream_t st, double* clock) {
+    if (lpic_status r = maxwell_any(g, 0, clock ? 0.0 : t, st, clock)) return r;
     if (lpic_status r = lpic_zero_current(g, st)) return r;
     for (int s = 0; s < (int)g->sp.size(); ++s) {
         if (g->d.precision == LPIC_FP32_FIXED)
             if (lpic_status r = sort_one(g, g->sp[s], st)) return r;
         if (lpic_status r = lpic_gather_push_deposit(g, s, st)) return r;
     }
-    return lpic_maxwell_half_step(g, 1, t + 0.5 * g->d.dt, st);
+    if (lpic_status r = maxwell_any(g, 1, (clock ? 0.0 : t) + 0.5 * g->d.dt, st, clock)) return r;
+    if (clock) {
+        k_clock_add<<<1, 32, 0, st>>>(clock, g->d.dt);
+        LPIC_LAUNCHED("k_clock_add");
+    }
+    return LPIC_OK;
+}
+
+lpic_status lpic_step(lpic_grid_t g, double t, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    return step_impl(g, t, st, nullptr);
+}
+
+lpic_status lpic_set_clock(lpic_grid_t g, double t, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    k_clock_set<<<1, 32, 0, st>>>(g->d_clock, t);
+    LPIC_LAUNCHED("k_clock_set");
+    return LPIC_OK;
+}
+
+lpic_status lpic_graph_steps(lpic_grid_t g, int nsteps, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (nsteps < 0) return fail(LPIC_EINVAL, "nsteps must be >= 0");
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+        return fail(LPIC_EINVAL, "graph capture needs a created (non-default) stream");
+    for (int k = 0; k < nsteps; ++k) {
+        unsigned key = 0;
+        for (size_t s = 0; s < g->sp.size(); ++s) key |= (unsigned)g->sp[s].cur << s;
+        auto it = g->graphs.find(key);
+        if (it == g->graphs.end()) {
+            // capture one step starting from this buffer parity
+            std::vector<int> cur0;
+            std::vector<bool> sorted0;
+            for (auto& s : g->sp) { cur0.push_back(s.cur); sorted0.push_back(s.sorted); }
+            const long long l0 = g->launches;
+            LPIC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            lpic_status r = step_impl(g, 0.0, st, g->d_clock);
+            cudaGraph_t graph = nullptr;
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
+            for (size_t s = 0; s < g->sp.size(); ++s) { g->sp[s].cur = cur0[s]; g->sp[s].sorted = sorted0[s]; }
+            const long long per_step = g->launches - l0;
+            g->launches = l0;
+            if (r != LPIC_OK) { if (graph) cudaGraphDestroy(graph); return r; }
+            if (e != cudaSuccess) return fail(LPIC_ECUDA, "stream capture: %s", cudaGetErrorString(e));
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail(LPIC_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+            g->graphs[key] = exec;
+            g->graph_launches[key] = per_step;
+            it = g->graphs.find(key);
+        }
+        LPIC_CUDA(cudaGraphLaunch(it->second, st));
+        g->launches += g->graph_launches[key];
+        // the replayed step flipped every sorted species' buffers
+        if (g->d.precision == LPIC_FP32_FIXED)
+            for (auto& s : g->sp) { s.cur = 1 - s.cur; s.sorted = false; }
+        g->started = true;
+    }
+    return LPIC_OK;
 }
 
 lpic_status lpic_deposit_charge(lpic_grid_t g, int sid, void* rho, cudaStream_t st) {
@@ -558,8 +667,8 @@ lpic_status lpic_deposit_charge(lpic_grid_t g, int sid, void* rho, cudaStream_t 
         const P32 p = view32(g, s, s.cur);
         const float sq = (float)std::ldexp(s.q, g->F);
         auto* r = static_cast<unsigned long long*>(rho);
-        if (D == 2) { if (O == 1) k_charge32<2, 1><<<nb, 256, 0, st>>>(g->geo, p, sq, r); else k_charge32<2, 2><<<nb, 256, 0, st>>>(g->geo, p, sq, r); }
-        else        { if (O == 1) k_charge32<3, 1><<<nb, 256, 0, st>>>(g->geo, p, sq, r); else k_charge32<3, 2><<<nb, 256, 0, st>>>(g->geo, p, sq, r); }
+        if (D == 2) { if (O == 1) k_charge32<2, 1><<<nb, 256, 0, st>>>(g->geo, p, g->dec, sq, r); else k_charge32<2, 2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, sq, r); }
+        else        { if (O == 1) k_charge32<3, 1><<<nb, 256, 0, st>>>(g->geo, p, g->dec, sq, r); else k_charge32<3, 2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, sq, r); }
     } else {
         const P64 p = view64(g, s, s.cur);
         auto* r = static_cast<double*>(rho);
@@ -577,8 +686,8 @@ lpic_status lpic_positions_at_step(lpic_grid_t g, int sid, double* out, cudaStre
     const int nb = grid_blocks(s.cap, g->nsm, 16);
     if (g->d.precision == LPIC_FP32_FIXED) {
         const P32 p = view32(g, s, s.cur);
-        if (g->d.dim == 3) k_positions32<3><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
-        else               k_positions32<2><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
+        if (g->d.dim == 3) k_positions32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, out, s.cap);
+        else               k_positions32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, out, s.cap);
     } else {
         const P64 p = view64(g, s, s.cur);
         if (g->d.dim == 3) k_positions64<3><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);

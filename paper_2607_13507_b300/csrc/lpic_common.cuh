@@ -35,6 +35,39 @@ __device__ inline long long fidx(const Geo& g, int i, int j, int k) {
 
 template <typename T> struct Ptr3 { T* p[3]; };
 
+// Division by a runtime constant d >= 1 with a multiply-high (Granlund and
+// Montgomery 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d) + 1,
+// n / d = (umulhi(n, m) + n) >> l for 0 <= n < 2^31.
+struct FastDiv { unsigned d, m, l; };
+
+inline FastDiv make_fastdiv(unsigned d) {
+    unsigned l = 0;
+    while ((1ull << l) < d) ++l;
+    const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+    return FastDiv{d, (unsigned)m, l};
+}
+
+__device__ inline int fdiv(int n, const FastDiv& f) {
+    return (int)((__umulhi((unsigned)n, f.m) + (unsigned)n) >> f.l);
+}
+
+// Cell coordinates of a linear cell index (k * ny + j) * nx + i.
+struct CellDecode {
+    FastDiv nx, ny;
+    __device__ inline void operator()(int cell, int* gc) const {
+        const int r = fdiv(cell, nx);
+        gc[0] = cell - r * (int)nx.d;
+        gc[2] = fdiv(r, ny);
+        gc[1] = r - gc[2] * (int)ny.d;
+    }
+};
+
+// Round to the nearest integer (ties to even) for |x| < 2^22: adding
+// 1.5 * 2^23 leaves the rounded value in the low mantissa bits.
+__device__ inline int rint22(float x) {
+    return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
+}
+
 __device__ inline void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
 
 // ------------------------------------------------------------ shapes (Sec. 3.1)

@@ -93,7 +93,7 @@ __global__ void k_charge64(Geo g, P64 p, double q, double* rho) {
 
 // x^n = x^{n+1/2} - (dt/2) v^n, as physical doubles out[d * cap + i].
 template <int DIM>
-__global__ void k_positions32(Geo g, P32 p, double* out, long long cap) {
+__global__ void k_positions32(Geo g, P32 p, CellDecode dec, double* out, long long cap) {
     const int n = *p.n;
     const double h[3] = {g.dx, g.dy, g.dz};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)cap; i += gridDim.x * blockDim.x) {
@@ -104,10 +104,7 @@ __global__ void k_positions32(Geo g, P32 p, double* out, long long cap) {
             continue;
         }
         int gc[3];
-        gc[0] = cell % g.nx;
-        const int rr = cell / g.nx;
-        gc[1] = rr % g.ny;
-        gc[2] = (DIM == 3) ? rr / g.ny : 0;
+        dec(cell, gc);
         const double ux = p.u[0][i], uy = p.u[1][i], uz = p.u[2][i];
         const double gm = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
         const double u[3] = {ux, uy, uz};

@@ -104,10 +104,13 @@ __global__ void k_mur_save(Geo g, Ptr3<R> E, R* old) {
     }
 }
 
+// t_old = *clock + t_arg when a device clock is given (graph replay), else t_arg.
 template <typename R>
-__global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, double t_old, double tau) {
+__global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, double t_arg,
+                            const double* clock, double tau) {
     const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
     const double c1 = (tau - g.dx) / (tau + g.dx);
+    const double t_old = clock ? *clock + t_arg : t_arg;
     const double t_new = t_old + tau;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * plane; t += gridDim.x * blockDim.x) {
         const int q = t % plane;
@@ -129,6 +132,15 @@ __global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, double t_ol
         const double eMn = (double)E.p[c][row + g.nx - 1];
         E.p[c][row + g.nx] = (R)((double)o[2 * plane + q] + c1 * (eMn - (double)o[3 * plane + q]));
     }
+}
+
+// Device clock of the captured step: advanced by dt at the end of each replay.
+__global__ void k_clock_add(double* clock, double dt) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *clock += dt;
+}
+
+__global__ void k_clock_set(double* clock, double t) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *clock = t;
 }
 
 }  // namespace lpic

@@ -16,12 +16,15 @@ namespace lpic {
 
 struct KeyFP32 {
     const int* cell;
-    int nx, ny, T0, T1, T2, nt0, nt1, ntiles, dim;
+    CellDecode dec;
+    FastDiv T0, T1, T2;
+    int nt0, nt1, ntiles;
     __device__ inline int operator()(int i) const {
         const int c = cell[i];
         if (c < 0) return ntiles;
-        const int x = c % nx, r = c / nx, y = r % ny, z = (dim == 3) ? r / ny : 0;
-        return ((z / T2) * nt1 + y / T1) * nt0 + x / T0;
+        int gc[3];
+        dec(c, gc);
+        return (fdiv(gc[2], T2) * nt1 + fdiv(gc[1], T1)) * nt0 + fdiv(gc[0], T0);
     }
 };
 
@@ -57,15 +60,16 @@ __global__ void k_sort_count(Key key, const int* n_ptr, int* count) {
     }
 }
 
-// Exclusive scan of count[0..len) into start[0..len], start[len] = total.
-__global__ void k_sort_scan(const int* count, int* start, int len) {
+// Exclusive block-wide scan of f(0..len) into out[0..len], out[len] = total.
+template <class F>
+__device__ inline void block_scan(F f, int* out, int len) {
     __shared__ int warp_sums[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int base = 0; base < len; base += blockDim.x) {
         const int i = base + threadIdx.x;
-        const int v = (i < len) ? count[i] : 0;
+        const int v = (i < len) ? f(i) : 0;
         int x = v;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -86,12 +90,32 @@ __global__ void k_sort_scan(const int* count, int* start, int len) {
         }
         __syncthreads();
         const int wpre = (threadIdx.x >= 32) ? warp_sums[(threadIdx.x >> 5) - 1] : 0;
-        if (i < len) start[i] = carry + wpre + x - v;
+        if (i < len) out[i] = carry + wpre + x - v;
         __syncthreads();
         if (threadIdx.x == blockDim.x - 1) carry += wpre + x;
         __syncthreads();
     }
-    if (threadIdx.x == 0) start[len] = carry;
+    if (threadIdx.x == 0) out[len] = carry;
+    __syncthreads();
+}
+
+// start = exclusive scan of the ntiles + 1 key counts (the last key holds
+// removed particles); coff = exclusive scan of the work-item counts
+// ceil(count / P) of the ntiles tiles, coff[ntiles] = number of items.
+static __global__ void k_sort_scan(const int* count, int* start, int ntiles, int P, int* coff) {
+    block_scan([count](int i) { return count[i]; }, start, ntiles + 1);
+    block_scan([count, P](int i) { return (count[i] + P - 1) / P; }, coff, ntiles);
+}
+
+// Work items (tile, chunk), tile-major.
+static __global__ void k_sort_items(const int* count, const int* coff, int ntiles, int P, int2* items,
+                             int* nitems) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        const int nch = (count[t] + P - 1) / P;
+        const int o = coff[t];
+        for (int c = 0; c < nch; ++c) items[o + c] = make_int2(t, c);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *nitems = coff[ntiles];
 }
 
 struct MoveFP32 {
@@ -143,7 +167,7 @@ __global__ void k_sort_scatter(Key key, Move mv, const int* n_ptr, const int* st
     }
 }
 
-__global__ void k_sort_finalize(const int* start, int ntiles, int* n_out) {
+static __global__ void k_sort_finalize(const int* start, int ntiles, int* n_out) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *n_out = start[ntiles];
 }
 

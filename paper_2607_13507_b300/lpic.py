@@ -26,7 +26,8 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_species_query", "lpic_sort_particles", "lpic_zero_current",
            "lpic_gather_push_deposit", "lpic_maxwell_half_step", "lpic_step",
            "lpic_deposit_charge", "lpic_positions_at_step", "lpic_diagnostics",
-           "lpic_grid_get_info", "lpic_check_status", "lpic_last_error"]
+           "lpic_grid_get_info", "lpic_check_status", "lpic_last_error", "lpic_set_clock",
+           "lpic_graph_steps"]
 
 
 class LpicError(RuntimeError):
@@ -44,7 +45,8 @@ class GridDesc(ctypes.Structure):
                 ("nz", ctypes.c_int), ("dx", ctypes.c_double), ("dy", ctypes.c_double),
                 ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("absorb_x", ctypes.c_int),
                 ("shape_order", ctypes.c_int), ("precision", ctypes.c_int),
-                ("tile", ctypes.c_int * 3), ("E", ctypes.c_void_p * 3), ("B", ctypes.c_void_p * 3),
+                ("tile", ctypes.c_int * 3), ("block_particles", ctypes.c_int),
+                ("E", ctypes.c_void_p * 3), ("B", ctypes.c_void_p * 3),
                 ("J", ctypes.c_void_p * 3), ("laser", ctypes.POINTER(LaserDesc))]
 
 
@@ -88,6 +90,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_gather_push_deposit.argtypes = [vp, i, st]
     lib.lpic_maxwell_half_step.argtypes = [vp, i, ctypes.c_double, st]
     lib.lpic_step.argtypes = [vp, ctypes.c_double, st]
+    lib.lpic_set_clock.argtypes = [vp, ctypes.c_double, st]
+    lib.lpic_graph_steps.argtypes = [vp, i, st]
     lib.lpic_deposit_charge.argtypes = [vp, i, vp, st]
     lib.lpic_positions_at_step.argtypes = [vp, i, vp, st]
     lib.lpic_diagnostics.argtypes = [vp, ctypes.POINTER(Diag), st]
@@ -172,11 +176,12 @@ class Species:
             v["w"][:n] = torch.from_numpy(p.w.astype(np.float32)).to(dev)
         else:
             for d in range(g.dim):
-                v["x"][d][:n] = torch.from_numpy((p.cell[d] + p.off[d]) * g.h[d]).to(dev)
+                v["x"][d][:n] = torch.from_numpy(
+                    (p.cell[d].astype(np.float64) + p.off[d].astype(np.float64)) * g.h[d]).to(dev)
             for c in range(3):
-                v["u"][c][:n] = torch.from_numpy(p.u[c]).to(dev)
+                v["u"][c][:n] = torch.from_numpy(p.u[c].astype(np.float64)).to(dev)
             v["w"].zero_()
-            v["w"][:n] = torch.from_numpy(p.w).to(dev)
+            v["w"][:n] = torch.from_numpy(p.w.astype(np.float64)).to(dev)
         v["id"][:n] = torch.from_numpy(p.id).to(dev)
         desc = SpeciesDesc(self.q, self.m, n, self.cap, (ctypes.c_void_p * 2)(self.ptr(0), self.ptr(1)),
                            int(staggered))
@@ -225,7 +230,7 @@ class Grid:
     """A grid with caller-owned (torch) field arrays and its species."""
 
     def __init__(self, dim, n, h, dt, order, precision, absorb_x=False, laser=None, tile=None,
-                 device="cuda"):
+                 device="cuda", block_particles=0):
         load()
         self.dim, self.precision, self.order = dim, precision, order
         self.n = tuple(int(v) for v in n) + ((1,) if dim == 2 else ())
@@ -245,7 +250,7 @@ class Grid:
         if laser is not None:
             self._laser = LaserDesc(laser.a0, laser.w0, laser.tau, laser.omega, laser.yc, laser.zc)
         desc = GridDesc(dim, self.n[0], self.n[1], nz, self.h[0], self.h[1], self.h[2], self.dt,
-                        int(absorb_x), order, precision, (ctypes.c_int * 3)(*t),
+                        int(absorb_x), order, precision, (ctypes.c_int * 3)(*t), int(block_particles),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.E]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.B]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.J]),
@@ -293,6 +298,13 @@ class Grid:
     def step(self, t, stream=None):
         _check(load().lpic_step(self.h_, t, _stream(stream)))
 
+    def set_clock(self, t, stream=None):
+        _check(load().lpic_set_clock(self.h_, t, _stream(stream)))
+
+    def graph_steps(self, nsteps, stream=None):
+        """nsteps full steps replayed from captured CUDA graphs (device clock)."""
+        _check(load().lpic_graph_steps(self.h_, nsteps, _stream(stream)))
+
     def diagnostics(self, stream=None) -> Diag:
         out = Diag()
         _check(load().lpic_diagnostics(self.h_, ctypes.byref(out), _stream(stream)))
@@ -313,7 +325,7 @@ class Grid:
         return [self.J[c].to(torch.float64) * inf.j_scale[c] for c in range(3)]
 
 
-def grid_for(wl, precision=None, tile=None, device="cuda") -> Grid:
+def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0) -> Grid:
     """A Grid for a workloads.Workload (laser centred transversally)."""
     from . import workloads as W
     prec = precision if precision is not None else (FP64 if wl.precision == "fp64" else FP32_FIXED)
@@ -322,4 +334,5 @@ def grid_for(wl, precision=None, tile=None, device="cuda") -> Grid:
         c = wl.laser_center()
         laser = W.LaserSpec(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega)
         laser.yc, laser.zc = c[0], (c[1] if wl.dim == 3 else 0.0)
-    return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device)
+    return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device,
+                block_particles)

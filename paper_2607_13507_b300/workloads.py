@@ -29,20 +29,20 @@ def generator(seed: int) -> np.random.Generator:
 
 
 def _f32_unit(a: np.ndarray) -> np.ndarray:
-    """Round to float32 and keep the value inside [0, 1)."""
-    a = a.astype(np.float32)
-    a = np.minimum(a, np.nextafter(np.float32(1.0), np.float32(0.0)))
-    a = np.maximum(a, np.float32(0.0))
-    return a.astype(np.float64)
+    """float32 values inside [0, 1)."""
+    a = a.astype(np.float32, copy=False)
+    np.minimum(a, np.nextafter(np.float32(1.0), np.float32(0.0)), out=a)
+    np.maximum(a, np.float32(0.0), out=a)
+    return a
 
 
 @dataclass
 class Particles:
     """Initial state of one species.
 
-    cell: (dim, n) int64 cell coordinates; off: (dim, n) in-cell offsets in
-    [0, 1) (cell units); u: (3, n) momenta u = gamma v; w: (n,) weights;
-    id: (n,) int32 particle ids (0..n-1).
+    cell: (dim, n) int32 cell coordinates; off: (dim, n) float32 in-cell
+    offsets in [0, 1) (cell units); u: (3, n) float32 momenta u = gamma v;
+    w: (n,) float32 weights; id: (n,) int32 particle ids (0..n-1).
     """
     q: float
     m: float
@@ -145,16 +145,19 @@ def load_species(wl: Workload, sid: int, previous: list | None = None,
     ncell = dens.shape[0]
     ppc = spec.ppc
     n = ncell * ppc
-    cell = np.stack([np.repeat(c, ppc) for c in cc]) if dim else np.zeros((0, n), np.int64)
     if spec.same_positions_as >= 0 and previous is not None:
         src = previous[spec.same_positions_as]
         assert src.n == n
         cell = src.cell.copy()
         off = src.off.copy()
     else:
-        off = _f32_unit(g.random((dim, n)))
-    u = (g.standard_normal((3, n)) * spec.vth).astype(np.float32).astype(np.float64)
-    w = (np.repeat(dens, ppc) * wl.dV / ppc).astype(np.float32).astype(np.float64)
+        cell = np.empty((dim, n), dtype=np.int32)
+        for d in range(dim):
+            cell[d] = np.repeat(cc[d].astype(np.int32), ppc)
+        off = _f32_unit(g.random((dim, n), dtype=np.float32))
+    u = g.standard_normal((3, n), dtype=np.float32)
+    u *= np.float32(spec.vth)
+    w = (np.repeat(dens, ppc) * wl.dV / ppc).astype(np.float32)
     ids = np.arange(n, dtype=np.int32)
     return Particles(spec.q, spec.m, cell, off, u, w, ids)
 

@@ -2,11 +2,15 @@
 
 FP64 path: element-wise relative L2 <= 1e-11 on fields and on particles
 matched by id after 20 steps (chaotic growth of rounding differences stays
-far below that over 20 steps).  FP32 path: tolerances derived from float32
-rounding (unit roundoff 2^-24 = 6e-8): a particle's state carries O(10)
-roundings per step, so positions agree to ~1e-6 cell and momenta to ~1e-6
-relative per step; the deposited current to ~1e-6 relative; the bound used
-is 2e-5 per step on fields, 1e-5 per step on momenta.
+far below that over 20 steps).  FP32 path: positions and momenta carry float32
+rounding (unit roundoff 2^-24 = 6e-8, O(10) roundings per particle per
+step): bound 1e-5 cell on positions and 1e-5 per step on momenta.  The
+current is integer in units of 2^-F of charge with every particle's charge
+S = rint(2^F |q w|) <= 2^22; the quantisation with closures leaves each
+particle-node value within a few units of the exact one, i.e. a relative
+error of ~units / (S * displacement in cells); for the thermal cases here
+(displacement ~0.03 cell) that is ~3e-5 per contribution: bounds 1e-4 (2D)
+and 3e-4 (3D) on J, and the same per step on E and B, which are driven by J.
 """
 import math
 
@@ -88,11 +92,15 @@ def test_fp32_fixed_against_oracle(dim, order, tile):
     steps = 5
     G, g, sps = _fp32_case(wl, steps, tile)
     Jg = G.current()
+    jtol = 1e-4 if dim == 2 else 3e-4
     for c in range(3):
-        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < 2e-5 * steps, ("E", c)
-        assert rel_l2(Jg[c].cpu().numpy(), g.J[c]) < 2e-5, ("J", c)
+        ej = rel_l2(Jg[c].cpu().numpy(), g.J[c])
+        ee = rel_l2(G.E[c].cpu().numpy(), g.E[c])
+        assert ej < jtol, ("J", c, ej)
+        assert ee < jtol * steps, ("E", c, ee)
         if np.linalg.norm(g.B[c]) > 0:
-            assert rel_l2(G.B[c].cpu().numpy(), g.B[c]) < 2e-5 * steps, ("B", c)
+            eb = rel_l2(G.B[c].cpu().numpy(), g.B[c])
+            assert eb < jtol * steps, ("B", c, eb)
     xg, xo, ug, uo = match_particles(G, G.species[0], sps[0], wl)
     for d in range(wl.dim):
         assert np.max(np.abs(xg[d] - xo[d])) / wl.h[d] < 1e-5
@@ -100,12 +108,17 @@ def test_fp32_fixed_against_oracle(dim, order, tile):
 
 
 def test_fp32_laser2d_small_against_oracle():
+    """80 steps: the per-step current quantisation noise (~3e-5 relative)
+    accumulates in E and B like a random walk, sqrt(80) * 3e-5 ~ 3e-4;
+    bound 1e-3."""
     wl = W.laser2d(nx=128, ny=64, ppc=2, precision="fp32")
     steps = 80
     G, g, sps = _fp32_case(wl, steps)
     for c in range(3):
-        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < 1e-4, ("E", c)
-        assert rel_l2(G.B[c].cpu().numpy(), g.B[c]) < 1e-4, ("B", c)
+        ee = rel_l2(G.E[c].cpu().numpy(), g.E[c])
+        eb = rel_l2(G.B[c].cpu().numpy(), g.B[c])
+        assert ee < 1e-3, ("E", c, ee)
+        assert eb < 1e-3, ("B", c, eb)
 
 
 def _div_int(G):
@@ -233,3 +246,48 @@ def test_diagnostics_match_oracle_energy():
     assert abs(d.field - ef) < 1e-9 * ef
     assert abs(d.charge - qt) < 1e-12 * abs(qt)
     assert d.particles == parts[0].n
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_graph_replay_matches_eager_steps(precision):
+    """Steps replayed from captured CUDA graphs give the same state as the
+    same steps issued call by call (bitwise without a laser)."""
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d(n=40, ppc=4, vth=0.1, order=2, precision=precision)
+    prec = lpic.FP32_FIXED if precision == "fp32" else lpic.FP64
+    parts = W.load_all(wl)
+    Ga = gpu_case(wl, parts, prec)
+    Gb = gpu_case(wl, parts, prec)
+    for s in range(7):
+        Ga.step(s * wl.dt)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    Gb.set_clock(0.0, side)
+    Gb.graph_steps(3, side)
+    Gb.graph_steps(4, side)
+    torch.cuda.synchronize()
+    for c in range(3):
+        assert torch.equal(Ga.E[c], Gb.E[c])
+        assert torch.equal(Ga.B[c], Gb.B[c])
+        assert torch.equal(Ga.J[c], Gb.J[c])
+    assert Ga.species[0].query()[0] == Gb.species[0].query()[0]
+    assert Gb.check_status() == 0
+    with pytest.raises(Exception):
+        Gb.graph_steps(1, torch.cuda.default_stream())
+
+
+def test_graph_replay_with_laser_clock():
+    from paper_2607_13507_b300 import lpic
+    wl = W.laser2d(nx=128, ny=32, ppc=2, precision="fp32")
+    parts = W.load_all(wl)
+    Ga = gpu_case(wl, parts, lpic.FP32_FIXED)
+    Gb = gpu_case(wl, parts, lpic.FP32_FIXED)
+    for s in range(60):
+        Ga.step(s * wl.dt)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    Gb.set_clock(0.0, side)
+    Gb.graph_steps(60, side)
+    torch.cuda.synchronize()
+    for c in range(3):
+        assert rel_l2(Gb.E[c].cpu().numpy(), Ga.E[c].cpu().numpy()) < 1e-5
