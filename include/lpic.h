@@ -223,6 +223,33 @@ lpic_status lpic_grid_get_info(lpic_grid_t grid, lpic_grid_info *out);
  * them; returns LPIC_EDEVICE when any bit was set. */
 lpic_status lpic_check_status(lpic_grid_t grid, cudaStream_t stream, unsigned *bits);
 
+/* Counting sort by cell tile of one FP32_FIXED particle buffer that allocates
+ * nothing (the paper has no counterpart; it serves callers that cannot
+ * allocate device memory: a host framework that owns all device memory
+ * through its own pool, a thread whose process is capturing a CUDA graph in
+ * global capture mode, or a real-time loop that cannot take the device
+ * synchronisation of cudaMalloc/cudaFree).  It needs no grid: the geometry is
+ * given directly.  src and dst are two distinct buffers in the FP32_FIXED
+ * particle layout above (capacity entries per array, multiple of 64, 256-byte
+ * aligned); count_in (device int) is the number of particles in src;
+ * count_out (device int) receives the number of particles written to dst
+ * (removed particles, cell < 0, are dropped); tile_start (device array of
+ * ntiles + 1 ints, tiles numbered x fastest) receives each tile's first index
+ * in dst and, last, the total.  Order inside a tile is not specified.
+ * Scratch: one fixed array in device global memory, held by every device that
+ * loads the library until the process exits, sized for at most
+ * LPIC_NOALLOC_MAX_TILES tiles; larger tilings return LPIC_EINVAL.  The first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array, so calls whose work overlaps on the GPU
+ * (other streams, other threads) race and give wrong results; serialise them.
+ * Asynchronous on `stream`. */
+#define LPIC_NOALLOC_MAX_TILES 65536
+lpic_status lpic_sort_tiles_static(int dim, int nx, int ny, int nz, const int tile[3],
+                                   const void *src, void *dst, long long capacity,
+                                   const int *count_in, int *count_out, int *tile_start,
+                                   cudaStream_t stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char *lpic_last_error(void);
 

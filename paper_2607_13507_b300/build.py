@@ -13,7 +13,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib", "liblpic.so")
-SOURCES = [os.path.join(CSRC, "lpic_api.cu")]
+SOURCES = [os.path.join(CSRC, "lpic_api.cu"), os.path.join(CSRC, "lpic_noalloc.cu")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

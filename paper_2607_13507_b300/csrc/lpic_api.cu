@@ -67,6 +67,11 @@ struct Species {
 
 }  // namespace
 
+namespace lpic {
+// Lets the other translation units of the library report through lpic_last_error.
+__attribute__((visibility("hidden"))) void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace lpic
+
 struct lpic_grid {
     lpic_grid_desc d{};
     Laser laser{};

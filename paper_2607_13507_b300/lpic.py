@@ -27,7 +27,7 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_gather_push_deposit", "lpic_maxwell_half_step", "lpic_step",
            "lpic_deposit_charge", "lpic_positions_at_step", "lpic_diagnostics",
            "lpic_grid_get_info", "lpic_check_status", "lpic_last_error", "lpic_set_clock",
-           "lpic_graph_steps"]
+           "lpic_graph_steps", "lpic_sort_tiles_static"]
 
 
 class LpicError(RuntimeError):
@@ -92,6 +92,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_step.argtypes = [vp, ctypes.c_double, st]
     lib.lpic_set_clock.argtypes = [vp, ctypes.c_double, st]
     lib.lpic_graph_steps.argtypes = [vp, i, st]
+    lib.lpic_sort_tiles_static.argtypes = [i, i, i, i, ctypes.POINTER(i), vp, vp, ctypes.c_longlong,
+                                           vp, vp, vp, st]
     lib.lpic_deposit_charge.argtypes = [vp, i, vp, st]
     lib.lpic_positions_at_step.argtypes = [vp, i, vp, st]
     lib.lpic_diagnostics.argtypes = [vp, ctypes.POINTER(Diag), st]
