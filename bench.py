@@ -148,6 +148,36 @@ def ncu_traffic(workload):
 
 
 # ------------------------------------------------------------------ the GPU arm
+TUNED = os.path.join(ROOT, "paper_2607_13507_b300", "tuned.json")
+
+
+def tuned_choice(args, wl):
+    """Tile shape, particles per block and sort interval: from the command
+    line, else from a fresh autotuning run (--autotune), else from the
+    committed autotuner results for this workload, else the defaults."""
+    from paper_2607_13507_b300 import autotune as A
+    ch = {"tile": None, "block_particles": 0, "sort_interval": 0, "source": "defaults"}
+    if args.precision != "fp32":
+        return ch
+    if args.autotune:
+        best, _ = A.autotune(wl, cache=TUNED if args.autotune_save else None,
+                             log=lambda m: print(m, file=sys.stderr))
+        ch = {"tile": list(best.tile), "block_particles": best.block_particles,
+              "sort_interval": best.sort_interval, "source": "autotune"}
+    elif os.path.exists(TUNED):
+        rec = json.load(open(TUNED)).get(A.signature(wl))
+        if rec:
+            c = rec["choice"]
+            ch = {"tile": list(c["tile"]), "block_particles": c["block_particles"],
+                  "sort_interval": c["sort_interval"], "source": "autotuner results"}
+    if args.tile:
+        ch.update(tile=[int(v) for v in args.tile.split("x")], source="command line")
+    if args.block_particles:
+        ch.update(block_particles=args.block_particles, source="command line")
+    if args.sort_interval:
+        ch.update(sort_interval=args.sort_interval, source="command line")
+    return ch
+
 def run_b300(args, rank, world, local_rank):
     import torch
     from paper_2607_13507_b300 import build, lpic
@@ -161,8 +191,10 @@ def run_b300(args, rank, world, local_rank):
 
     wl = make_workload(args.workload, args.precision, seed_offset=rank, ny=args.ny)
     prec = lpic.FP32_FIXED if args.precision == "fp32" else lpic.FP64
+    tuned = tuned_choice(args, wl)
     parts = W.load_all(wl)
-    G = lpic.grid_for(wl, prec, device=dev)
+    G = lpic.grid_for(wl, prec, device=dev, tile=tuned["tile"], block_particles=tuned["block_particles"],
+                      sort_interval=tuned["sort_interval"])
     for p in parts:
         G.add_species(p, stream=stream)
     loaded = [p.n // wl.species[i].ppc for i, p in enumerate(parts)]
@@ -170,29 +202,10 @@ def run_b300(args, rank, world, local_rank):
     dt = G.dt
     pre = WORKLOADS[args.workload][1] if args.pre_steps is None else args.pre_steps
 
-    def one_step(t, evs=None):
-        G.maxwell_half(0, t, stream)
-        G.zero_current(stream)
-        for sp in G.species:
-            if prec == lpic.FP32_FIXED:
-                G.sort(sp.id, stream)
-            if evs is not None:
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                G.gather_push_deposit(sp.id, stream)
-                b.record(stream)
-                evs.append((sp.id, a, b))
-            else:
-                G.gather_push_deposit(sp.id, stream)
-        G.maxwell_half(1, t + 0.5 * dt, stream)
-
     step = 0
     with torch.cuda.stream(stream):
-        for _ in range(pre):
-            one_step(step * dt)
-            step += 1
-        for _ in range(args.warmup):
-            one_step(step * dt)
+        for _ in range(pre + args.warmup):
+            G.step(step * dt, stream)
             step += 1
     stream.synchronize()
     if G.check_status(stream) != 0:
@@ -205,13 +218,13 @@ def run_b300(args, rank, world, local_rank):
     clock.start()
     time.sleep(0.3)
     launches0 = G.info().launches
-    evs = []
+    G.kernel_timing(args.steps * len(G.species))
     t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     t_start.record(stream)
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
-            one_step(step * dt, evs)
+            G.step(step * dt, stream)
             step += 1
     t_stop.record(stream)
     torch.cuda.synchronize(dev)
@@ -223,17 +236,17 @@ def run_b300(args, rank, world, local_rank):
     counts1 = [sp.query(stream)[1] for sp in G.species]
     psteps = sum(0.5 * (a + b) for a, b in zip(counts0, counts1)) * args.steps
 
-    # dominant kernel: per-launch times and algorithmic bytes
-    kt = {}
-    for sid, a, b in evs:
-        kt.setdefault(sid, []).append(a.elapsed_time(b) / 1e3)
-    gpd_time = sum(sum(v) for v in kt.values())
+    # dominant kernel: per-launch times (events recorded by the library on the
+    # kernel's stream) and algorithmic bytes
+    gpd_ms, gpd_launches = G.kernel_time()
+    G.kernel_timing(0)
+    gpd_time = gpd_ms / 1e3
     algo_bytes_step = 0
     for i, sp in enumerate(G.species):
         n_mean = 0.5 * (counts0[i] + counts1[i])
         algo_bytes_step += algorithmic_bytes(wl, n_mean, loaded[i], args.precision)[0]
     launch_bytes = algo_bytes_step / len(G.species)
-    launch_time = gpd_time / max(1, sum(len(v) for v in kt.values()))
+    launch_time = gpd_time / max(1, gpd_launches)
 
     if world > 1:
         t = torch.tensor([elapsed, psteps], dtype=torch.float64, device=dev)
@@ -269,7 +282,7 @@ def run_b300(args, rank, world, local_rank):
                     sum(counts0) * algorithmic_bytes(wl, 1, 0, args.precision)[1] / 2 / 1e9),
                 "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             },
-            "gpd_particle_steps_per_s": psteps / max(gpd_time, 1e-12) / world if world == 1 else None,
+            "gpd_particle_steps_per_s": psteps / max(gpd_time, 1e-12) if world == 1 else None,
             "roofline": {
                 "bound": "hbm", "kernel": "k_gpd32" if args.precision == "fp32" else "k_gpd64",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -282,6 +295,8 @@ def run_b300(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+    if result is not None:
+        result["config"]["tuning"] = tuned
     state = dict(G=G, stream=stream, dev=dev, step=step, counts=counts1, wl=wl)
     return result, state
 
@@ -394,6 +409,11 @@ def main():
     ap.add_argument("--pre-steps", type=int, default=None,
                     help="untimed steps before warm-up (default: bring the laser onto the target)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--tile", default=None, help="tile shape, e.g. 8x8")
+    ap.add_argument("--block-particles", type=int, default=0)
+    ap.add_argument("--sort-interval", type=int, default=0)
+    ap.add_argument("--autotune", action="store_true", help="autotune tile/block/sort interval first")
+    ap.add_argument("--autotune-save", action="store_true", help="store the autotuner result")
     ap.add_argument("--ny", type=int, default=None,
                     help="transverse cells of the 2D laser workload (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -104,6 +104,9 @@ typedef struct {
     int block_particles;        /* FP32 path: at most this many particles per thread block
                                    (a crowded tile is split into several work items);
                                    0 = default (4096), else in [256, 2^20] */
+    int sort_interval;          /* FP32 path: lpic_step sorts every sort_interval steps
+                                   (0 or 1: every step); the tiles then carry a margin of
+                                   ceil((sort_interval - 1) c dt / h) cells for the drift */
     void *E[3], *B[3], *J[3];   /* caller-owned device field arrays (see layout) */
     const lpic_laser_desc *laser; /* NULL: no laser; copied at create (needs absorb_x) */
 } lpic_grid_desc;
@@ -174,8 +177,8 @@ lpic_status lpic_zero_current(lpic_grid_t grid, cudaStream_t stream);
  * (Sec. 3.1), Boris u^n -> u^{n+1} (Sec. 3.1), advance the position by
  * dt v^{n+1} to x^{n+3/2}, and add the Esirkepov current of that straight
  * path (Sec. 3.1) to J.  FP64 path: one thread per particle, double atomics.
- * FP32 path: needs the species sorted by tile since its last push (the sort
- * of the same step); one thread block per tile with the tile's E/B halo and
+ * FP32 path: needs the species sorted by tile within its last sort_interval
+ * pushes; one thread block per tile with the tile's E/B halo and
  * an int64 fixed-point J accumulator in shared memory, flushed once per tile
  * with integer atomics (deterministic, bit-exact continuity). */
 lpic_status lpic_gather_push_deposit(lpic_grid_t grid, int species_id, cudaStream_t stream);
@@ -187,7 +190,9 @@ lpic_status lpic_gather_push_deposit(lpic_grid_t grid, int species_id, cudaStrea
 lpic_status lpic_maxwell_half_step(lpic_grid_t grid, int half, double t, cudaStream_t stream);
 
 /* One full step t -> t + dt (Algorithm 1): Maxwell half 0, zero J, per
- * species sort (FP32 path) and gather_push_deposit, Maxwell half 1. */
+ * species sort (FP32 path, every sort_interval steps; the push before a sort
+ * also builds the next sort's tile histogram) and gather_push_deposit,
+ * Maxwell half 1. */
 lpic_status lpic_step(lpic_grid_t grid, double t, cudaStream_t stream);
 
 /* Set the device clock that captured steps read the laser time from. */
@@ -218,6 +223,14 @@ lpic_status lpic_positions_at_step(lpic_grid_t grid, int species_id, double *out
 lpic_status lpic_diagnostics(lpic_grid_t grid, lpic_diag *out, cudaStream_t stream);
 
 lpic_status lpic_grid_get_info(lpic_grid_t grid, lpic_grid_info *out);
+
+/* Benchmark timing of the fused particle kernel: lpic_kernel_timing(g, n)
+ * (re)starts recording CUDA events on the launching stream around the next n
+ * launches of that kernel (0 stops); lpic_kernel_time waits for them and
+ * returns the summed elapsed milliseconds and the number of timed launches.
+ * Eager calls only (not under graph capture). */
+lpic_status lpic_kernel_timing(lpic_grid_t grid, int max_launches);
+lpic_status lpic_kernel_time(lpic_grid_t grid, double *ms, long long *launches);
 
 /* Synchronise `stream`, return the device status bits in *bits and clear
  * them; returns LPIC_EDEVICE when any bit was set. */

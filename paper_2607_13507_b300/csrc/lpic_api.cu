@@ -62,7 +62,9 @@ struct Species {
     int* d_nitems = nullptr;
     long long item_cap = 0;
     double wmax = 0;
-    bool sorted = false;         // sorted since the last push (FP32 path needs it)
+    bool sorted = false;         // sorted at least once
+    int since_sort = 1 << 30;    // pushes since the last sort
+    bool counts_fresh = false;   // d_count holds the histogram of the current cells
 };
 
 }  // namespace
@@ -91,11 +93,17 @@ struct lpic_grid {
     size_t smem32 = 0;
     long long launches = 0;
     int P = 4096;                              // particles per work item (FP32 path)
+    int K = 1;                                 // sort interval (steps)
+    int m[3] = {0, 0, 0};                      // drift margin of the tiles (cells)
     CellDecode dec{};
     FastDiv fT[3]{};
     double* d_clock = nullptr;                 // device time for graph replays
     std::map<unsigned, cudaGraphExec_t> graphs;  // captured steps keyed by buffer parity
     std::map<unsigned, long long> graph_launches;
+    // optional timing of the fused particle kernel (benchmarks)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;               // pairs (start, stop)
+    size_t ev_used = 0;
     bool attrs_set = false;
 };
 
@@ -161,10 +169,15 @@ __global__ void k_absmax_f64(const double* w, const int* n, unsigned long long* 
 
 // tile-kernel instance and its dynamic shared memory
 template <int DIM, int ORDER>
-lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st) {
+lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
     const P32 p = view32(g, s, s.cur);
     Tiles t{};
-    for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; }
+    for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; t.m[d] = g->m[d]; t.fT[d] = g->fT[d]; }
+    t.next_count = nullptr;
+    if (count_next) {
+        LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (g->ntiles + 1), st));
+        t.next_count = s.d_count;
+    }
     t.start = s.d_start;
     t.items = s.d_items;
     t.nitems = s.d_nitems;
@@ -245,18 +258,22 @@ lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st, cons
     return LPIC_OK;
 }
 
-lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st) {
+// use_counts: d_count already holds the tile histogram of the current cells
+// (computed by the preceding push), so the counting pass is skipped.
+lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st, bool use_counts = false) {
     const int other = 1 - s.cur;
     const int nt = (int)g->ntiles;
-    LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (nt + 1), st));
+    if (!use_counts) LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (nt + 1), st));
     LPIC_CUDA(cudaMemsetAsync(s.d_cursor, 0, sizeof(int) * (nt + 1), st));
     const int nb = grid_blocks(s.cap, g->nsm, 16);
     const int dim = g->d.dim;
     if (g->d.precision == LPIC_FP32_FIXED) {
         const P32 src = view32(g, s, s.cur), dst = view32(g, s, other);
         KeyFP32 key{src.cell, g->dec, g->fT[0], g->fT[1], g->fT[2], g->nt[0], g->nt[1], nt};
-        k_sort_count<<<nb, 256, 0, st>>>(key, s.d_n, s.d_count);
-        LPIC_LAUNCHED("k_sort_count");
+        if (!use_counts) {
+            k_sort_count<<<nb, 256, 0, st>>>(key, s.d_n, s.d_count);
+            LPIC_LAUNCHED("k_sort_count");
+        }
         k_sort_scan<<<1, 1024, 0, st>>>(s.d_count, s.d_start, nt, g->P, s.d_coff);
         LPIC_LAUNCHED("k_sort_scan");
         k_sort_items<<<grid_blocks(nt, g->nsm), 256, 0, st>>>(s.d_count, s.d_coff, nt, g->P, s.d_items, s.d_nitems);
@@ -279,6 +296,8 @@ lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st) {
     LPIC_LAUNCHED("k_sort_finalize");
     s.cur = other;
     s.sorted = true;
+    s.since_sort = 0;
+    s.counts_fresh = false;
     return LPIC_OK;
 }
 
@@ -356,6 +375,7 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     if (d.laser && !d.absorb_x) return fail(LPIC_EINVAL, "a laser needs absorbing x edges");
     if (d.block_particles != 0 && (d.block_particles < 256 || d.block_particles > (1 << 20)))
         return fail(LPIC_EINVAL, "block_particles must be 0 or in [256, 2^20]");
+    if (d.sort_interval < 0 || d.sort_interval > 64) return fail(LPIC_EINVAL, "sort_interval must be in [0, 64]");
     for (int c = 0; c < 3; ++c)
         if (!d.E[c] || !d.B[c] || !d.J[c]) return fail(LPIC_EINVAL, "field pointer %d is NULL", c);
     auto* g = new (std::nothrow) lpic_grid;
@@ -388,10 +408,16 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     for (int k = 0; k < 3; ++k) g->fT[k] = make_fastdiv((unsigned)g->T[k]);
     g->dec = CellDecode{make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny)};
     if (d.block_particles > 0) g->P = d.block_particles;
+    g->K = d.sort_interval > 1 ? d.sort_interval : 1;
+    {
+        // a particle moves less than c dt / h cells per step (Courant limit)
+        const double hh[3] = {d.dx, d.dy, d.dim == 3 ? d.dz : 1.0};
+        for (int k = 0; k < d.dim; ++k) g->m[k] = (int)std::ceil((g->K - 1) * d.dt / hh[k] - 1e-12);
+    }
     {
         const int D = d.dim;
         long long G = 1, H = 1;
-        for (int k = 0; k < D; ++k) { G *= g->T[k] + 4; H *= g->T[k] + 5; }
+        for (int k = 0; k < D; ++k) { G *= g->T[k] + 2 * g->m[k] + 4; H *= g->T[k] + 2 * g->m[k] + 5; }
         g->smem32 = (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 12;
         if (d.precision == LPIC_FP32_FIXED && g->smem32 > 227 * 1024) {
             delete g;
@@ -434,6 +460,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
         cudaFree(s.d_coff); cudaFree(s.d_items); cudaFree(s.d_nitems);
     }
     for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    for (auto e : g->ev) cudaEventDestroy(e);
     cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur);
     cudaFree(g->d_clock);
     delete g;
@@ -558,22 +585,34 @@ lpic_status lpic_zero_current(lpic_grid_t g, cudaStream_t st) {
     return LPIC_OK;
 }
 
-lpic_status lpic_gather_push_deposit(lpic_grid_t g, int sid, cudaStream_t st) {
-    if (lpic_status r = check_species(g, sid)) return r;
+static lpic_status gpd_impl(lpic_grid_t g, int sid, cudaStream_t st, bool count_next) {
     Species& s = g->sp[sid];
     g->started = true;
     const int D = g->d.dim, O = g->d.shape_order;
     lpic_status r;
     if (g->d.precision == LPIC_FP32_FIXED) {
-        if (!s.sorted) return fail(LPIC_EINVAL, "species %d must be sorted by tile before each push", sid);
-        if (D == 2) r = (O == 1) ? launch_gpd32<2, 1>(g, s, st) : launch_gpd32<2, 2>(g, s, st);
-        else        r = (O == 1) ? launch_gpd32<3, 1>(g, s, st) : launch_gpd32<3, 2>(g, s, st);
-        s.sorted = false;
+        if (!s.sorted || s.since_sort >= g->K)
+            return fail(LPIC_EINVAL, "species %d must be sorted by tile at least every %d pushes", sid, g->K);
+        const bool timed = g->timing && g->ev_used + 2 <= g->ev.size();
+        if (timed) LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used], st));
+        if (D == 2) r = (O == 1) ? launch_gpd32<2, 1>(g, s, st, count_next) : launch_gpd32<2, 2>(g, s, st, count_next);
+        else        r = (O == 1) ? launch_gpd32<3, 1>(g, s, st, count_next) : launch_gpd32<3, 2>(g, s, st, count_next);
+        if (timed) { LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used + 1], st)); g->ev_used += 2; }
+        s.since_sort += 1;
+        s.counts_fresh = count_next && r == LPIC_OK;
     } else {
+        const bool timed = g->timing && g->ev_used + 2 <= g->ev.size();
+        if (timed) LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used], st));
         if (D == 2) r = (O == 1) ? launch_gpd64<2, 1>(g, s, st) : launch_gpd64<2, 2>(g, s, st);
         else        r = (O == 1) ? launch_gpd64<3, 1>(g, s, st) : launch_gpd64<3, 2>(g, s, st);
+        if (timed) { LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used + 1], st)); g->ev_used += 2; }
     }
     return r;
+}
+
+lpic_status lpic_gather_push_deposit(lpic_grid_t g, int sid, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    return gpd_impl(g, sid, st, false);
 }
 
 static lpic_status maxwell_any(lpic_grid_t g, int half, double t, cudaStream_t st, const double* clock) {
@@ -596,9 +635,15 @@ static lpic_status step_impl(lpic_grid_t g, double t, cudaStream_t st, double* c
     if (lpic_status r = maxwell_any(g, 0, clock ? 0.0 : t, st, clock)) return r;
     if (lpic_status r = lpic_zero_current(g, st)) return r;
     for (int s = 0; s < (int)g->sp.size(); ++s) {
-        if (g->d.precision == LPIC_FP32_FIXED)
-            if (lpic_status r = sort_one(g, g->sp[s], st)) return r;
-        if (lpic_status r = lpic_gather_push_deposit(g, s, st)) return r;
+        Species& sp = g->sp[s];
+        bool count_next = false;
+        if (g->d.precision == LPIC_FP32_FIXED) {
+            // sort every K steps; the push before a sort counts its tile keys
+            if (!sp.sorted || sp.since_sort >= g->K)
+                if (lpic_status r = sort_one(g, sp, st, sp.sorted && sp.counts_fresh)) return r;
+            count_next = sp.since_sort + 1 >= g->K;
+        }
+        if (lpic_status r = gpd_impl(g, s, st, count_next)) return r;
     }
     if (lpic_status r = maxwell_any(g, 1, (clock ? 0.0 : t) + 0.5 * g->d.dt, st, clock)) return r;
     if (clock) {
@@ -628,18 +673,24 @@ lpic_status lpic_graph_steps(lpic_grid_t g, int nsteps, cudaStream_t st) {
     for (int k = 0; k < nsteps; ++k) {
         unsigned key = 0;
         for (size_t s = 0; s < g->sp.size(); ++s) key |= (unsigned)g->sp[s].cur << s;
+        if (g->d.precision == LPIC_FP32_FIXED && !g->sp.empty()) {
+            const Species& s0 = g->sp[0];
+            const int phase = (!s0.sorted || s0.since_sort >= g->K) ? 0 : s0.since_sort;
+            key |= (unsigned)phase << 16 | (unsigned)(s0.sorted && s0.counts_fresh) << 24 | (unsigned)s0.sorted << 25;
+        }
         auto it = g->graphs.find(key);
         if (it == g->graphs.end()) {
             // capture one step starting from this buffer parity
-            std::vector<int> cur0;
-            std::vector<bool> sorted0;
-            for (auto& s : g->sp) { cur0.push_back(s.cur); sorted0.push_back(s.sorted); }
+            std::vector<Species> saved = g->sp;
             const long long l0 = g->launches;
             LPIC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             lpic_status r = step_impl(g, 0.0, st, g->d_clock);
             cudaGraph_t graph = nullptr;
             cudaError_t e = cudaStreamEndCapture(st, &graph);
-            for (size_t s = 0; s < g->sp.size(); ++s) { g->sp[s].cur = cur0[s]; g->sp[s].sorted = sorted0[s]; }
+            for (size_t s = 0; s < g->sp.size(); ++s) {
+                g->sp[s].cur = saved[s].cur; g->sp[s].sorted = saved[s].sorted;
+                g->sp[s].since_sort = saved[s].since_sort; g->sp[s].counts_fresh = saved[s].counts_fresh;
+            }
             const long long per_step = g->launches - l0;
             g->launches = l0;
             if (r != LPIC_OK) { if (graph) cudaGraphDestroy(graph); return r; }
@@ -654,9 +705,13 @@ lpic_status lpic_graph_steps(lpic_grid_t g, int nsteps, cudaStream_t st) {
         }
         LPIC_CUDA(cudaGraphLaunch(it->second, st));
         g->launches += g->graph_launches[key];
-        // the replayed step flipped every sorted species' buffers
+        // replay the host-side bookkeeping of the captured step
         if (g->d.precision == LPIC_FP32_FIXED)
-            for (auto& s : g->sp) { s.cur = 1 - s.cur; s.sorted = false; }
+            for (auto& s : g->sp) {
+                if (!s.sorted || s.since_sort >= g->K) { s.cur = 1 - s.cur; s.sorted = true; s.since_sort = 0; }
+                s.since_sort += 1;
+                s.counts_fresh = s.since_sort >= g->K;
+            }
         g->started = true;
     }
     return LPIC_OK;
@@ -731,6 +786,35 @@ lpic_status lpic_diagnostics(lpic_grid_t g, lpic_diag* out, cudaStream_t st) {
     out->charge = acc[1];
     out->field = acc[2];
     out->particles = (long long)cnt;
+    return LPIC_OK;
+}
+
+lpic_status lpic_kernel_timing(lpic_grid_t g, int max_launches) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (max_launches < 0) return fail(LPIC_EINVAL, "max_launches must be >= 0");
+    for (auto e : g->ev) cudaEventDestroy(e);
+    g->ev.clear();
+    g->ev_used = 0;
+    g->timing = max_launches > 0;
+    for (int i = 0; i < 2 * max_launches; ++i) {
+        cudaEvent_t e;
+        LPIC_CUDA(cudaEventCreate(&e));
+        g->ev.push_back(e);
+    }
+    return LPIC_OK;
+}
+
+lpic_status lpic_kernel_time(lpic_grid_t g, double* ms, long long* launches) {
+    if (lpic_status r = check_grid(g)) return r;
+    double total = 0.0;
+    for (size_t i = 0; i + 1 < g->ev_used; i += 2) {
+        LPIC_CUDA(cudaEventSynchronize(g->ev[i + 1]));
+        float t = 0.0f;
+        LPIC_CUDA(cudaEventElapsedTime(&t, g->ev[i], g->ev[i + 1]));
+        total += t;
+    }
+    if (ms) *ms = total;
+    if (launches) *launches = (long long)(g->ev_used / 2);
     return LPIC_OK;
 }
 

@@ -158,6 +158,23 @@ __device__ inline void boris(R& ux, R& uy, R& uz, R k, R ex, R ey, R ez, R bx, R
     uz = mz + (px * sy - py * sx) + k * ez;
 }
 
+// FP32 Boris with hardware reciprocal square root and fast division (a few
+// ulp, within the FP32 path's error budget).
+__device__ inline void boris_f32(float& ux, float& uy, float& uz, float k, float ex, float ey,
+                                 float ez, float bx, float by, float bz) {
+    const float mx = ux + k * ex, my = uy + k * ey, mz = uz + k * ez;
+    const float kg = k * rsqrtf(1.0f + mx * mx + my * my + mz * mz);
+    const float tx = kg * bx, ty = kg * by, tz = kg * bz;
+    const float f = __fdividef(2.0f, 1.0f + tx * tx + ty * ty + tz * tz);
+    const float sx = f * tx, sy = f * ty, sz = f * tz;
+    const float px = mx + (my * tz - mz * ty);
+    const float py = my + (mz * tx - mx * tz);
+    const float pz = mz + (mx * ty - my * tx);
+    ux = mx + (py * sz - pz * sy) + k * ex;
+    uy = my + (pz * sx - px * sz) + k * ey;
+    uz = mz + (px * sy - py * sx) + k * ez;
+}
+
 // ------------------------------------------------------------ laser (Sec. 4.2)
 struct Laser {
     int on; double a0, w0, tau, omega, yc, zc;

@@ -55,10 +55,13 @@ struct P32 {
 struct Tiles {
     int T[3];            // cells per tile
     int nt[3];           // tiles per dimension
+    int m[3];            // margin (cells) the particles may have drifted since the sort
     const int* start;    // ntiles + 1 prefix offsets (after the sort)
     const int2* items;   // (tile, chunk) work items
     const int* nitems;   // device count of work items
     int P;               // particles per chunk
+    FastDiv fT[3];       // division by T (tile keys of the next sort)
+    int* next_count;     // if set: histogram of the new tile keys for the next sort
 };
 
 template <int ORDER, class W>
@@ -348,8 +351,17 @@ __device__ inline void charge_int(unsigned long long* rho, const Geo& g, const i
 // ----------------------------------------------------------- the tile kernel
 // Shared memory: 6 field boxes (T+4 per dimension, halo 2 below and 2 above),
 // an int32 round box and an int64 total box for J (T+5 per dimension).
+// Blocks per SM the register allocation targets (2D: the kernel fits 80
+// registers with negligible spills; 3D TSC needs the full register file).
+#ifndef LPIC_GPD2D_MINB
+#define LPIC_GPD2D_MINB 3
+#endif
+#ifndef LPIC_GPD3D_MINB
+#define LPIC_GPD3D_MINB 1
+#endif
+
 template <int DIM, int ORDER>
-__global__ void __launch_bounds__(256) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<const float> B,
+__global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<const float> B,
                                                Ptr3<unsigned long long> J, P32 p, Tiles t,
                                                CellDecode dec, float k, float sq, float dth0,
                                                float dth1, float dth2, unsigned* st) {
@@ -360,10 +372,13 @@ __global__ void __launch_bounds__(256) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<
     const int beg = tbeg + item.y * t.P;
     const int end = min(beg + t.P, tend);
     if (beg >= end) return;
-    const int t0[3] = {(tile % t.nt[0]) * t.T[0], ((tile / t.nt[0]) % t.nt[1]) * t.T[1],
-                       DIM == 3 ? (tile / (t.nt[0] * t.nt[1])) * t.T[2] : 0};
-    const int G0 = t.T[0] + 4, G1 = t.T[1] + 4, G2 = (DIM == 3) ? t.T[2] + 4 : 1;
-    const int H0 = t.T[0] + 5, H1 = t.T[1] + 5, H2 = (DIM == 3) ? t.T[2] + 5 : 1;
+    // box origin: the tile origin less the drift margin; particles sit in
+    // local cells [0, T + 2m) of it
+    const int t0[3] = {(tile % t.nt[0]) * t.T[0] - t.m[0], ((tile / t.nt[0]) % t.nt[1]) * t.T[1] - t.m[1],
+                       DIM == 3 ? (tile / (t.nt[0] * t.nt[1])) * t.T[2] - t.m[2] : 0};
+    const int Te[3] = {t.T[0] + 2 * t.m[0], t.T[1] + 2 * t.m[1], t.T[2] + 2 * t.m[2]};
+    const int G0 = Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
+    const int H0 = Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
     const int fsz = G0 * G1 * G2, jsz = H0 * H1 * H2;
     extern __shared__ float4 smem4[];
     float* sF = reinterpret_cast<float*>(smem4);
@@ -387,13 +402,23 @@ __global__ void __launch_bounds__(256) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<
     for (int rnd = 0; rnd < nround; ++rnd) {
         const int i = beg + rnd * blockDim.x + threadIdx.x;
         const int cell = (i < end) ? p.cell[i] : -1;
+        int cell_out = cell;      // the particle's cell after this round (-1: removed)
         if (cell >= 0) {
             int gc[3];
             dec(cell, gc);
             int lc[3] = {gc[0] - t0[0], gc[1] - t0[1], DIM == 3 ? gc[2] - t0[2] : 0};
             bool inside = true;
+            const int nn[3] = {g.nx, g.ny, g.nz};
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) inside &= (lc[d] >= 0 && lc[d] < t.T[d]);
+            for (int d = 0; d < DIM; ++d) {
+                // a particle that crossed a periodic edge since the sort is
+                // taken at its image next to the tile
+                if (!(d == 0 && g.absorb)) {
+                    if (lc[d] < 0) lc[d] += nn[d];
+                    else if (lc[d] >= Te[d]) lc[d] -= nn[d];
+                }
+                inside &= (lc[d] >= 0 && lc[d] < Te[d]);
+            }
             if (!inside) {
                 set_status(st, LPIC_ST_HALO);
             } else {
@@ -428,10 +453,11 @@ __global__ void __launch_bounds__(256) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<
                     }
                     fld[comp] = accv;
                 }
-                boris<float>(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
+                boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
                 if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
                     set_status(st, LPIC_ST_NAN);
                     p.cell[i] = -1;
+                    cell_out = -1;
                 } else {
                     const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
                     const float uu[3] = {ux, uy, uz};
@@ -452,6 +478,7 @@ __global__ void __launch_bounds__(256) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<
                     if (cfl) {
                         set_status(st, LPIC_ST_CFL);
                         p.cell[i] = -1;
+                        cell_out = -1;
                     } else {
                         const float s = sq * w;
                         if (DIM == 3) deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
@@ -465,13 +492,26 @@ __global__ void __launch_bounds__(256) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<
                         else ng[0] = wrapi(ng[0], g.nx);
                         ng[1] = wrapi(ng[1], g.ny);
                         if (DIM == 3) ng[2] = wrapi(ng[2], g.nz);
-                        p.cell[i] = dead ? -1 : (ng[2] * g.ny + ng[1]) * g.nx + ng[0];
+                        cell_out = dead ? -1 : (ng[2] * g.ny + ng[1]) * g.nx + ng[0];
+                        p.cell[i] = cell_out;
 #pragma unroll
                         for (int d = 0; d < DIM; ++d) p.off[d][i] = fe[d];
                         p.u[0][i] = ux; p.u[1][i] = uy; p.u[2][i] = uz;
                     }
                 }
             }
+        }
+        // histogram of the tile keys for the next sort (all lanes take part)
+        if (t.next_count) {
+            int key = -1;
+            if (cell_out >= 0) {
+                int gc2[3];
+                dec(cell_out, gc2);
+                key = (fdiv(gc2[2], t.fT[2]) * t.nt[1] + fdiv(gc2[1], t.fT[1])) * t.nt[0] + fdiv(gc2[0], t.fT[0]);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(t.next_count + key, __popc(peers));
         }
         // fold the round's int32 box into the int64 box
         __syncthreads();

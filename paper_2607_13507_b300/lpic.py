@@ -27,7 +27,8 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_gather_push_deposit", "lpic_maxwell_half_step", "lpic_step",
            "lpic_deposit_charge", "lpic_positions_at_step", "lpic_diagnostics",
            "lpic_grid_get_info", "lpic_check_status", "lpic_last_error", "lpic_set_clock",
-           "lpic_graph_steps", "lpic_sort_tiles_static"]
+           "lpic_graph_steps", "lpic_sort_tiles_static", "lpic_kernel_timing",
+           "lpic_kernel_time"]
 
 
 class LpicError(RuntimeError):
@@ -46,6 +47,7 @@ class GridDesc(ctypes.Structure):
                 ("dz", ctypes.c_double), ("dt", ctypes.c_double), ("absorb_x", ctypes.c_int),
                 ("shape_order", ctypes.c_int), ("precision", ctypes.c_int),
                 ("tile", ctypes.c_int * 3), ("block_particles", ctypes.c_int),
+                ("sort_interval", ctypes.c_int),
                 ("E", ctypes.c_void_p * 3), ("B", ctypes.c_void_p * 3),
                 ("J", ctypes.c_void_p * 3), ("laser", ctypes.POINTER(LaserDesc))]
 
@@ -92,6 +94,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_step.argtypes = [vp, ctypes.c_double, st]
     lib.lpic_set_clock.argtypes = [vp, ctypes.c_double, st]
     lib.lpic_graph_steps.argtypes = [vp, i, st]
+    lib.lpic_kernel_timing.argtypes = [vp, i]
+    lib.lpic_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.lpic_sort_tiles_static.argtypes = [i, i, i, i, ctypes.POINTER(i), vp, vp, ctypes.c_longlong,
                                            vp, vp, vp, st]
     lib.lpic_deposit_charge.argtypes = [vp, i, vp, st]
@@ -232,7 +236,7 @@ class Grid:
     """A grid with caller-owned (torch) field arrays and its species."""
 
     def __init__(self, dim, n, h, dt, order, precision, absorb_x=False, laser=None, tile=None,
-                 device="cuda", block_particles=0):
+                 device="cuda", block_particles=0, sort_interval=0):
         load()
         self.dim, self.precision, self.order = dim, precision, order
         self.n = tuple(int(v) for v in n) + ((1,) if dim == 2 else ())
@@ -252,7 +256,7 @@ class Grid:
         if laser is not None:
             self._laser = LaserDesc(laser.a0, laser.w0, laser.tau, laser.omega, laser.yc, laser.zc)
         desc = GridDesc(dim, self.n[0], self.n[1], nz, self.h[0], self.h[1], self.h[2], self.dt,
-                        int(absorb_x), order, precision, (ctypes.c_int * 3)(*t), int(block_particles),
+                        int(absorb_x), order, precision, (ctypes.c_int * 3)(*t), int(block_particles), int(sort_interval),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.E]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.B]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.J]),
@@ -307,6 +311,16 @@ class Grid:
         """nsteps full steps replayed from captured CUDA graphs (device clock)."""
         _check(load().lpic_graph_steps(self.h_, nsteps, _stream(stream)))
 
+    def kernel_timing(self, max_launches):
+        """Record CUDA events around the next max_launches fused-kernel launches."""
+        _check(load().lpic_kernel_timing(self.h_, int(max_launches)))
+
+    def kernel_time(self):
+        """(summed milliseconds, launches) of the timed fused-kernel launches."""
+        ms, n = ctypes.c_double(), ctypes.c_longlong()
+        _check(load().lpic_kernel_time(self.h_, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
     def diagnostics(self, stream=None) -> Diag:
         out = Diag()
         _check(load().lpic_diagnostics(self.h_, ctypes.byref(out), _stream(stream)))
@@ -327,7 +341,7 @@ class Grid:
         return [self.J[c].to(torch.float64) * inf.j_scale[c] for c in range(3)]
 
 
-def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0) -> Grid:
+def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, sort_interval=0) -> Grid:
     """A Grid for a workloads.Workload (laser centred transversally)."""
     from . import workloads as W
     prec = precision if precision is not None else (FP64 if wl.precision == "fp64" else FP32_FIXED)
@@ -337,4 +351,4 @@ def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0) ->
         laser = W.LaserSpec(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega)
         laser.yc, laser.zc = c[0], (c[1] if wl.dim == 3 else 0.0)
     return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device,
-                block_particles)
+                block_particles, sort_interval)

@@ -251,7 +251,7 @@ def test_diagnostics_match_oracle_energy():
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_graph_replay_matches_eager_steps(precision):
     """Steps replayed from captured CUDA graphs give the same state as the
-    same steps issued call by call (bitwise without a laser)."""
+    same steps issued call by call (FP32 path: bitwise)."""
     from paper_2607_13507_b300 import lpic
     wl = W.thermal2d(n=40, ppc=4, vth=0.1, order=2, precision=precision)
     prec = lpic.FP32_FIXED if precision == "fp32" else lpic.FP64
@@ -267,9 +267,11 @@ def test_graph_replay_matches_eager_steps(precision):
     Gb.graph_steps(4, side)
     torch.cuda.synchronize()
     for c in range(3):
-        assert torch.equal(Ga.E[c], Gb.E[c])
-        assert torch.equal(Ga.B[c], Gb.B[c])
-        assert torch.equal(Ga.J[c], Gb.J[c])
+        for a, b in ((Ga.E[c], Gb.E[c]), (Ga.B[c], Gb.B[c]), (Ga.J[c], Gb.J[c])):
+            if precision == "fp32":
+                assert torch.equal(a, b)        # integer current: bitwise
+            else:                               # double atomics: summation order varies
+                assert rel_l2(b.cpu().numpy(), a.cpu().numpy()) < 1e-13
     assert Ga.species[0].query()[0] == Gb.species[0].query()[0]
     assert Gb.check_status() == 0
     with pytest.raises(Exception):
@@ -291,3 +293,43 @@ def test_graph_replay_with_laser_clock():
     torch.cuda.synchronize()
     for c in range(3):
         assert rel_l2(Gb.E[c].cpu().numpy(), Ga.E[c].cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("case", ["thermal2d", "laser2d", "thermal3d"])
+def test_sort_interval_gives_bitwise_identical_state(case):
+    """Sorting every 3 steps instead of every step changes only the order in
+    which particles are visited: every particle's update depends on the
+    fields and its own state, and the current is an integer sum, so fields,
+    currents and every particle's state must agree bit for bit (and no
+    particle may leave its tile's drift margin, including across periodic
+    edges)."""
+    from paper_2607_13507_b300 import lpic
+    if case == "thermal2d":
+        wl = W.thermal2d(n=48, ppc=4, vth=0.3, order=2, precision="fp32")
+    elif case == "laser2d":
+        wl = W.laser2d(nx=128, ny=32, ppc=2, precision="fp32")
+    else:
+        wl = W.thermal3d(n=16, ppc=2, vth=0.3, order=2)
+    parts = W.load_all(wl)
+    tile = (8, 8) if wl.dim == 2 else (4, 4, 4)     # 3D: the drift margin enlarges the boxes
+    G1 = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile)
+    G3 = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile, sort_interval=3)
+    for p in parts:
+        G1.add_species(p)
+        G3.add_species(p)
+    for s in range(8):
+        G1.step(s * wl.dt)
+        G3.step(s * wl.dt)
+    torch.cuda.synchronize()
+    assert G1.check_status() == 0 and G3.check_status() == 0
+    for c in range(3):
+        assert torch.equal(G1.E[c], G3.E[c])
+        assert torch.equal(G1.B[c], G3.B[c])
+        assert torch.equal(G1.J[c], G3.J[c])
+    for a, b in zip(G1.species, G3.species):
+        sa, sb = a.state(), b.state()
+        oa, ob = np.argsort(sa["id"]), np.argsort(sb["id"])
+        assert np.array_equal(sa["id"][oa], sb["id"][ob])
+        assert np.array_equal(sa["cell"][oa], sb["cell"][ob])
+        assert np.array_equal(sa["off"][:, oa], sb["off"][:, ob])
+        assert np.array_equal(sa["u"][:, oa], sb["u"][:, ob])
