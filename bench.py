@@ -42,12 +42,12 @@ WORKLOADS = {
 }
 
 
-def make_workload(name, precision, seed_offset=0, ny=None):
+def make_workload(name, precision, seed_offset=0, ny=None, n3=None):
     from paper_2607_13507_b300 import workloads as W
     if name == "laser2d":
         wl = W.laser2d(precision=precision, ny=ny or 1024)
     elif name == "thermal3d":
-        wl = W.thermal3d(precision=precision)
+        wl = W.thermal3d(precision=precision, n=n3 or 256)
     elif name == "thermal2d":
         wl = W.thermal2d(precision=precision)
     else:
@@ -189,7 +189,7 @@ def run_b300(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
 
-    wl = make_workload(args.workload, args.precision, seed_offset=rank, ny=args.ny)
+    wl = make_workload(args.workload, args.precision, seed_offset=rank, ny=args.ny, n3=args.n3)
     prec = lpic.FP32_FIXED if args.precision == "fp32" else lpic.FP64
     tuned = tuned_choice(args, wl)
     parts = W.load_all(wl)
@@ -414,6 +414,8 @@ def main():
     ap.add_argument("--sort-interval", type=int, default=0)
     ap.add_argument("--autotune", action="store_true", help="autotune tile/block/sort interval first")
     ap.add_argument("--autotune-save", action="store_true", help="store the autotuner result")
+    ap.add_argument("--n3", type=int, default=None,
+                    help="cells per side of the 3D thermal workload (smaller cases for profiling)")
     ap.add_argument("--ny", type=int, default=None,
                     help="transverse cells of the 2D laser workload (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -75,7 +75,8 @@ typedef enum {
 
 /* device status bits (lpic_check_status) */
 #define LPIC_ST_CFL       0x1u  /* a particle moved >= 1 cell in a step */
-#define LPIC_ST_HALO      0x2u  /* a particle left its tile's halo (sort too rare) */
+#define LPIC_ST_HALO      0x2u  /* reserved (particles beyond a tile's margin take the
+                                   global-memory path instead) */
 #define LPIC_ST_NAN       0x4u  /* non-finite momentum */
 #define LPIC_ST_OUTSIDE   0x8u  /* a deposit or gather reached past an absorbing edge */
 #define LPIC_ST_OVERFLOW  0x10u /* a fixed-point value exceeded its bound */
@@ -106,7 +107,9 @@ typedef struct {
                                    0 = default (4096), else in [256, 2^20] */
     int sort_interval;          /* FP32 path: lpic_step sorts every sort_interval steps
                                    (0 or 1: every step); the tiles then carry a margin of
-                                   ceil((sort_interval - 1) c dt / h) cells for the drift */
+                                   ceil((sort_interval - 1) c dt / h) cells for the drift
+                                   (less if the boxes would not fit in shared memory);
+                                   particles beyond it take a global-memory path */
     void *E[3], *B[3], *J[3];   /* caller-owned device field arrays (see layout) */
     const lpic_laser_desc *laser; /* NULL: no laser; copied at create (needs absorb_x) */
 } lpic_grid_desc;
@@ -235,6 +238,29 @@ lpic_status lpic_kernel_time(lpic_grid_t grid, double *ms, long long *launches);
 /* Synchronise `stream`, return the device status bits in *bits and clear
  * them; returns LPIC_EDEVICE when any bit was set. */
 lpic_status lpic_check_status(lpic_grid_t grid, cudaStream_t stream, unsigned *bits);
+
+/* Ensembles: many independent grids stepped together (batched scheduling).
+ * One launch per field pass and per sort pass covers every grid, and one
+ * persistent particle kernel takes (species, work item) entries from a
+ * device queue that visits the densest species first.  Requirements: at
+ * least one grid; all grids on the FP32_FIXED path with the same dimension,
+ * shape order, tile shape and block_particles, sort_interval <= 1, periodic
+ * boundaries and no laser; every grid has its species added and all species
+ * buffers at the same parity.  The grids stay owned by the caller and must
+ * outlive the ensemble; while it exists they are stepped through it (queries
+ * and diagnostics on the grids remain valid). */
+typedef struct lpic_ensemble *lpic_ensemble_t;
+lpic_status lpic_create_ensemble(lpic_grid_t *grids, int n, lpic_ensemble_t *out);
+lpic_status lpic_destroy_ensemble(lpic_ensemble_t ensemble);
+/* One step of every grid (as lpic_step). */
+lpic_status lpic_ensemble_step(lpic_ensemble_t ensemble, cudaStream_t stream);
+/* nsteps ensemble steps replayed from captured CUDA graphs (one per buffer
+ * parity); `stream` must be a created stream. */
+lpic_status lpic_ensemble_graph_steps(lpic_ensemble_t ensemble, int nsteps, cudaStream_t stream);
+/* Synchronise; status bits of the ensemble and of every grid, cleared. */
+lpic_status lpic_ensemble_check_status(lpic_ensemble_t ensemble, cudaStream_t stream, unsigned *bits);
+/* Kernel launches issued by the ensemble so far. */
+lpic_status lpic_ensemble_launches(lpic_ensemble_t ensemble, long long *launches);
 
 /* Counting sort by cell tile of one FP32_FIXED particle buffer that allocates
  * nothing (the paper has no counterpart; it serves callers that cannot

@@ -13,6 +13,7 @@
 #include "lpic.h"
 #include "lpic_common.cuh"
 #include "lpic_diag.cuh"
+#include "lpic_ensemble.cuh"
 #include "lpic_field.cuh"
 #include "lpic_fp32.cuh"
 #include "lpic_fp64.cuh"
@@ -60,7 +61,10 @@ struct Species {
     int* d_coff = nullptr;       // ntiles + 1 work-item offsets
     int2* d_items = nullptr;     // work items (tile, chunk)
     int* d_nitems = nullptr;
+    int* d_esc = nullptr;        // particles beyond their tile's margin (capacity)
+    int* d_nesc = nullptr;
     long long item_cap = 0;
+    long long count0 = 0;        // particles at add time
     double wmax = 0;
     bool sorted = false;         // sorted at least once
     int since_sort = 1 << 30;    // pushes since the last sort
@@ -94,6 +98,7 @@ struct lpic_grid {
     long long launches = 0;
     int P = 4096;                              // particles per work item (FP32 path)
     int K = 1;                                 // sort interval (steps)
+    int SX = 0;                                // compile-time box row stride (2D), 0 = runtime
     int m[3] = {0, 0, 0};                      // drift margin of the tiles (cells)
     CellDecode dec{};
     FastDiv fT[3]{};
@@ -167,6 +172,24 @@ __global__ void k_absmax_f64(const double* w, const int* n, unsigned long long* 
     atomicMax(out, m);
 }
 
+template <int DIM, int ORDER>
+void (*pick_gpd(int SX))(GpdArgs) {
+    if constexpr (DIM == 2) {
+        if (SX == 32) return k_gpd32<2, ORDER, 32>;
+        if (SX == 64) return k_gpd32<2, ORDER, 64>;
+    }
+    return k_gpd32<DIM, ORDER, 0>;
+}
+
+template <int DIM, int ORDER>
+void (*pick_queue(int SX))(const GpdArgs*, const int*, const int*, int, int*) {
+    if constexpr (DIM == 2) {
+        if (SX == 32) return k_gpd32_queue<2, ORDER, 32>;
+        if (SX == 64) return k_gpd32_queue<2, ORDER, 64>;
+    }
+    return k_gpd32_queue<DIM, ORDER, 0>;
+}
+
 // tile-kernel instance and its dynamic shared memory
 template <int DIM, int ORDER>
 lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
@@ -178,18 +201,26 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_n
         LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (g->ntiles + 1), st));
         t.next_count = s.d_count;
     }
+    t.esc = s.d_esc;
+    t.nesc = s.d_nesc;
+    LPIC_CUDA(cudaMemsetAsync(s.d_nesc, 0, sizeof(int), st));
     t.start = s.d_start;
     t.items = s.d_items;
     t.nitems = s.d_nitems;
     t.P = g->P;
-    auto kern = k_gpd32<DIM, ORDER>;
+    auto kern = pick_gpd<DIM, ORDER>(g->SX);
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
-    kern<<<(unsigned)s.item_cap, 256, g->smem32, st>>>(
+    GpdArgs A{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
+              p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
+              (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status};
+    kern<<<(unsigned)s.item_cap, 256, g->smem32, st>>>(A);
+    LPIC_LAUNCHED("k_gpd32");
+    k_gpd32_escape<DIM, ORDER><<<2 * g->nsm, 256, 0, st>>>(
         g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
         p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
         (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status);
-    LPIC_LAUNCHED("k_gpd32");
+    LPIC_LAUNCHED("k_gpd32_escape");
     return LPIC_OK;
 }
 
@@ -204,8 +235,8 @@ lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
 }
 
 template <int DIM, int ORDER>
-cudaError_t set_smem_attrs(size_t bytes) {
-    return cudaFuncSetAttribute(k_gpd32<DIM, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t set_smem_attrs(size_t bytes, int SX) {
+    return cudaFuncSetAttribute(pick_gpd<DIM, ORDER>(SX), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)bytes);
 }
 
@@ -414,11 +445,30 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         const double hh[3] = {d.dx, d.dy, d.dim == 3 ? d.dz : 1.0};
         for (int k = 0; k < d.dim; ++k) g->m[k] = (int)std::ceil((g->K - 1) * d.dt / hh[k] - 1e-12);
     }
+    // box row stride: a compile-time 32 or 64 in 2D when the (margin-widened)
+    // tile fits, so shared-memory addresses fold into immediates
+    auto stride_for = [&](const int* m) {
+        const int w = g->T[0] + 2 * m[0] + 5;
+        return d.dim != 2 ? 0 : (w <= 32 ? 32 : (w <= 64 ? 64 : 0));
+    };
+    // shrink the margin until the tile's boxes fit in shared memory; particles
+    // that drift further take the global-memory path
+    auto smem_for = [&](const int* m) {
+        const int sx = stride_for(m);
+        long long G = 1, H = 1;
+        for (int k = 0; k < d.dim; ++k) {
+            G *= (k == 0 && sx) ? sx : g->T[k] + 2 * m[k] + 4;
+            H *= (k == 0 && sx) ? sx : g->T[k] + 2 * m[k] + 5;
+        }
+        return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 12;
+    };
+    while (smem_for(g->m) > 227 * 1024 && (g->m[0] > 0 || g->m[1] > 0 || g->m[2] > 0))
+        for (int k = 0; k < 3; ++k) g->m[k] = g->m[k] > 0 ? g->m[k] - 1 : 0;
     {
         const int D = d.dim;
-        long long G = 1, H = 1;
-        for (int k = 0; k < D; ++k) { G *= g->T[k] + 2 * g->m[k] + 4; H *= g->T[k] + 2 * g->m[k] + 5; }
-        g->smem32 = (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 12;
+        (void)D;
+        g->SX = stride_for(g->m);
+        g->smem32 = smem_for(g->m);
         if (d.precision == LPIC_FP32_FIXED && g->smem32 > 227 * 1024) {
             delete g;
             return fail(LPIC_EINVAL, "tile needs %zu bytes of shared memory (> 227 KB)", g->smem32);
@@ -443,8 +493,8 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         return fail(LPIC_ECUDA, "memset failed");
     }
     if (d.precision == LPIC_FP32_FIXED) {
-        cudaError_t e = d.dim == 2 ? (d.shape_order == 1 ? set_smem_attrs<2, 1>(g->smem32) : set_smem_attrs<2, 2>(g->smem32))
-                                   : (d.shape_order == 1 ? set_smem_attrs<3, 1>(g->smem32) : set_smem_attrs<3, 2>(g->smem32));
+        cudaError_t e = d.dim == 2 ? (d.shape_order == 1 ? set_smem_attrs<2, 1>(g->smem32, g->SX) : set_smem_attrs<2, 2>(g->smem32, g->SX))
+                                   : (d.shape_order == 1 ? set_smem_attrs<3, 1>(g->smem32, g->SX) : set_smem_attrs<3, 2>(g->smem32, g->SX));
         if (e != cudaSuccess) { lpic_destroy_grid(g); return fail(LPIC_ECUDA, "shared memory attribute: %s", cudaGetErrorString(e)); }
     }
     recompute_shift(g);
@@ -458,6 +508,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     for (auto& s : g->sp) {
         cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
         cudaFree(s.d_coff); cudaFree(s.d_items); cudaFree(s.d_nitems);
+        cudaFree(s.d_esc); cudaFree(s.d_nesc);
     }
     for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : g->ev) cudaEventDestroy(e);
@@ -493,7 +544,7 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
     if (!aligned(d.buffers[0], 256) || !aligned(d.buffers[1], 256))
         return fail(LPIC_EINVAL, "particle buffers must be 256-byte aligned");
     Species s;
-    s.q = d.q; s.m = d.m; s.cap = d.capacity;
+    s.q = d.q; s.m = d.m; s.cap = d.capacity; s.count0 = d.count;
     s.buf[0] = d.buffers[0]; s.buf[1] = d.buffers[1];
     const int nt = (int)g->ntiles;
     s.item_cap = nt + (d.capacity + g->P - 1) / g->P + 1;
@@ -503,9 +554,12 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
         cudaMalloc(&s.d_cursor, sizeof(int) * (nt + 1)) != cudaSuccess ||
         cudaMalloc(&s.d_coff, sizeof(int) * (nt + 1)) != cudaSuccess ||
         cudaMalloc(&s.d_items, sizeof(int2) * s.item_cap) != cudaSuccess ||
-        cudaMalloc(&s.d_nitems, sizeof(int) * 4) != cudaSuccess) {
+        cudaMalloc(&s.d_nitems, sizeof(int) * 4) != cudaSuccess ||
+        cudaMalloc(&s.d_esc, sizeof(int) * d.capacity) != cudaSuccess ||
+        cudaMalloc(&s.d_nesc, sizeof(int) * 4) != cudaSuccess) {
         cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
         cudaFree(s.d_coff); cudaFree(s.d_items); cudaFree(s.d_nitems);
+        cudaFree(s.d_esc); cudaFree(s.d_nesc);
         return fail(LPIC_ENOMEM, "species scratch allocation failed");
     }
     const int n = (int)d.count;
@@ -827,6 +881,308 @@ lpic_status lpic_check_status(lpic_grid_t g, cudaStream_t st, unsigned* bits) {
     LPIC_CUDA(cudaStreamSynchronize(st));
     if (bits) *bits = b;
     if (b) return fail(LPIC_EDEVICE, "device status bits 0x%x", b);
+    return LPIC_OK;
+}
+
+}  // extern "C"
+
+// ======================================================================= ensembles
+struct lpic_ensemble {
+    std::vector<lpic_grid_t> grids;
+    int dim = 2, order = 1, nsm = 148, blocks = 1, SX = 0;
+    int ninst = 0, nslots = 0;
+    size_t smem = 0;
+    EnsField* d_fields = nullptr;
+    EnsSort* d_sort = nullptr;
+    GpdArgs* d_args[2] = {nullptr, nullptr};
+    int* d_order = nullptr;
+    int* d_prefix = nullptr;
+    int* d_head = nullptr;
+    unsigned* d_status = nullptr;
+    std::vector<std::pair<int, int>> slots;     // (grid, species)
+    int parity = 0;
+    bool counted = false;                        // histograms hold the current cells
+    long long launches = 0;
+    long long max_ntiles = 1, max_field = 1, max_cap = 1;
+    std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, long long> graph_launches;
+};
+
+namespace {
+
+template <int DIM, int ORDER>
+cudaError_t ens_attrs(size_t bytes, int SX, const void** fn) {
+    auto k = pick_queue<DIM, ORDER>(SX);
+    *fn = reinterpret_cast<const void*>(k);
+    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <int DIM, int ORDER>
+lpic_status ens_push(lpic_ensemble* e, cudaStream_t st) {
+    lpic_ensemble* g = e;   // LPIC_LAUNCHED counts on g
+    pick_queue<DIM, ORDER>(e->SX)<<<e->blocks, 256, e->smem, st>>>(e->d_args[e->parity], e->d_order, e->d_prefix,
+                                                                 e->nslots, e->d_head);
+    LPIC_LAUNCHED("k_gpd32_queue");
+    return LPIC_OK;
+}
+
+lpic_status ens_step_impl(lpic_ensemble* e, cudaStream_t st) {
+    lpic_ensemble* g = e;
+    const dim3 fgrid((unsigned)std::min<long long>((e->max_field + 255) / 256, 1024), (unsigned)e->ninst);
+    const dim3 sgrid((unsigned)std::min<long long>((e->max_cap + 255) / 256, 512), (unsigned)e->nslots);
+    const dim3 tgrid((unsigned)std::min<long long>((e->max_ntiles + 255) / 256, 64), (unsigned)e->nslots);
+    if (e->dim == 3) k_update_E_many<3><<<fgrid, 256, 0, st>>>(e->d_fields);
+    else             k_update_E_many<2><<<fgrid, 256, 0, st>>>(e->d_fields);
+    LPIC_LAUNCHED("k_update_E_many");
+    if (e->dim == 3) k_update_B_many<3><<<fgrid, 256, 0, st>>>(e->d_fields);
+    else             k_update_B_many<2><<<fgrid, 256, 0, st>>>(e->d_fields);
+    LPIC_LAUNCHED("k_update_B_many");
+    k_zero_J_many<<<fgrid, 256, 0, st>>>(e->d_fields);
+    LPIC_LAUNCHED("k_zero_J_many");
+    // sort every slot from buffer `parity` into the other one
+    k_sort_zero_many<<<tgrid, 256, 0, st>>>(e->d_sort, e->counted ? 0 : 1);
+    LPIC_LAUNCHED("k_sort_zero_many");
+    if (!e->counted) {
+        k_sort_count_many<<<sgrid, 256, 0, st>>>(e->d_sort, e->parity);
+        LPIC_LAUNCHED("k_sort_count_many");
+    }
+    k_sort_scan_many<<<e->nslots, 1024, 0, st>>>(e->d_sort);
+    LPIC_LAUNCHED("k_sort_scan_many");
+    k_sort_items_many<<<tgrid, 256, 0, st>>>(e->d_sort);
+    LPIC_LAUNCHED("k_sort_items_many");
+    k_sort_scatter_many<<<sgrid, 256, 0, st>>>(e->d_sort, e->parity);
+    LPIC_LAUNCHED("k_sort_scatter_many");
+    k_sort_finalize_many<<<1, 256, 0, st>>>(e->d_sort, e->nslots);
+    LPIC_LAUNCHED("k_sort_finalize_many");
+    k_count_zero_many<<<tgrid, 256, 0, st>>>(e->d_sort);
+    LPIC_LAUNCHED("k_count_zero_many");
+    k_queue_prefix<<<1, 1024, 0, st>>>(e->d_sort, e->d_order, e->nslots, e->d_prefix, e->d_head);
+    LPIC_LAUNCHED("k_queue_prefix");
+    e->parity ^= 1;
+    lpic_status r;
+    if (e->dim == 2) r = e->order == 1 ? ens_push<2, 1>(e, st) : ens_push<2, 2>(e, st);
+    else             r = e->order == 1 ? ens_push<3, 1>(e, st) : ens_push<3, 2>(e, st);
+    if (r != LPIC_OK) return r;
+    k_check_escapes<<<1, 256, 0, st>>>(e->d_sort, e->nslots, e->d_status);
+    LPIC_LAUNCHED("k_check_escapes");
+    if (e->dim == 3) k_update_B_many<3><<<fgrid, 256, 0, st>>>(e->d_fields);
+    else             k_update_B_many<2><<<fgrid, 256, 0, st>>>(e->d_fields);
+    LPIC_LAUNCHED("k_update_B_many");
+    if (e->dim == 3) k_update_E_many<3><<<fgrid, 256, 0, st>>>(e->d_fields);
+    else             k_update_E_many<2><<<fgrid, 256, 0, st>>>(e->d_fields);
+    LPIC_LAUNCHED("k_update_E_many");
+    e->counted = true;
+    return LPIC_OK;
+}
+
+// the grids' own bookkeeping after an ensemble step (every species flipped)
+void ens_sync_grids(lpic_ensemble* e) {
+    for (auto& sl : e->slots) {
+        Species& s = e->grids[sl.first]->sp[sl.second];
+        s.cur = e->parity;
+        s.sorted = true;
+        s.since_sort = 1;
+        s.counts_fresh = true;
+        e->grids[sl.first]->started = true;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out) {
+    if (!grids || !out || n < 1) return fail(LPIC_EINVAL, "need at least one grid");
+    *out = nullptr;
+    const lpic_grid_t g0 = grids[0];
+    if (!g0) return fail(LPIC_EINVAL, "grid 0 is NULL");
+    for (int i = 0; i < n; ++i) {
+        const lpic_grid_t g = grids[i];
+        if (!g) return fail(LPIC_EINVAL, "grid %d is NULL", i);
+        if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "ensembles need the FP32 path");
+        if (g->d.dim != g0->d.dim || g->d.shape_order != g0->d.shape_order)
+            return fail(LPIC_EINVAL, "grid %d: dimension and shape order must match grid 0", i);
+        for (int k = 0; k < 3; ++k)
+            if (g->T[k] != g0->T[k]) return fail(LPIC_EINVAL, "grid %d: tile shape must match grid 0", i);
+        if (g->P != g0->P) return fail(LPIC_EINVAL, "grid %d: block_particles must match grid 0", i);
+        if (g->K != 1) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles sort every step (sort_interval <= 1)", i);
+        if (g->geo.absorb || g->laser.on) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles need periodic grids", i);
+        if (g->sp.empty()) return fail(LPIC_EINVAL, "grid %d has no species", i);
+        for (auto& s : g->sp)
+            if (s.cur != g0->sp[0].cur) return fail(LPIC_EINVAL, "grid %d: species buffer parity differs", i);
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == g) return fail(LPIC_EINVAL, "grid %d appears twice", i);
+    }
+    auto* e = new (std::nothrow) lpic_ensemble;
+    if (!e) return fail(LPIC_ENOMEM, "host allocation failed");
+    e->grids.assign(grids, grids + n);
+    e->dim = g0->d.dim; e->order = g0->d.shape_order; e->ninst = n; e->nsm = g0->nsm;
+    e->smem = g0->smem32;
+    e->SX = g0->SX;
+    e->parity = g0->sp[0].cur;
+    std::vector<EnsField> hf(n);
+    std::vector<EnsSort> hs;
+    std::vector<GpdArgs> ha[2];
+    std::vector<double> density;
+    for (int i = 0; i < n; ++i) {
+        lpic_grid* g = grids[i];
+        EnsField& f = hf[i];
+        f.g = g->geo;
+        for (int c = 0; c < 3; ++c) {
+            f.a.E[c] = static_cast<float*>(g->d.E[c]);
+            f.a.B[c] = static_cast<float*>(g->d.B[c]);
+            f.a.J[c] = static_cast<const long long*>(g->d.J[c]);
+            f.J[c] = static_cast<unsigned long long*>(g->d.J[c]);
+        }
+        const double tau = 0.5 * g->d.dt;
+        f.a.rdx = (float)(1.0 / g->d.dx); f.a.rdy = (float)(1.0 / g->d.dy);
+        f.a.rdz = (float)(g->d.dim == 3 ? 1.0 / g->d.dz : 0.0);
+        f.a.tau = (float)tau;
+        for (int c = 0; c < 3; ++c) f.a.jfac[c] = tau * g->jscale[c];
+        f.nfield = g->nfield;
+        e->max_field = std::max(e->max_field, g->nfield);
+        e->max_ntiles = std::max(e->max_ntiles, g->ntiles);
+        for (int sidx = 0; sidx < (int)g->sp.size(); ++sidx) {
+            Species& s = g->sp[sidx];
+            e->slots.push_back({i, sidx});
+            e->max_cap = std::max(e->max_cap, s.cap);
+            EnsSort so{};
+            for (int b = 0; b < 2; ++b) {
+                const P32 src = view32(g, s, b), dst = view32(g, s, 1 - b);
+                so.key[b] = KeyFP32{src.cell, g->dec, g->fT[0], g->fT[1], g->fT[2], g->nt[0], g->nt[1], (int)g->ntiles};
+                so.mv[b] = MoveFP32{src, dst, g->d.dim};
+                Tiles t{};
+                for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; t.m[d] = g->m[d]; t.fT[d] = g->fT[d]; }
+                t.start = s.d_start; t.items = s.d_items; t.nitems = s.d_nitems; t.P = g->P;
+                t.next_count = s.d_count; t.esc = s.d_esc; t.nesc = s.d_nesc;
+                // the push runs after the step's sort flipped the parity: it
+                // reads the buffer the particles were sorted into
+                const P32 pv = view32(g, s, b);
+                const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
+                const float sq = (float)std::ldexp(s.q, g->F);
+                ha[b].push_back(GpdArgs{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B),
+                                        ptr3<unsigned long long>(g->d.J), pv, t, g->dec, k, sq,
+                                        (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
+                                        (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status});
+            }
+            so.n = s.d_n; so.count = s.d_count; so.start = s.d_start; so.cursor = s.d_cursor;
+            so.coff = s.d_coff; so.items = s.d_items; so.nitems = s.d_nitems; so.nesc = s.d_nesc;
+            so.ntiles = (int)g->ntiles; so.P = g->P;
+            hs.push_back(so);
+            density.push_back((double)s.count0 / (double)((long long)g->d.nx * g->d.ny * g->geo.nz));
+        }
+    }
+    e->nslots = (int)hs.size();
+    // queue order: densest slots first (their work items are the fullest)
+    std::vector<int> order(e->nslots);
+    for (int i = 0; i < e->nslots; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return density[a] > density[b]; });
+    auto cleanup = [&](lpic_status st, const char* msg) { lpic_destroy_ensemble(e); return fail(st, "%s", msg); };
+    if (cudaMalloc(&e->d_fields, sizeof(EnsField) * n) != cudaSuccess ||
+        cudaMalloc(&e->d_sort, sizeof(EnsSort) * e->nslots) != cudaSuccess ||
+        cudaMalloc(&e->d_args[0], sizeof(GpdArgs) * e->nslots) != cudaSuccess ||
+        cudaMalloc(&e->d_args[1], sizeof(GpdArgs) * e->nslots) != cudaSuccess ||
+        cudaMalloc(&e->d_order, sizeof(int) * e->nslots) != cudaSuccess ||
+        cudaMalloc(&e->d_prefix, sizeof(int) * (e->nslots + 1)) != cudaSuccess ||
+        cudaMalloc(&e->d_head, 64) != cudaSuccess ||
+        cudaMalloc(&e->d_status, 64) != cudaSuccess)
+        return cleanup(LPIC_ENOMEM, "ensemble table allocation failed");
+    if (cudaMemcpy(e->d_fields, hf.data(), sizeof(EnsField) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_sort, hs.data(), sizeof(EnsSort) * e->nslots, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_args[0], ha[0].data(), sizeof(GpdArgs) * e->nslots, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_args[1], ha[1].data(), sizeof(GpdArgs) * e->nslots, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(e->d_order, order.data(), sizeof(int) * e->nslots, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(e->d_status, 0, 64) != cudaSuccess)
+        return cleanup(LPIC_ECUDA, "ensemble table upload failed");
+    const void* fn = nullptr;
+    cudaError_t ce = e->dim == 2 ? (e->order == 1 ? ens_attrs<2, 1>(e->smem, e->SX, &fn) : ens_attrs<2, 2>(e->smem, e->SX, &fn))
+                                 : (e->order == 1 ? ens_attrs<3, 1>(e->smem, e->SX, &fn) : ens_attrs<3, 2>(e->smem, e->SX, &fn));
+    if (ce != cudaSuccess) return cleanup(LPIC_ECUDA, "queue kernel shared memory attribute failed");
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, e->smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    e->blocks = per_sm * e->nsm;
+    e->counted = false;     // the first step counts the tile keys itself
+    *out = e;
+    return LPIC_OK;
+}
+
+lpic_status lpic_destroy_ensemble(lpic_ensemble_t e) {
+    if (!e) return LPIC_OK;
+    cudaDeviceSynchronize();
+    for (auto& kv : e->graphs) cudaGraphExecDestroy(kv.second);
+    cudaFree(e->d_fields); cudaFree(e->d_sort); cudaFree(e->d_args[0]); cudaFree(e->d_args[1]);
+    cudaFree(e->d_order); cudaFree(e->d_prefix); cudaFree(e->d_head); cudaFree(e->d_status);
+    delete e;
+    return LPIC_OK;
+}
+
+lpic_status lpic_ensemble_step(lpic_ensemble_t e, cudaStream_t st) {
+    if (!e) return fail(LPIC_EINVAL, "ensemble is NULL");
+    if (lpic_status r = ens_step_impl(e, st)) return r;
+    ens_sync_grids(e);
+    return LPIC_OK;
+}
+
+lpic_status lpic_ensemble_graph_steps(lpic_ensemble_t e, int nsteps, cudaStream_t st) {
+    if (!e) return fail(LPIC_EINVAL, "ensemble is NULL");
+    if (nsteps < 0) return fail(LPIC_EINVAL, "nsteps must be >= 0");
+    if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
+        return fail(LPIC_EINVAL, "graph capture needs a created (non-default) stream");
+    for (int k = 0; k < nsteps; ++k) {
+        const int key = e->parity | (e->counted ? 2 : 0);
+        auto it = e->graphs.find(key);
+        if (it == e->graphs.end()) {
+            const int parity0 = e->parity;
+            const bool counted0 = e->counted;
+            const long long l0 = e->launches;
+            LPIC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            lpic_status r = ens_step_impl(e, st);
+            cudaGraph_t graph = nullptr;
+            cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            e->parity = parity0; e->counted = counted0;
+            const long long per = e->launches - l0;
+            e->launches = l0;
+            if (r != LPIC_OK) { if (graph) cudaGraphDestroy(graph); return r; }
+            if (ce != cudaSuccess) return fail(LPIC_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+            cudaGraphExec_t exec = nullptr;
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ce != cudaSuccess) return fail(LPIC_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+            e->graphs[key] = exec;
+            e->graph_launches[key] = per;
+            it = e->graphs.find(key);
+        }
+        LPIC_CUDA(cudaGraphLaunch(it->second, st));
+        e->launches += e->graph_launches[key];
+        e->parity ^= 1;
+        e->counted = true;
+        ens_sync_grids(e);
+    }
+    return LPIC_OK;
+}
+
+lpic_status lpic_ensemble_check_status(lpic_ensemble_t e, cudaStream_t st, unsigned* bits) {
+    if (!e) return fail(LPIC_EINVAL, "ensemble is NULL");
+    unsigned b = 0;
+    LPIC_CUDA(cudaMemcpyAsync(&b, e->d_status, 4, cudaMemcpyDeviceToHost, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    for (auto g : e->grids) {
+        unsigned gb = 0;
+        LPIC_CUDA(cudaMemcpyAsync(&gb, g->d_status, 4, cudaMemcpyDeviceToHost, st));
+        LPIC_CUDA(cudaStreamSynchronize(st));
+        b |= gb;
+        LPIC_CUDA(cudaMemsetAsync(g->d_status, 0, 4, st));
+    }
+    LPIC_CUDA(cudaMemsetAsync(e->d_status, 0, 4, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    if (bits) *bits = b;
+    if (b) return fail(LPIC_EDEVICE, "device status bits 0x%x", b);
+    return LPIC_OK;
+}
+
+lpic_status lpic_ensemble_launches(lpic_ensemble_t e, long long* launches) {
+    if (!e || !launches) return fail(LPIC_EINVAL, "NULL argument");
+    *launches = e->launches;
     return LPIC_OK;
 }
 

@@ -24,10 +24,9 @@ struct FieldArgs {
 };
 
 template <int DIM, typename R, typename JT>
-__global__ void k_update_E(Geo g, FieldArgs<R, JT> a) {
+__device__ inline void update_E_range(const Geo& g, const FieldArgs<R, JT>& a, long long n0, long long step) {
     const long long total = (long long)g.fx * g.ny * (DIM == 3 ? g.nz : 1);
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total;
-         n += (long long)gridDim.x * blockDim.x) {
+    for (long long n = n0; n < total; n += step) {
         const int i = (int)(n % g.fx);
         const long long r = n / g.fx;
         const int j = (int)(r % g.ny);
@@ -58,10 +57,9 @@ __global__ void k_update_E(Geo g, FieldArgs<R, JT> a) {
 }
 
 template <int DIM, typename R, typename JT>
-__global__ void k_update_B(Geo g, FieldArgs<R, JT> a) {
+__device__ inline void update_B_range(const Geo& g, const FieldArgs<R, JT>& a, long long n0, long long step) {
     const long long total = (long long)g.fx * g.ny * (DIM == 3 ? g.nz : 1);
-    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < total;
-         n += (long long)gridDim.x * blockDim.x) {
+    for (long long n = n0; n < total; n += step) {
         const int i = (int)(n % g.fx);
         const long long r = n / g.fx;
         const int j = (int)(r % g.ny);
@@ -88,6 +86,16 @@ __global__ void k_update_B(Geo g, FieldArgs<R, JT> a) {
             a.B[2][n] -= a.tau * cz;
         }
     }
+}
+
+template <int DIM, typename R, typename JT>
+__global__ void k_update_E(Geo g, FieldArgs<R, JT> a) {
+    update_E_range<DIM>(g, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
+}
+
+template <int DIM, typename R, typename JT>
+__global__ void k_update_B(Geo g, FieldArgs<R, JT> a) {
+    update_B_range<DIM>(g, a, blockIdx.x * (long long)blockDim.x + threadIdx.x, (long long)gridDim.x * blockDim.x);
 }
 
 // Save E_y, E_z on planes i = 0, 1, nx-1, nx before the E update:

@@ -62,6 +62,8 @@ struct Tiles {
     int P;               // particles per chunk
     FastDiv fT[3];       // division by T (tile keys of the next sort)
     int* next_count;     // if set: histogram of the new tile keys for the next sort
+    int* esc;            // indices of particles beyond the tile's margin ...
+    int* nesc;           // ... and their count (pushed by k_gpd32_escape)
 };
 
 template <int ORDER, class W>
@@ -74,12 +76,11 @@ __device__ inline void place32(float (&S)[ORDER + 2], const W& w, int off) {
     }
 }
 
-// Adds a lane's value to the int32 round box with a native 32-bit atomic.
+// Adds a lane's value to the int32 round box with a native 32-bit atomic
+// (zeros included: a predicated branch per value costs more than the add).
 struct Acc32 {
     int* sJ;
-    __device__ inline void operator()(int idx, int v) const {
-        if (v != 0) atomicAdd(sJ + idx, v);
-    }
+    __device__ inline void operator()(int idx, int v) const { atomicAdd(sJ + idx, v); }
 };
 
 // Hierarchical integer charge of one stencil placed in a window of WN nodes
@@ -181,14 +182,14 @@ __device__ inline void deposit2d(const Acc& acc, int jsz, int H0, const int* lc,
         }
     }
     // J_z: s v_z W_z, W_z = A_x A_y + DS_x DS_y / 12 (needs no closure in 2D)
-    const float svz = s * vz;
+    const float svz = s * vz, svz12 = svz * (1.0f / 12.0f);
 #pragma unroll
-    for (int a = 0; a < WN; ++a)
+    for (int a = 0; a < WN; ++a) {
+        const float pa = svz * Ax[a], qa = svz12 * DSx[a];
 #pragma unroll
-        for (int b = 0; b < WN; ++b) {
-            const float wz = Ax[a] * Ay[b] + DSx[a] * DSy[b] * (1.0f / 12.0f);
-            acc(2 * jsz + (basey + b + 2) * H0 + (basex + a + 2), rint22(svz * wz));
-        }
+        for (int b = 0; b < WN; ++b)
+            acc(2 * jsz + (basey + b + 2) * H0 + (basex + a + 2), rint22(pa * Ay[b] + qa * DSy[b]));
+    }
 }
 
 // ----------------------------------------------------------- 3D deposit
@@ -360,13 +361,34 @@ __device__ inline void charge_int(unsigned long long* rho, const Geo& g, const i
 #define LPIC_GPD3D_MINB 1
 #endif
 
-template <int DIM, int ORDER>
-__global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB) k_gpd32(Geo g, Ptr3<const float> E, Ptr3<const float> B,
-                                               Ptr3<unsigned long long> J, P32 p, Tiles t,
-                                               CellDecode dec, float k, float sq, float dth0,
-                                               float dth1, float dth2, unsigned* st) {
-    if ((int)blockIdx.x >= *t.nitems) return;
-    const int2 item = t.items[blockIdx.x];
+// Everything the fused kernel needs for one species of one grid.
+struct GpdArgs {
+    Geo g;
+    Ptr3<const float> E, B;
+    Ptr3<unsigned long long> J;
+    P32 p;
+    Tiles t;
+    CellDecode dec;
+    float k, sq, dth0, dth1, dth2;
+    unsigned* st;
+};
+
+// One work item (a tile, or a chunk of a crowded tile) of one species.
+// SX > 0: the row stride of the field and current boxes is the compile-time
+// SX (boxes padded), so shared-memory addresses fold into immediates.
+template <int DIM, int ORDER, int SX>
+__device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float4* smem4) {
+    const Geo& g = A.g;
+    const Ptr3<const float>& E = A.E;
+    const Ptr3<const float>& B = A.B;
+    const Ptr3<unsigned long long>& J = A.J;
+    const P32& p = A.p;
+    const Tiles& t = A.t;
+    const CellDecode& dec = A.dec;
+    const float k = A.k, sq = A.sq, dth0 = A.dth0, dth1 = A.dth1, dth2 = A.dth2;
+    unsigned* st = A.st;
+
+    const int2 item = t.items[item_index];
     const int tile = item.x;
     const int tbeg = t.start[tile], tend = t.start[tile + 1];
     const int beg = tbeg + item.y * t.P;
@@ -377,10 +399,10 @@ __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_M
     const int t0[3] = {(tile % t.nt[0]) * t.T[0] - t.m[0], ((tile / t.nt[0]) % t.nt[1]) * t.T[1] - t.m[1],
                        DIM == 3 ? (tile / (t.nt[0] * t.nt[1])) * t.T[2] - t.m[2] : 0};
     const int Te[3] = {t.T[0] + 2 * t.m[0], t.T[1] + 2 * t.m[1], t.T[2] + 2 * t.m[2]};
-    const int G0 = Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
-    const int H0 = Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
+    const int G0 = SX ? SX : Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
+    const int H0 = SX ? SX : Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
+    const int gw = Te[0] + 4;     // used width of a field-box row
     const int fsz = G0 * G1 * G2, jsz = H0 * H1 * H2;
-    extern __shared__ float4 smem4[];
     float* sF = reinterpret_cast<float*>(smem4);
     long long* sJ = reinterpret_cast<long long*>(sF + ((6 * fsz + 3) & ~3));
     int* sR = reinterpret_cast<int*>(sJ + 3 * jsz);
@@ -388,7 +410,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_M
     for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
         const int c = idx / fsz, r = idx - c * fsz;
         const int lx = r % G0, ly = (r / G0) % G1, lz = r / (G0 * G1);
-        const long long m = fidx(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
+        const long long m = (lx < gw) ? fidx(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0) : -1;
         const float* src = c == 0 ? E.p[0] : c == 1 ? E.p[1] : c == 2 ? E.p[2]
                          : c == 3 ? B.p[0] : c == 4 ? B.p[1] : B.p[2];
         sF[idx] = (m < 0) ? 0.0f : src[m];
@@ -420,7 +442,10 @@ __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_M
                 inside &= (lc[d] >= 0 && lc[d] < Te[d]);
             }
             if (!inside) {
-                set_status(st, LPIC_ST_HALO);
+                // beyond the tile's drift margin: queued for the global-memory
+                // path, which also counts its new tile key
+                t.esc[atomicAdd(t.nesc, 1)] = i;
+                cell_out = -1;
             } else {
                 float f[3] = {p.off[0][i], p.off[1][i], DIM == 3 ? p.off[2][i] : 0.0f};
                 float ux = p.u[0][i], uy = p.u[1][i], uz = p.u[2][i];
@@ -535,6 +560,178 @@ __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_M
         atomicAdd(dst + m, static_cast<unsigned long long>(v));
     }
     if (outside) set_status(st, LPIC_ST_OUTSIDE);
+}
+
+
+template <int DIM, int ORDER, int SX>
+__global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB) k_gpd32(GpdArgs A) {
+    extern __shared__ float4 smem4[];
+    if ((int)blockIdx.x >= *A.t.nitems) return;
+    gpd_item<DIM, ORDER, SX>(A, blockIdx.x, smem4);
+}
+
+// Persistent form for a batch of grids: blocks pull work items from one
+// device queue that runs over the species slots in the given order (densest
+// first), slots[order[r]] owning queue entries prefix[r] .. prefix[r+1]-1.
+template <int DIM, int ORDER, int SX>
+__global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB)
+k_gpd32_queue(const GpdArgs* slots, const int* order, const int* prefix, int nslots, int* head) {
+    extern __shared__ float4 smem4[];
+    __shared__ int s_q;
+    const int total = prefix[nslots];
+    for (;;) {
+        if (threadIdx.x == 0) s_q = atomicAdd(head, 1);
+        __syncthreads();
+        const int q = s_q;
+        __syncthreads();
+        if (q >= total) break;
+        int lo = 0, hi = nslots;             // prefix[lo] <= q < prefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (prefix[mid] <= q) lo = mid; else hi = mid;
+        }
+        gpd_item<DIM, ORDER, SX>(slots[order[lo]], q - prefix[lo], smem4);
+        __syncthreads();
+    }
+}
+
+// Accumulates a deposit straight into the global int64 J.  The deposit's box
+// index is read in a virtual box of HV nodes per dimension whose local frame
+// puts the particle's cell at 2: box coordinate X is global node gc + X - 4.
+template <int DIM>
+struct AccGlobal {
+    static constexpr int HV = 10;
+    const Geo* g;
+    Ptr3<unsigned long long> J;
+    int gc[3];
+    unsigned* st;
+    __device__ inline void operator()(int idx, int v) const {
+        if (v == 0) return;
+        constexpr int jsz = (DIM == 3) ? HV * HV * HV : HV * HV;
+        const int c = idx / jsz, r = idx - c * jsz;
+        const int X = r % HV, Y = (r / HV) % HV, Z = r / (HV * HV);
+        const long long m = fidx(*g, gc[0] + X - 4, gc[1] + Y - 4, DIM == 3 ? gc[2] + Z - 4 : 0);
+        if (m < 0) { set_status(st, LPIC_ST_OUTSIDE); return; }
+        unsigned long long* dst = c == 0 ? J.p[0] : c == 1 ? J.p[1] : J.p[2];
+        atomicAdd(dst + m, static_cast<unsigned long long>(static_cast<long long>(v)));
+    }
+};
+
+// The same push for the particles the tile kernel queued: fields gathered from
+// global memory, current added with global integer atomics (same integer
+// quantisation, so the result is identical to the shared-memory path).
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(256) k_gpd32_escape(Geo g, Ptr3<const float> E, Ptr3<const float> B,
+                                                      Ptr3<unsigned long long> J, P32 p, Tiles t,
+                                                      CellDecode dec, float k, float sq, float dth0,
+                                                      float dth1, float dth2, unsigned* st) {
+    const int nesc = *t.nesc;
+    const float dth[3] = {dth0, dth1, dth2};
+    const int stride = gridDim.x * blockDim.x;
+    const int nround = (nesc + stride - 1) / stride;
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int r = 0; r < nround; ++r, j += stride) {
+        int cell_out = -1;
+        if (j < nesc) {
+            const int i = t.esc[j];
+            int gc[3];
+            dec(p.cell[i], gc);
+            if (DIM == 2) gc[2] = 0;
+            float f[3] = {p.off[0][i], p.off[1][i], DIM == 3 ? p.off[2][i] : 0.0f};
+            float ux = p.u[0][i], uy = p.u[1][i], uz = p.u[2][i];
+            const float w = p.w[i];
+            // local frame with the particle's cell at 2 (lc = 2)
+            int lc[3] = {2, 2, DIM == 3 ? 2 : 0};
+            const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
+            const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
+            float fld[6];
+            bool outside = false;
+#pragma unroll
+            for (int comp = 0; comp < 6; ++comp) {
+                const bool hx = (comp == 0 || comp == 4 || comp == 5);
+                const bool hy = (comp == 1 || comp == 3 || comp == 5);
+                const bool hz = (comp == 2 || comp == 3 || comp == 4);
+                const int bx = hx ? hx_.base : nx_.base, by = hy ? hy_.base : ny_.base;
+                const int bz = (DIM == 3) ? (hz ? hz_.base : nz_.base) : 0;
+                const float* F = comp == 0 ? E.p[0] : comp == 1 ? E.p[1] : comp == 2 ? E.p[2]
+                               : comp == 3 ? B.p[0] : comp == 4 ? B.p[1] : B.p[2];
+                float accv = 0.0f;
+#pragma unroll
+                for (int c = 0; c < (DIM == 3 ? ORDER + 1 : 1); ++c) {
+                    const float wzv = (DIM == 3) ? (hz ? hz_.w[c] : nz_.w[c]) : 1.0f;
+#pragma unroll
+                    for (int b = 0; b <= ORDER; ++b) {
+                        const float wyz = (hy ? hy_.w[b] : ny_.w[b]) * wzv;
+#pragma unroll
+                        for (int a = 0; a <= ORDER; ++a) {
+                            const long long m = fidx(g, gc[0] + bx + a - 2, gc[1] + by + b - 2,
+                                                     DIM == 3 ? gc[2] + bz + c - 2 : 0);
+                            if (m < 0) { outside = true; continue; }
+                            accv += F[m] * ((hx ? hx_.w[a] : nx_.w[a]) * wyz);
+                        }
+                    }
+                }
+                fld[comp] = accv;
+            }
+            if (outside) set_status(st, LPIC_ST_OUTSIDE);
+            boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
+            if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
+                set_status(st, LPIC_ST_NAN);
+                p.cell[i] = -1;
+            } else {
+                const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
+                const float uu[3] = {ux, uy, uz};
+                int ce[3] = {lc[0], lc[1], lc[2]};
+                float fe[3] = {0.0f, 0.0f, 0.0f};
+                bool cfl = false;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) {
+                    const float dl = uu[d] * ig * dth[d];
+                    cfl |= !(fabsf(dl) < 1.0f);
+                    const float fr = f[d] + dl;
+                    int carry = (int)floorf(fr);
+                    float fn = fr - (float)carry;
+                    if (fn >= 1.0f) { fn -= 1.0f; carry += 1; }
+                    ce[d] = lc[d] + carry;
+                    fe[d] = fn;
+                }
+                if (cfl) {
+                    set_status(st, LPIC_ST_CFL);
+                    p.cell[i] = -1;
+                } else {
+                    const AccGlobal<DIM> acc{&g, J, {gc[0], gc[1], gc[2]}, st};
+                    constexpr int HV = AccGlobal<DIM>::HV;
+                    const float s = sq * w;
+                    if (DIM == 3) deposit3d<ORDER>(acc, HV * HV * HV, HV, HV, lc, f, ce, fe, s);
+                    else          deposit2d<ORDER>(acc, HV * HV, HV, lc, f, ce, fe, s, uz * ig);
+                    int ng[3];
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) ng[d] = (d < DIM) ? gc[d] + ce[d] - lc[d] : 0;
+                    bool dead = false;
+                    if (g.absorb) dead = (ng[0] < 2 || ng[0] >= g.nx - 2);
+                    else ng[0] = wrapi(ng[0], g.nx);
+                    ng[1] = wrapi(ng[1], g.ny);
+                    if (DIM == 3) ng[2] = wrapi(ng[2], g.nz);
+                    cell_out = dead ? -1 : (ng[2] * g.ny + ng[1]) * g.nx + ng[0];
+                    p.cell[i] = cell_out;
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) p.off[d][i] = fe[d];
+                    p.u[0][i] = ux; p.u[1][i] = uy; p.u[2][i] = uz;
+                }
+            }
+        }
+        if (t.next_count) {
+            int key = -1;
+            if (cell_out >= 0) {
+                int gc2[3];
+                dec(cell_out, gc2);
+                key = (fdiv(gc2[2], t.fT[2]) * t.nt[1] + fdiv(gc2[1], t.fT[1])) * t.nt[0] + fdiv(gc2[0], t.fT[0]);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(t.next_count + key, __popc(peers));
+        }
+    }
 }
 
 // x^0 -> x^{1/2}: offsets advance by (dt/2) v / h with carries into the cell.

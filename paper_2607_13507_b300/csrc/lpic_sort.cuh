@@ -45,12 +45,9 @@ struct KeyFP64 {
 __device__ inline unsigned lane_id() { return threadIdx.x & 31; }
 
 template <class Key>
-__global__ void k_sort_count(Key key, const int* n_ptr, int* count) {
-    const int n = *n_ptr;
-    const int stride = gridDim.x * blockDim.x;
+__device__ inline void sort_count_body(const Key& key, int n, int* count, int i, int stride) {
     // every lane of a warp runs the same number of iterations
     const int nround = (n + stride - 1) / stride;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     for (int r = 0; r < nround; ++r, i += stride) {
         const bool valid = i < n;
         const int k = valid ? key(i) : -1;
@@ -58,6 +55,11 @@ __global__ void k_sort_count(Key key, const int* n_ptr, int* count) {
         const int leader = __ffs(peers) - 1;
         if (valid && (int)lane_id() == leader) atomicAdd(count + k, __popc(peers));
     }
+}
+
+template <class Key>
+__global__ void k_sort_count(Key key, const int* n_ptr, int* count) {
+    sort_count_body(key, *n_ptr, count, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
 }
 
 // Exclusive block-wide scan of f(0..len) into out[0..len], out[len] = total.
@@ -146,12 +148,9 @@ struct MoveFP64 {
 };
 
 template <class Key, class Move>
-__global__ void k_sort_scatter(Key key, Move mv, const int* n_ptr, const int* start, int* cursor,
-                               int ntiles) {
-    const int n = *n_ptr;
-    const int stride = gridDim.x * blockDim.x;
+__device__ inline void sort_scatter_body(const Key& key, const Move& mv, int n, const int* start,
+                                         int* cursor, int ntiles, int i, int stride) {
     const int nround = (n + stride - 1) / stride;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
     for (int r = 0; r < nround; ++r, i += stride) {
         const bool valid = i < n;
         const int k = valid ? key(i) : -1;
@@ -165,6 +164,13 @@ __global__ void k_sort_scatter(Key key, Move mv, const int* n_ptr, const int* st
             mv(i, start[k] + base + rank);
         }
     }
+}
+
+template <class Key, class Move>
+__global__ void k_sort_scatter(Key key, Move mv, const int* n_ptr, const int* start, int* cursor,
+                               int ntiles) {
+    sort_scatter_body(key, mv, *n_ptr, start, cursor, ntiles, blockIdx.x * blockDim.x + threadIdx.x,
+                      gridDim.x * blockDim.x);
 }
 
 static __global__ void k_sort_finalize(const int* start, int ntiles, int* n_out) {

@@ -28,7 +28,9 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_deposit_charge", "lpic_positions_at_step", "lpic_diagnostics",
            "lpic_grid_get_info", "lpic_check_status", "lpic_last_error", "lpic_set_clock",
            "lpic_graph_steps", "lpic_sort_tiles_static", "lpic_kernel_timing",
-           "lpic_kernel_time"]
+           "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
+           "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
+           "lpic_ensemble_launches"]
 
 
 class LpicError(RuntimeError):
@@ -95,6 +97,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_set_clock.argtypes = [vp, ctypes.c_double, st]
     lib.lpic_graph_steps.argtypes = [vp, i, st]
     lib.lpic_kernel_timing.argtypes = [vp, i]
+    lib.lpic_create_ensemble.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+    lib.lpic_destroy_ensemble.argtypes = [vp]
+    lib.lpic_ensemble_step.argtypes = [vp, st]
+    lib.lpic_ensemble_graph_steps.argtypes = [vp, i, st]
+    lib.lpic_ensemble_check_status.argtypes = [vp, st, ctypes.POINTER(ctypes.c_uint)]
+    lib.lpic_ensemble_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     lib.lpic_kernel_time.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
     lib.lpic_sort_tiles_static.argtypes = [i, i, i, i, ctypes.POINTER(i), vp, vp, ctypes.c_longlong,
                                            vp, vp, vp, st]
@@ -339,6 +347,47 @@ class Grid:
             return [j.clone() for j in self.J]
         inf = self.info()
         return [self.J[c].to(torch.float64) * inf.j_scale[c] for c in range(3)]
+
+
+class Ensemble:
+    """Independent grids stepped together (batched kernels, one persistent
+    particle kernel with a device work queue)."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.h_.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(load().lpic_create_ensemble(arr, len(self.grids), ctypes.byref(h)))
+        self.h_ = h
+
+    def close(self):
+        if getattr(self, "h_", None):
+            load().lpic_destroy_ensemble(self.h_)
+            self.h_ = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, stream=None):
+        _check(load().lpic_ensemble_step(self.h_, _stream(stream)))
+
+    def graph_steps(self, nsteps, stream=None):
+        _check(load().lpic_ensemble_graph_steps(self.h_, int(nsteps), _stream(stream)))
+
+    def check_status(self, stream=None) -> int:
+        bits = ctypes.c_uint()
+        rc = load().lpic_ensemble_check_status(self.h_, _stream(stream), ctypes.byref(bits))
+        if rc not in (0, 4):
+            _check(rc)
+        return bits.value
+
+    def launches(self) -> int:
+        n = ctypes.c_longlong()
+        _check(load().lpic_ensemble_launches(self.h_, ctypes.byref(n)))
+        return n.value
 
 
 def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, sort_interval=0) -> Grid:
