@@ -39,6 +39,9 @@ WORKLOADS = {
     "thermal3d": ("3D3V periodic thermal plasma 256^3, 8 electrons/cell (134M), v_th=0.05c, TSC, "
                   "FP32 cell+offset positions, int64 fixed-point deposit", 0),
     "thermal2d": ("2D3V periodic thermal plasma 64x64, 16 electrons/cell, v_th=0.01c, CIC", 0),
+    "ensemble": ("96 independent 2D3V periodic plasmas in one ensemble (batched kernels, persistent "
+                 "work-queue particle kernel, one CUDA graph per step): sides 128-768, 4-64 "
+                 "particles/cell, v_th 0.005-0.1c, CIC, FP32 + fixed point", 0),
 }
 
 
@@ -301,6 +304,80 @@ def run_b300(args, rank, world, local_rank):
     return result, state
 
 
+def run_ensemble(args, rank, world, local_rank):
+    """The batched ensemble: every step of all members is one replay of the
+    captured ensemble step (batched field and sort kernels, one persistent
+    particle kernel over the device work queue)."""
+    import torch
+    from paper_2607_13507_b300 import build, lpic
+    from paper_2607_13507_b300 import workloads as W
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    members = W.ensemble(count=args.ensemble_count, seed=W.SEED_BASE + 4000 + 97 * rank)
+    grids, counts, loaded = [], 0, 0
+    for wl in members:
+        parts = W.load_all(wl)
+        G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(16, 8), device=dev)
+        G.add_species(parts[0], stream=stream)
+        counts += parts[0].n
+        loaded += parts[0].n // wl.species[0].ppc
+        grids.append(G)
+        del parts
+    ens = lpic.Ensemble(grids)
+    ens.graph_steps(args.warmup, stream)
+    stream.synchronize()
+    if ens.check_status(stream) != 0:
+        raise SystemExit("device status bits set during warm-up")
+    if world > 1:
+        torch.distributed.barrier()
+    clock = ClockSampler(local_rank)
+    clock.start()
+    time.sleep(0.3)
+    l0 = ens.launches()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    ens.graph_steps(args.steps, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    elapsed = a.elapsed_time(b) / 1e3
+    clocks = clock.stop()
+    if ens.check_status(stream) != 0:
+        raise SystemExit("device status bits set during the timed steps")
+    n_now = sum(G.species[0].query(stream)[1] for G in grids)
+    psteps = 0.5 * (counts + n_now) * args.steps
+    if world > 1:
+        t = torch.tensor([elapsed, psteps], dtype=torch.float64, device=dev)
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        elapsed, psteps = float(mx[0]), float(t[1])
+    if rank != 0:
+        return None
+    peaks, which = measured_peaks()
+    wl0 = members[0]
+    per_ps = algorithmic_bytes(wl0, 1, 0, "fp32")[1]
+    step_bytes = counts * per_ps + loaded * algorithmic_bytes(wl0, 0, 1, "fp32")[2]
+    achieved = step_bytes / (elapsed / args.steps) / 1e9
+    return {
+        "metric": "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)",
+        "value": psteps / elapsed, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (int64 fixed-point current)",
+        "data": "synthetic (seeded Philox initial conditions)",
+        "config": {"workload": WORKLOADS["ensemble"][0], "members": len(members),
+                   "particles": int(counts), "l2": "inputs larger than L2",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "kernel": "whole ensemble step", "achieved": achieved,
+                     "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
+                     "frac": achieved / float(peaks["hbm_gbs"]), "peak_source": f"{which} hbm_gbs",
+                     "traffic": None},
+        "gpu_launches": int(ens.launches() - l0), "clocks": clocks,
+    }
+
+
 def run_e2e(args, st):
     """Same metric through host buffers: every step copies the state (particle
     buffers and fields) from pinned host memory to the device, runs the step,
@@ -409,6 +486,7 @@ def main():
     ap.add_argument("--pre-steps", type=int, default=None,
                     help="untimed steps before warm-up (default: bring the laser onto the target)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ensemble-count", type=int, default=96)
     ap.add_argument("--tile", default=None, help="tile shape, e.g. 8x8")
     ap.add_argument("--block-particles", type=int, default=0)
     ap.add_argument("--sort-interval", type=int, default=0)
@@ -439,6 +517,14 @@ def main():
     if world > 1:
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if args.workload == "ensemble":
+        res = run_ensemble(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
     res, state = run_b300(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_e2e:

@@ -98,7 +98,6 @@ struct lpic_grid {
     long long launches = 0;
     int P = 4096;                              // particles per work item (FP32 path)
     int K = 1;                                 // sort interval (steps)
-    int SX = 0;                                // compile-time box row stride (2D), 0 = runtime
     int m[3] = {0, 0, 0};                      // drift margin of the tiles (cells)
     CellDecode dec{};
     FastDiv fT[3]{};
@@ -172,24 +171,6 @@ __global__ void k_absmax_f64(const double* w, const int* n, unsigned long long* 
     atomicMax(out, m);
 }
 
-template <int DIM, int ORDER>
-void (*pick_gpd(int SX))(GpdArgs) {
-    if constexpr (DIM == 2) {
-        if (SX == 32) return k_gpd32<2, ORDER, 32>;
-        if (SX == 64) return k_gpd32<2, ORDER, 64>;
-    }
-    return k_gpd32<DIM, ORDER, 0>;
-}
-
-template <int DIM, int ORDER>
-void (*pick_queue(int SX))(const GpdArgs*, const int*, const int*, int, int*) {
-    if constexpr (DIM == 2) {
-        if (SX == 32) return k_gpd32_queue<2, ORDER, 32>;
-        if (SX == 64) return k_gpd32_queue<2, ORDER, 64>;
-    }
-    return k_gpd32_queue<DIM, ORDER, 0>;
-}
-
 // tile-kernel instance and its dynamic shared memory
 template <int DIM, int ORDER>
 lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
@@ -208,7 +189,7 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_n
     t.items = s.d_items;
     t.nitems = s.d_nitems;
     t.P = g->P;
-    auto kern = pick_gpd<DIM, ORDER>(g->SX);
+    auto kern = k_gpd32<DIM, ORDER>;
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
     GpdArgs A{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
@@ -235,8 +216,8 @@ lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
 }
 
 template <int DIM, int ORDER>
-cudaError_t set_smem_attrs(size_t bytes, int SX) {
-    return cudaFuncSetAttribute(pick_gpd<DIM, ORDER>(SX), cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t set_smem_attrs(size_t bytes) {
+    return cudaFuncSetAttribute(k_gpd32<DIM, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)bytes);
 }
 
@@ -445,21 +426,11 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         const double hh[3] = {d.dx, d.dy, d.dim == 3 ? d.dz : 1.0};
         for (int k = 0; k < d.dim; ++k) g->m[k] = (int)std::ceil((g->K - 1) * d.dt / hh[k] - 1e-12);
     }
-    // box row stride: a compile-time 32 or 64 in 2D when the (margin-widened)
-    // tile fits, so shared-memory addresses fold into immediates
-    auto stride_for = [&](const int* m) {
-        const int w = g->T[0] + 2 * m[0] + 5;
-        return d.dim != 2 ? 0 : (w <= 32 ? 32 : (w <= 64 ? 64 : 0));
-    };
     // shrink the margin until the tile's boxes fit in shared memory; particles
     // that drift further take the global-memory path
     auto smem_for = [&](const int* m) {
-        const int sx = stride_for(m);
         long long G = 1, H = 1;
-        for (int k = 0; k < d.dim; ++k) {
-            G *= (k == 0 && sx) ? sx : g->T[k] + 2 * m[k] + 4;
-            H *= (k == 0 && sx) ? sx : g->T[k] + 2 * m[k] + 5;
-        }
+        for (int k = 0; k < d.dim; ++k) { G *= g->T[k] + 2 * m[k] + 4; H *= g->T[k] + 2 * m[k] + 5; }
         return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 12;
     };
     while (smem_for(g->m) > 227 * 1024 && (g->m[0] > 0 || g->m[1] > 0 || g->m[2] > 0))
@@ -467,7 +438,6 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     {
         const int D = d.dim;
         (void)D;
-        g->SX = stride_for(g->m);
         g->smem32 = smem_for(g->m);
         if (d.precision == LPIC_FP32_FIXED && g->smem32 > 227 * 1024) {
             delete g;
@@ -493,8 +463,8 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         return fail(LPIC_ECUDA, "memset failed");
     }
     if (d.precision == LPIC_FP32_FIXED) {
-        cudaError_t e = d.dim == 2 ? (d.shape_order == 1 ? set_smem_attrs<2, 1>(g->smem32, g->SX) : set_smem_attrs<2, 2>(g->smem32, g->SX))
-                                   : (d.shape_order == 1 ? set_smem_attrs<3, 1>(g->smem32, g->SX) : set_smem_attrs<3, 2>(g->smem32, g->SX));
+        cudaError_t e = d.dim == 2 ? (d.shape_order == 1 ? set_smem_attrs<2, 1>(g->smem32) : set_smem_attrs<2, 2>(g->smem32))
+                                   : (d.shape_order == 1 ? set_smem_attrs<3, 1>(g->smem32) : set_smem_attrs<3, 2>(g->smem32));
         if (e != cudaSuccess) { lpic_destroy_grid(g); return fail(LPIC_ECUDA, "shared memory attribute: %s", cudaGetErrorString(e)); }
     }
     recompute_shift(g);
@@ -889,7 +859,7 @@ lpic_status lpic_check_status(lpic_grid_t g, cudaStream_t st, unsigned* bits) {
 // ======================================================================= ensembles
 struct lpic_ensemble {
     std::vector<lpic_grid_t> grids;
-    int dim = 2, order = 1, nsm = 148, blocks = 1, SX = 0;
+    int dim = 2, order = 1, nsm = 148, blocks = 1;
     int ninst = 0, nslots = 0;
     size_t smem = 0;
     EnsField* d_fields = nullptr;
@@ -911,17 +881,16 @@ struct lpic_ensemble {
 namespace {
 
 template <int DIM, int ORDER>
-cudaError_t ens_attrs(size_t bytes, int SX, const void** fn) {
-    auto k = pick_queue<DIM, ORDER>(SX);
-    *fn = reinterpret_cast<const void*>(k);
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+cudaError_t ens_attrs(size_t bytes, const void** fn) {
+    *fn = reinterpret_cast<const void*>(k_gpd32_queue<DIM, ORDER>);
+    return cudaFuncSetAttribute(k_gpd32_queue<DIM, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <int DIM, int ORDER>
 lpic_status ens_push(lpic_ensemble* e, cudaStream_t st) {
     lpic_ensemble* g = e;   // LPIC_LAUNCHED counts on g
-    pick_queue<DIM, ORDER>(e->SX)<<<e->blocks, 256, e->smem, st>>>(e->d_args[e->parity], e->d_order, e->d_prefix,
-                                                                 e->nslots, e->d_head);
+    k_gpd32_queue<DIM, ORDER><<<e->blocks, 256, e->smem, st>>>(e->d_args[e->parity], e->d_order, e->d_prefix,
+                                                            e->nslots, e->d_head);
     LPIC_LAUNCHED("k_gpd32_queue");
     return LPIC_OK;
 }
@@ -1018,7 +987,6 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
     e->grids.assign(grids, grids + n);
     e->dim = g0->d.dim; e->order = g0->d.shape_order; e->ninst = n; e->nsm = g0->nsm;
     e->smem = g0->smem32;
-    e->SX = g0->SX;
     e->parity = g0->sp[0].cur;
     std::vector<EnsField> hf(n);
     std::vector<EnsSort> hs;
@@ -1095,8 +1063,8 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
         cudaMemset(e->d_status, 0, 64) != cudaSuccess)
         return cleanup(LPIC_ECUDA, "ensemble table upload failed");
     const void* fn = nullptr;
-    cudaError_t ce = e->dim == 2 ? (e->order == 1 ? ens_attrs<2, 1>(e->smem, e->SX, &fn) : ens_attrs<2, 2>(e->smem, e->SX, &fn))
-                                 : (e->order == 1 ? ens_attrs<3, 1>(e->smem, e->SX, &fn) : ens_attrs<3, 2>(e->smem, e->SX, &fn));
+    cudaError_t ce = e->dim == 2 ? (e->order == 1 ? ens_attrs<2, 1>(e->smem, &fn) : ens_attrs<2, 2>(e->smem, &fn))
+                                 : (e->order == 1 ? ens_attrs<3, 1>(e->smem, &fn) : ens_attrs<3, 2>(e->smem, &fn));
     if (ce != cudaSuccess) return cleanup(LPIC_ECUDA, "queue kernel shared memory attribute failed");
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, e->smem) != cudaSuccess || per_sm < 1) per_sm = 1;

@@ -76,11 +76,17 @@ __device__ inline void place32(float (&S)[ORDER + 2], const W& w, int off) {
     }
 }
 
-// Adds a lane's value to the int32 round box with a native 32-bit atomic
-// (zeros included: a predicated branch per value costs more than the add).
+// Adds a lane's value to the int32 round box with a native 32-bit atomic.
+// SKIP_ZERO: only nonzero values (2D: slowly moving particles leave most
+// window values at zero and lanes of one cell would otherwise all hit the same
+// addresses; 3D: most values are nonzero and the test costs more than it saves
+// -- both measured).
+template <bool SKIP_ZERO>
 struct Acc32 {
     int* sJ;
-    __device__ inline void operator()(int idx, int v) const { atomicAdd(sJ + idx, v); }
+    __device__ inline void operator()(int idx, int v) const {
+        if (!SKIP_ZERO || v != 0) atomicAdd(sJ + idx, v);
+    }
 };
 
 // Hierarchical integer charge of one stencil placed in a window of WN nodes
@@ -110,19 +116,18 @@ __device__ inline void charge_levels_2d(const int (&qx)[WN], const float (&Sy)[W
 }
 
 // ----------------------------------------------------------- 2D deposit
-// lc/f: start cell (relative to the tile origin) and offset; ce/fe: end.
-// Node (a, b) of component c lives at c * jsz + (b + 2) * H0 + (a + 2).
-template <int ORDER, class Acc>
-__device__ inline void deposit2d(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
-                                 const int* ce, const float* fe, float s, float vz) {
-    constexpr int WN = ORDER + 2;
-    const NodeW<ORDER> ax(lc[0], f[0]), ay(lc[1], f[1]), bx(ce[0], fe[0]), by(ce[1], fe[1]);
-    const int basex = min(ax.base, bx.base), basey = min(ay.base, by.base);
-    const int o0x = ax.base - basex, o1x = bx.base - basex;
-    const int o0y = ay.base - basey, o1y = by.base - basey;
-    float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
-    place32<ORDER>(S0x, ax, o0x); place32<ORDER>(S1x, bx, o1x);
-    place32<ORDER>(S0y, ay, o0y); place32<ORDER>(S1y, by, o1y);
+// The construction on a window of WN nodes per dimension starting at
+// (basex, basey); the start/end stencils sit at offsets o0*/o1* in it.
+// Node (a, b) of component c lives at c * jsz + (b + 2) * H0 + (a + 2) of the
+// box (coordinates relative to the box's local frame).
+// The rounding residuals of W_x go to row cx and column cy: the stencil's
+// last node where both stencils coincide in that dimension (so that the
+// window size never changes the integers), else the window's last node.
+template <int ORDER, int WN, class Acc>
+__device__ inline void deposit2d_core(const Acc& acc, int jsz, int H0, int basex, int basey, int o0x,
+                                      int o1x, int o0y, int o1y, int cx, int cy,
+                                      const float (&S0x)[WN], const float (&S1x)[WN],
+                                      const float (&S0y)[WN], const float (&S1y)[WN], float s, float vz) {
     const int sint = rint22(s);
     int qx0[WN], qx1[WN], dQ[WN][WN], M[WN];
     {
@@ -145,22 +150,29 @@ __device__ inline void deposit2d(const Acc& acc, int jsz, int H0, const int* lc,
         DSx[a] = S1x[a] - S0x[a]; DSy[a] = S1y[a] - S0y[a];
         Ax[a] = 0.5f * (S0x[a] + S1x[a]); Ay[a] = 0.5f * (S0y[a] + S1y[a]);
     }
-    // W_x with closures; W_y = dQ - W_x
+    // W_x with closures on row cx and column cy; W_y = dQ - W_x
     int Wx[WN][WN];
 #pragma unroll
-    for (int a = 0; a < WN - 1; ++a) {
+    for (int a = 0; a < WN; ++a) {
         int row = 0;
         const float sdx = s * DSx[a];
 #pragma unroll
-        for (int b = 0; b < WN - 1; ++b) { Wx[a][b] = rint22(sdx * Ay[b]); row += Wx[a][b]; }
-        Wx[a][WN - 1] = M[a] - row;
+        for (int b = 0; b < WN; ++b) {
+            const int v = (b == cy) ? 0 : rint22(sdx * Ay[b]);
+            Wx[a][b] = v; row += v;
+        }
+#pragma unroll
+        for (int b = 0; b < WN; ++b)
+            if (b == cy) Wx[a][b] = M[a] - row;
     }
 #pragma unroll
     for (int b = 0; b < WN; ++b) {
         int col = 0;
 #pragma unroll
-        for (int a = 0; a < WN - 1; ++a) col += Wx[a][b];
-        Wx[WN - 1][b] = -col;
+        for (int a = 0; a < WN; ++a) col += (a == cx) ? 0 : Wx[a][b];
+#pragma unroll
+        for (int a = 0; a < WN; ++a)
+            if (a == cx) Wx[a][b] = -col;
     }
     // J_x: running sum along a; J_y: running sum along b
 #pragma unroll
@@ -190,6 +202,44 @@ __device__ inline void deposit2d(const Acc& acc, int jsz, int H0, const int* lc,
         for (int b = 0; b < WN; ++b)
             acc(2 * jsz + (basey + b + 2) * H0 + (basex + a + 2), rint22(pa * Ay[b] + qa * DSy[b]));
     }
+}
+
+// General case: the window of ORDER + 2 nodes holds both stencils.
+template <int ORDER, class Acc>
+__device__ inline void deposit2d(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
+                                 const int* ce, const float* fe, float s, float vz) {
+    constexpr int WN = ORDER + 2;
+    const NodeW<ORDER> ax(lc[0], f[0]), ay(lc[1], f[1]), bx(ce[0], fe[0]), by(ce[1], fe[1]);
+    const int basex = min(ax.base, bx.base), basey = min(ay.base, by.base);
+    const int o0x = ax.base - basex, o1x = bx.base - basex;
+    const int o0y = ay.base - basey, o1y = by.base - basey;
+    float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
+    place32<ORDER>(S0x, ax, o0x); place32<ORDER>(S1x, bx, o1x);
+    place32<ORDER>(S0y, ay, o0y); place32<ORDER>(S1y, by, o1y);
+    const int cx = (o0x == o1x) ? o0x + ORDER : WN - 1;
+    const int cy = (o0y == o1y) ? o0y + ORDER : WN - 1;
+    deposit2d_core<ORDER, WN>(acc, jsz, H0, basex, basey, o0x, o1x, o0y, o1y, cx, cy, S0x, S1x, S0y, S1y,
+                              s, vz);
+}
+
+// Both stencils start at the same node in both dimensions (the particle kept
+// its nearest node): the window is the stencil itself, ORDER + 1 nodes.
+template <int ORDER, class Acc>
+__device__ inline void deposit2d_same(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
+                                      const int* ce, const float* fe, float s, float vz) {
+    constexpr int WN = ORDER + 1;
+    const NodeW<ORDER> ax(lc[0], f[0]), ay(lc[1], f[1]), bx(ce[0], fe[0]), by(ce[1], fe[1]);
+    float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
+#pragma unroll
+    for (int a = 0; a < WN; ++a) { S0x[a] = ax.w[a]; S1x[a] = bx.w[a]; S0y[a] = ay.w[a]; S1y[a] = by.w[a]; }
+    deposit2d_core<ORDER, WN>(acc, jsz, H0, ax.base, ay.base, 0, 0, 0, 0, ORDER, ORDER, S0x, S1x, S0y, S1y,
+                              s, vz);
+}
+
+template <int ORDER>
+__device__ inline bool same_stencils2d(const int* lc, const float* f, const int* ce, const float* fe) {
+    return NodeW<ORDER>(lc[0], f[0]).base == NodeW<ORDER>(ce[0], fe[0]).base &&
+           NodeW<ORDER>(lc[1], f[1]).base == NodeW<ORDER>(ce[1], fe[1]).base;
 }
 
 // ----------------------------------------------------------- 3D deposit
@@ -353,12 +403,13 @@ __device__ inline void charge_int(unsigned long long* rho, const Geo& g, const i
 // Shared memory: 6 field boxes (T+4 per dimension, halo 2 below and 2 above),
 // an int32 round box and an int64 total box for J (T+5 per dimension).
 // Blocks per SM the register allocation targets (2D: the kernel fits 80
-// registers with negligible spills; 3D TSC needs the full register file).
+// registers with negligible spills; 3D: 128 registers, a few spills, measured
+// 1.57x faster than one block per SM at 255 registers).
 #ifndef LPIC_GPD2D_MINB
 #define LPIC_GPD2D_MINB 3
 #endif
 #ifndef LPIC_GPD3D_MINB
-#define LPIC_GPD3D_MINB 1
+#define LPIC_GPD3D_MINB 2
 #endif
 
 // Everything the fused kernel needs for one species of one grid.
@@ -374,9 +425,7 @@ struct GpdArgs {
 };
 
 // One work item (a tile, or a chunk of a crowded tile) of one species.
-// SX > 0: the row stride of the field and current boxes is the compile-time
-// SX (boxes padded), so shared-memory addresses fold into immediates.
-template <int DIM, int ORDER, int SX>
+template <int DIM, int ORDER>
 __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float4* smem4) {
     const Geo& g = A.g;
     const Ptr3<const float>& E = A.E;
@@ -399,9 +448,8 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     const int t0[3] = {(tile % t.nt[0]) * t.T[0] - t.m[0], ((tile / t.nt[0]) % t.nt[1]) * t.T[1] - t.m[1],
                        DIM == 3 ? (tile / (t.nt[0] * t.nt[1])) * t.T[2] - t.m[2] : 0};
     const int Te[3] = {t.T[0] + 2 * t.m[0], t.T[1] + 2 * t.m[1], t.T[2] + 2 * t.m[2]};
-    const int G0 = SX ? SX : Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
-    const int H0 = SX ? SX : Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
-    const int gw = Te[0] + 4;     // used width of a field-box row
+    const int G0 = Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
+    const int H0 = Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
     const int fsz = G0 * G1 * G2, jsz = H0 * H1 * H2;
     float* sF = reinterpret_cast<float*>(smem4);
     long long* sJ = reinterpret_cast<long long*>(sF + ((6 * fsz + 3) & ~3));
@@ -410,7 +458,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
         const int c = idx / fsz, r = idx - c * fsz;
         const int lx = r % G0, ly = (r / G0) % G1, lz = r / (G0 * G1);
-        const long long m = (lx < gw) ? fidx(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0) : -1;
+        const long long m = fidx(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
         const float* src = c == 0 ? E.p[0] : c == 1 ? E.p[1] : c == 2 ? E.p[2]
                          : c == 3 ? B.p[0] : c == 4 ? B.p[1] : B.p[2];
         sF[idx] = (m < 0) ? 0.0f : src[m];
@@ -419,7 +467,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     __syncthreads();
 
     const float dth[3] = {dth0, dth1, dth2};
-    const Acc32 acc{sR};
+    const Acc32<DIM == 2> acc{sR};
     const int nround = (end - beg + blockDim.x - 1) / blockDim.x;
     for (int rnd = 0; rnd < nround; ++rnd) {
         const int i = beg + rnd * blockDim.x + threadIdx.x;
@@ -506,8 +554,16 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                         cell_out = -1;
                     } else {
                         const float s = sq * w;
-                        if (DIM == 3) deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
-                        else          deposit2d<ORDER>(acc, jsz, H0, lc, f, ce, fe, s, uz * ig);
+                        if (DIM == 3) {
+                            deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
+                        } else {
+                            // the stencil-sized window when every converged lane allows it
+                            const bool same = same_stencils2d<ORDER>(lc, f, ce, fe);
+                            if (__all_sync(__activemask(), same))
+                                deposit2d_same<ORDER>(acc, jsz, H0, lc, f, ce, fe, s, uz * ig);
+                            else
+                                deposit2d<ORDER>(acc, jsz, H0, lc, f, ce, fe, s, uz * ig);
+                        }
                         // store x^{n+3/2} and u^{n+1}
                         int ng[3];
 #pragma unroll
@@ -563,17 +619,17 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 }
 
 
-template <int DIM, int ORDER, int SX>
+template <int DIM, int ORDER>
 __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB) k_gpd32(GpdArgs A) {
     extern __shared__ float4 smem4[];
     if ((int)blockIdx.x >= *A.t.nitems) return;
-    gpd_item<DIM, ORDER, SX>(A, blockIdx.x, smem4);
+    gpd_item<DIM, ORDER>(A, blockIdx.x, smem4);
 }
 
 // Persistent form for a batch of grids: blocks pull work items from one
 // device queue that runs over the species slots in the given order (densest
 // first), slots[order[r]] owning queue entries prefix[r] .. prefix[r+1]-1.
-template <int DIM, int ORDER, int SX>
+template <int DIM, int ORDER>
 __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB)
 k_gpd32_queue(const GpdArgs* slots, const int* order, const int* prefix, int nslots, int* head) {
     extern __shared__ float4 smem4[];
@@ -590,7 +646,7 @@ k_gpd32_queue(const GpdArgs* slots, const int* order, const int* prefix, int nsl
             const int mid = (lo + hi) >> 1;
             if (prefix[mid] <= q) lo = mid; else hi = mid;
         }
-        gpd_item<DIM, ORDER, SX>(slots[order[lo]], q - prefix[lo], smem4);
+        gpd_item<DIM, ORDER>(slots[order[lo]], q - prefix[lo], smem4);
         __syncthreads();
     }
 }

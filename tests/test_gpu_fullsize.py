@@ -1,0 +1,119 @@
+"""Long runs and the full-size benchmark workload.
+
+* The plain 2D thermal plasma (64 x 64, 16 per cell, CIC) for its full 200
+  steps: the total-energy history of the GPU paths follows the oracle's
+  within 1 % of the initial energy at every sample (PIC is chaotic, so long
+  runs are compared on histories, not element by element).
+* The 2D laser-plasma at full size (2048 x 1024, 67 M particles, TSC, FP32
+  fixed point): a random sample of particles pushed by the oracle in the
+  GPU's own fields agrees with the GPU push to float32 precision, and the
+  integer continuity identity holds exactly on the whole grid.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2607_13507_b300 import workloads as W
+
+from pic_cases import gpu_case, oracle_case
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2607_13507_b300 import build, lpic
+    build.build()
+    lpic.load()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_energy_history_200_steps(precision):
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d()                       # 64 x 64, 16 per cell, 200 steps
+    parts = W.load_all(wl)
+    g, sps = oracle_case(wl, parts)
+    G = gpu_case(wl, parts, lpic.FP64 if precision == "fp64" else lpic.FP32_FIXED)
+    e0 = None
+    hist_g, hist_o = [], []
+    for s in range(wl.steps + 1):
+        if s % 10 == 0:
+            torch.cuda.synchronize()
+            d = G.diagnostics()
+            ek, ef, _ = O.energy(g, sps)
+            hist_g.append(d.kinetic + d.field)
+            hist_o.append(ek + ef)
+            if e0 is None:
+                e0 = ek + ef
+        if s < wl.steps:
+            O.step(g, sps, s * wl.dt)
+            G.step(s * wl.dt)
+    hist_g, hist_o = np.array(hist_g), np.array(hist_o)
+    assert np.max(np.abs(hist_g - hist_o)) < 0.01 * e0
+    # the heating itself (finite-grid instability at dx = 10 Debye lengths)
+    # must be reproduced, not just the initial energy
+    dg, do = hist_g - hist_g[0], hist_o - hist_o[0]
+    assert np.max(np.abs(dg - do)) < 0.01 * max(np.max(np.abs(do)), 1e-3 * e0)
+    assert G.check_status() == 0
+
+
+def test_laser2d_full_size_sampled_push_and_exact_continuity():
+    from paper_2607_13507_b300 import lpic
+    wl = W.laser2d()
+    parts = W.load_all(wl)
+    G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(16, 8), block_particles=8192)
+    for p in parts:
+        G.add_species(p)
+    del parts
+    for s in range(3):
+        G.step(s * wl.dt)
+    # state at the start of step 3: fields after its first half step
+    t3 = 3 * wl.dt
+    G.maxwell_half(0, t3)
+    G.zero_current()
+    sp = G.species[0]
+    G.sort(sp.id)
+    st = sp.state()
+    rng = np.random.Generator(np.random.Philox(5))
+    pick = rng.choice(st["id"].shape[0], size=2000, replace=False)
+    ids = st["id"][pick]
+    rho0 = sp.charge()
+    # the oracle push of the sample in the GPU's fields
+    g = O.Grid(2, wl.n, wl.h, wl.dt, wl.order, absorb_x=True)
+    for c in range(3):
+        g.E[c][...] = G.E[c].cpu().numpy().astype(np.float64)
+        g.B[c][...] = G.B[c].cpu().numpy().astype(np.float64)
+    h = np.array(wl.h)[:, None]
+    u = st["u"][:, pick].astype(np.float64)
+    gam = np.sqrt(1.0 + (u ** 2).sum(0))
+    xh = (st["cell"][pick] % wl.n[0], st["cell"][pick] // wl.n[0])
+    x_half = (np.stack(xh).astype(np.float64) + st["off"][:, pick].astype(np.float64)) * h
+    x_int = x_half - 0.5 * wl.dt * u[:2] / gam
+    osp = O.Species(-1.0, 1.0, x_int, u, st["w"][pick].astype(np.float64))
+    O.push_species(g, osp)
+    # the GPU push of all particles
+    G.gather_push_deposit(sp.id)
+    torch.cuda.synchronize()
+    assert G.check_status() == 0
+    st1 = sp.state()
+    x1 = sp.positions_at_step()
+    where = {int(i): k for k, i in enumerate(st1["id"])}
+    rows = np.array([where[int(i)] for i in ids])
+    ug = st1["u"][:, rows].astype(np.float64)
+    rel = np.linalg.norm(ug - osp.u) / np.linalg.norm(osp.u)
+    assert rel < 1e-5, rel
+    diff = x1[:, rows] - osp.x[:2]
+    Ly = wl.n[1] * wl.h[1]
+    diff[1] = np.remainder(diff[1] + 0.5 * Ly, Ly) - 0.5 * Ly      # periodic y
+    dx = np.abs(diff) / h
+    assert np.max(dx) < 1e-5, np.max(dx)
+    # exact integer continuity over the whole grid (absorbing x: interior columns)
+    rho1 = sp.charge()
+    J = G.J
+    div = (J[0] - torch.roll(J[0], 1, 2)) + (J[1] - torch.roll(J[1], 1, 1))
+    res = (rho1 - rho0 + div)[:, :, 4:-4]
+    assert torch.count_nonzero(res).item() == 0
