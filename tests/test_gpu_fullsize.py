@@ -101,8 +101,9 @@ def test_laser2d_full_size_sampled_push_and_exact_continuity():
     assert G.check_status() == 0
     st1 = sp.state()
     x1 = sp.positions_at_step()
-    where = {int(i): k for k, i in enumerate(st1["id"])}
-    rows = np.array([where[int(i)] for i in ids])
+    order = np.argsort(st1["id"])
+    rows = order[np.searchsorted(st1["id"][order], ids)]
+    assert np.array_equal(st1["id"][rows], ids)
     ug = st1["u"][:, rows].astype(np.float64)
     rel = np.linalg.norm(ug - osp.u) / np.linalg.norm(osp.u)
     assert rel < 1e-5, rel
