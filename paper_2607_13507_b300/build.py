@@ -13,7 +13,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib", "liblpic.so")
-SOURCES = [os.path.join(CSRC, "lpic_api.cu"), os.path.join(CSRC, "lpic_noalloc.cu")]
+SOURCES = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -39,14 +39,32 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         if all(os.path.getmtime(f) <= t for f in _deps()):
             return OUT
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    tmp = OUT + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--shared", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-o", tmp, *SOURCES,
-           *(extra or [])]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
-    os.replace(tmp, OUT)
+    tag = f"tmp{os.getpid()}"
+    objdir = os.path.join(os.path.dirname(OUT), "obj." + tag)
+    os.makedirs(objdir, exist_ok=True)
+    try:
+        # one translation unit per process (the tile-kernel instances are the
+        # long ones), then one link
+        objs, procs = [], []
+        for src in SOURCES:
+            obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
+            cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                   "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-c", src, "-o", obj, *(extra or [])]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            objs.append(obj)
+            procs.append((src, subprocess.Popen(cmd)))
+        failed = [src for src, p in procs if p.wait() != 0]
+        if failed:
+            raise subprocess.CalledProcessError(1, "nvcc " + " ".join(os.path.basename(f) for f in failed))
+        tmp = OUT + "." + tag
+        cmd = [nvcc(), *ARCH, "--shared", "-o", tmp, *objs]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        subprocess.check_call(cmd)
+        os.replace(tmp, OUT)
+    finally:
+        shutil.rmtree(objdir, ignore_errors=True)
     return OUT
 
 

@@ -17,6 +17,7 @@
 #include "lpic_field.cuh"
 #include "lpic_fp32.cuh"
 #include "lpic_fp64.cuh"
+#include "lpic_gpd32.h"
 #include "lpic_sort.cuh"
 
 using namespace lpic;
@@ -189,18 +190,14 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_n
     t.items = s.d_items;
     t.nitems = s.d_nitems;
     t.P = g->P;
-    auto kern = k_gpd32<DIM, ORDER>;
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
     GpdArgs A{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
               p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
               (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status};
-    kern<<<(unsigned)s.item_cap, 256, g->smem32, st>>>(A);
+    Gpd32<DIM, ORDER>::tile(A, (unsigned)s.item_cap, g->smem32, st);
     LPIC_LAUNCHED("k_gpd32");
-    k_gpd32_escape<DIM, ORDER><<<2 * g->nsm, 256, 0, st>>>(
-        g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
-        p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
-        (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status);
+    Gpd32<DIM, ORDER>::escape(A, (unsigned)(2 * g->nsm), st);
     LPIC_LAUNCHED("k_gpd32_escape");
     return LPIC_OK;
 }
@@ -217,8 +214,7 @@ lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
 
 template <int DIM, int ORDER>
 cudaError_t set_smem_attrs(size_t bytes) {
-    return cudaFuncSetAttribute(k_gpd32<DIM, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)bytes);
+    return Gpd32<DIM, ORDER>::set_smem(bytes);
 }
 
 // clock != nullptr: the laser time is read from the device clock plus t.
@@ -431,7 +427,7 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     auto smem_for = [&](const int* m) {
         long long G = 1, H = 1;
         for (int k = 0; k < d.dim; ++k) { G *= g->T[k] + 2 * m[k] + 4; H *= g->T[k] + 2 * m[k] + 5; }
-        return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)(3 * H) * 12;
+        return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)((3 * H + 3) & ~3LL) * 12 + (d.dim == 3 ? (size_t)kStageBytes : 0);
     };
     while (smem_for(g->m) > 227 * 1024 && (g->m[0] > 0 || g->m[1] > 0 || g->m[2] > 0))
         for (int k = 0; k < 3; ++k) g->m[k] = g->m[k] > 0 ? g->m[k] - 1 : 0;
@@ -882,15 +878,15 @@ namespace {
 
 template <int DIM, int ORDER>
 cudaError_t ens_attrs(size_t bytes, const void** fn) {
-    *fn = reinterpret_cast<const void*>(k_gpd32_queue<DIM, ORDER>);
-    return cudaFuncSetAttribute(k_gpd32_queue<DIM, ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    *fn = Gpd32<DIM, ORDER>::queue_fn();
+    return Gpd32<DIM, ORDER>::set_smem(bytes);
 }
 
 template <int DIM, int ORDER>
 lpic_status ens_push(lpic_ensemble* e, cudaStream_t st) {
     lpic_ensemble* g = e;   // LPIC_LAUNCHED counts on g
-    k_gpd32_queue<DIM, ORDER><<<e->blocks, 256, e->smem, st>>>(e->d_args[e->parity], e->d_order, e->d_prefix,
-                                                            e->nslots, e->d_head);
+    Gpd32<DIM, ORDER>::queue(e->d_args[e->parity], e->d_order, e->d_prefix, e->nslots, e->d_head,
+                             (unsigned)e->blocks, e->smem, st);
     LPIC_LAUNCHED("k_gpd32_queue");
     return LPIC_OK;
 }

@@ -67,6 +67,11 @@ struct CellDecode {
 __device__ inline int rint22(float x) {
     return __float_as_int(__fadd_rn(x, 12582912.0f)) - 0x4B400000;
 }
+// rint(a * b) with one rounding: the product is formed exactly inside the
+// fused multiply-add, so this is the nearest integer to the exact a * b.
+__device__ inline int rint22_mul(float a, float b) {
+    return __float_as_int(__fmaf_rn(a, b, 12582912.0f)) - 0x4B400000;
+}
 
 __device__ inline void set_status(unsigned* st, unsigned bit) { atomicOr(st, bit); }
 

@@ -96,7 +96,7 @@ template <int WN>
 __device__ inline void charge_levels_1d(float s, int S, const float (&Sx)[WN], int o, int (&qx)[WN]) {
     int sum = 0;
 #pragma unroll
-    for (int a = 0; a < WN; ++a) { qx[a] = rint22(__fmul_rn(s, Sx[a])); sum += qx[a]; }
+    for (int a = 0; a < WN; ++a) { qx[a] = rint22_mul(s, Sx[a]); sum += qx[a]; }
 #pragma unroll
     for (int a = 0; a < WN; ++a) qx[a] += (a == o + 1) ? S - sum : 0;
 }
@@ -109,7 +109,7 @@ __device__ inline void charge_levels_2d(const int (&qx)[WN], const float (&Sy)[W
         int sum = 0;
         const float fa = (float)qx[a];
 #pragma unroll
-        for (int b = 0; b < WN; ++b) { qxy[a][b] = rint22(__fmul_rn(fa, Sy[b])); sum += qxy[a][b]; }
+        for (int b = 0; b < WN; ++b) { qxy[a][b] = rint22_mul(fa, Sy[b]); sum += qxy[a][b]; }
 #pragma unroll
         for (int b = 0; b < WN; ++b) qxy[a][b] += (b == o + 1) ? qx[a] - sum : 0;
     }
@@ -158,7 +158,7 @@ __device__ inline void deposit2d_core(const Acc& acc, int jsz, int H0, int basex
         const float sdx = s * DSx[a];
 #pragma unroll
         for (int b = 0; b < WN; ++b) {
-            const int v = (b == cy) ? 0 : rint22(sdx * Ay[b]);
+            const int v = (b == cy) ? 0 : rint22_mul(sdx, Ay[b]);
             Wx[a][b] = v; row += v;
         }
 #pragma unroll
@@ -193,14 +193,19 @@ __device__ inline void deposit2d_core(const Acc& acc, int jsz, int H0, int basex
             acc(jsz + (basey + b + 2) * H0 + (basex + a + 2), run);
         }
     }
-    // J_z: s v_z W_z, W_z = A_x A_y + DS_x DS_y / 12 (needs no closure in 2D)
+    // J_z: s v_z W_z, W_z = A_x A_y + DS_x DS_y / 12 (needs no closure in 2D,
+    // so any fixed integer rounding of it will do: the DS term is rounded to an
+    // integer first, then the sum)
     const float svz = s * vz, svz12 = svz * (1.0f / 12.0f);
 #pragma unroll
     for (int a = 0; a < WN; ++a) {
         const float pa = svz * Ax[a], qa = svz12 * DSx[a];
 #pragma unroll
-        for (int b = 0; b < WN; ++b)
-            acc(2 * jsz + (basey + b + 2) * H0 + (basex + a + 2), rint22(pa * Ay[b] + qa * DSy[b]));
+        for (int b = 0; b < WN; ++b) {
+            const float t = __fmaf_rn(qa, DSy[b], 12582912.0f);
+            acc(2 * jsz + (basey + b + 2) * H0 + (basex + a + 2),
+                __float_as_int(__fmaf_rn(pa, Ay[b], t)) - 0x4B400000);
+        }
     }
 }
 
@@ -236,37 +241,28 @@ __device__ inline void deposit2d_same(const Acc& acc, int jsz, int H0, const int
                               s, vz);
 }
 
-template <int ORDER>
-__device__ inline bool same_stencils2d(const int* lc, const float* f, const int* ce, const float* fe) {
-    return NodeW<ORDER>(lc[0], f[0]).base == NodeW<ORDER>(ce[0], fe[0]).base &&
-           NodeW<ORDER>(lc[1], f[1]).base == NodeW<ORDER>(ce[1], fe[1]).base;
-}
-
 // ----------------------------------------------------------- 3D deposit
 // Same construction as the 2D deposit one level up, evaluated slab by slab
 // in y (b) so that only the closure sums cross slabs: X(a, b) (target of
 // sum_c W_x) per slab with running row sums, W_y(a, b, c) with running sums
 // over b (their negative is J_y), and W_z = dQ - W_x - W_y inside the slab.
-template <int ORDER, class Acc>
-__device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const int* lc,
-                                 const float* f, const int* ce, const float* fe, float s) {
-    constexpr int WN = ORDER + 2;
+// Window of WN nodes per dimension from (bs0, bs1, bs2); the start/end
+// stencils sit at offsets o*0 / o*1 in it; residuals go to the window's last
+// node.
+template <int ORDER, int WN, class Acc>
+__device__ inline void deposit3d_core(const Acc& acc, int jsz, int H0, int H1, int bs0, int bs1, int bs2,
+                                      int ox0, int ox1, int oy0, int oy1, int oz0, int oz1,
+                                      const float (&S0x)[WN], const float (&S1x)[WN],
+                                      const float (&S0y)[WN], const float (&S1y)[WN],
+                                      const float (&S0z)[WN], const float (&S1z)[WN], float s) {
     constexpr int L = WN - 1;
-    const NodeW<ORDER> a0(lc[0], f[0]), a1(lc[1], f[1]), a2(lc[2], f[2]);
-    const NodeW<ORDER> b0(ce[0], fe[0]), b1(ce[1], fe[1]), b2(ce[2], fe[2]);
-    const int bs0 = min(a0.base, b0.base), bs1 = min(a1.base, b1.base), bs2 = min(a2.base, b2.base);
-    float S0x[WN], S1x[WN], S0y[WN], S1y[WN], S0z[WN], S1z[WN];
-    place32<ORDER>(S0x, a0, a0.base - bs0); place32<ORDER>(S1x, b0, b0.base - bs0);
-    place32<ORDER>(S0y, a1, a1.base - bs1); place32<ORDER>(S1y, b1, b1.base - bs1);
-    place32<ORDER>(S0z, a2, a2.base - bs2); place32<ORDER>(S1z, b2, b2.base - bs2);
-    const int oz0 = a2.base - bs2, oz1 = b2.base - bs2;
     const int sint = rint22(s);
 
     int qx0[WN], qx1[WN], qxy0[WN][WN], qxy1[WN][WN];
-    charge_levels_1d<WN>(s, sint, S0x, a0.base - bs0, qx0);
-    charge_levels_1d<WN>(s, sint, S1x, b0.base - bs0, qx1);
-    charge_levels_2d<WN>(qx0, S0y, a1.base - bs1, qxy0);
-    charge_levels_2d<WN>(qx1, S1y, b1.base - bs1, qxy1);
+    charge_levels_1d<WN>(s, sint, S0x, ox0, qx0);
+    charge_levels_1d<WN>(s, sint, S1x, ox1, qx1);
+    charge_levels_2d<WN>(qx0, S0y, oy0, qxy0);
+    charge_levels_2d<WN>(qx1, S1y, oy1, qxy1);
 
     int xrow[WN];          // running sum over b of X(a, b), a < L
     int wys[WN][WN];       // running sum over b of W_y(a, b, c)
@@ -276,16 +272,23 @@ __device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const 
 #pragma unroll
         for (int c = 0; c < WN; ++c) wys[a][c] = 0;
     }
+    float sdx[WN], Az[WN], DSz[WN];
+#pragma unroll
+    for (int a = 0; a < WN; ++a) {
+        sdx[a] = s * (S1x[a] - S0x[a]);
+        Az[a] = 0.5f * (S0z[a] + S1z[a]); DSz[a] = S1z[a] - S0z[a];
+    }
 #pragma unroll
     for (int b = 0; b < WN; ++b) {
         const float ay = 0.5f * (S0y[b] + S1y[b]), dsy = S1y[b] - S0y[b];
+        const float sdy = s * dsy, dsy12 = dsy * (1.0f / 12.0f);
         // X(., b) with its closures; Y(., b) = Z(., b) - X(., b)
         int X[WN];
         {
             int col = 0;
 #pragma unroll
             for (int a = 0; a < L; ++a) {
-                const int v = (b < L) ? rint22(s * (S1x[a] - S0x[a]) * ay) : (qx1[a] - qx0[a]) - xrow[a];
+                const int v = (b < L) ? rint22_mul(sdx[a], ay) : (qx1[a] - qx0[a]) - xrow[a];
                 X[a] = v; xrow[a] += v; col += v;
             }
             X[L] = -col;
@@ -298,8 +301,8 @@ __device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const 
             int sum0 = 0, sum1 = 0;
 #pragma unroll
             for (int c = 0; c < WN; ++c) {
-                const int q0 = rint22(__fmul_rn(f0, S0z[c]));
-                const int q1 = rint22(__fmul_rn(f1, S1z[c]));
+                const int q0 = rint22_mul(f0, S0z[c]);
+                const int q1 = rint22_mul(f1, S1z[c]);
                 dq[a][c] = q1 - q0; sum0 += q0; sum1 += q1;
             }
 #pragma unroll
@@ -313,12 +316,11 @@ __device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const 
             for (int a = 0; a < WN; ++a) cs[a] = 0;
 #pragma unroll
             for (int c = 0; c < WN; ++c) {
-                const float az = 0.5f * (S0z[c] + S1z[c]), dsz = S1z[c] - S0z[c];
-                const float kyz = ay * az + dsy * dsz * (1.0f / 12.0f);
+                const float kyz = __fmaf_rn(ay, Az[c], dsy12 * DSz[c]);
                 int colsum = 0, run = 0;
 #pragma unroll
                 for (int a = 0; a < L; ++a) {
-                    const int v = (c < L) ? rint22(s * (S1x[a] - S0x[a]) * kyz) : X[a] - cs[a];
+                    const int v = (c < L) ? rint22_mul(sdx[a], kyz) : X[a] - cs[a];
                     cs[a] += v; colsum += v;
                     dq[a][c] -= v;
                     run -= v;
@@ -331,15 +333,14 @@ __device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const 
         // the last slab closes sum_b W_y = 0.  J_y is minus the running sum over b.
 #pragma unroll
         for (int a = 0; a < WN; ++a) {
-            const float ax = 0.5f * (S0x[a] + S1x[a]), dsx = S1x[a] - S0x[a];
+            const float ax = 0.5f * (S0x[a] + S1x[a]), dsx12 = (S1x[a] - S0x[a]) * (1.0f / 12.0f);
             const int Y = (qxy1[a][b] - qxy0[a][b]) - X[a];
             int cs = 0;
 #pragma unroll
             for (int c = 0; c < WN; ++c) {
                 int v;
                 if (b < L) {
-                    const float az = 0.5f * (S0z[c] + S1z[c]), dsz = S1z[c] - S0z[c];
-                    v = (c < L) ? rint22(s * dsy * (ax * az + dsx * dsz * (1.0f / 12.0f))) : Y - cs;
+                    v = (c < L) ? rint22_mul(sdy, __fmaf_rn(ax, Az[c], dsx12 * DSz[c])) : Y - cs;
                     cs += v;
                     wys[a][c] += v;
                     acc(jsz + ((bs2 + c + 2) * H1 + (bs1 + b + 2)) * H0 + (bs0 + a + 2), -wys[a][c]);
@@ -360,6 +361,52 @@ __device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const 
             }
         }
     }
+}
+
+
+// General case: the window of ORDER + 2 nodes per dimension holds both stencils.
+template <int ORDER, class Acc>
+__device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const int* lc,
+                                 const float* f, const int* ce, const float* fe, float s) {
+    constexpr int WN = ORDER + 2;
+    const NodeW<ORDER> a0(lc[0], f[0]), a1(lc[1], f[1]), a2(lc[2], f[2]);
+    const NodeW<ORDER> b0(ce[0], fe[0]), b1(ce[1], fe[1]), b2(ce[2], fe[2]);
+    const int bs0 = min(a0.base, b0.base), bs1 = min(a1.base, b1.base), bs2 = min(a2.base, b2.base);
+    float S0x[WN], S1x[WN], S0y[WN], S1y[WN], S0z[WN], S1z[WN];
+    place32<ORDER>(S0x, a0, a0.base - bs0); place32<ORDER>(S1x, b0, b0.base - bs0);
+    place32<ORDER>(S0y, a1, a1.base - bs1); place32<ORDER>(S1y, b1, b1.base - bs1);
+    place32<ORDER>(S0z, a2, a2.base - bs2); place32<ORDER>(S1z, b2, b2.base - bs2);
+    deposit3d_core<ORDER, WN>(acc, jsz, H0, H1, bs0, bs1, bs2, a0.base - bs0, b0.base - bs0,
+                              a1.base - bs1, b1.base - bs1, a2.base - bs2, b2.base - bs2,
+                              S0x, S1x, S0y, S1y, S0z, S1z, s);
+}
+
+// Both stencils start at the same node in every dimension: the window is the
+// stencil itself, ORDER + 1 nodes per dimension.
+template <int ORDER, class Acc>
+__device__ inline void deposit3d_same(const Acc& acc, int jsz, int H0, int H1, const int* lc,
+                                      const float* f, const int* ce, const float* fe, float s) {
+    constexpr int WN = ORDER + 1;
+    const NodeW<ORDER> a0(lc[0], f[0]), a1(lc[1], f[1]), a2(lc[2], f[2]);
+    const NodeW<ORDER> b0(ce[0], fe[0]), b1(ce[1], fe[1]), b2(ce[2], fe[2]);
+    float S0x[WN], S1x[WN], S0y[WN], S1y[WN], S0z[WN], S1z[WN];
+#pragma unroll
+    for (int a = 0; a < WN; ++a) {
+        S0x[a] = a0.w[a]; S1x[a] = b0.w[a]; S0y[a] = a1.w[a]; S1y[a] = b1.w[a];
+        S0z[a] = a2.w[a]; S1z[a] = b2.w[a];
+    }
+    deposit3d_core<ORDER, WN>(acc, jsz, H0, H1, a0.base, a1.base, a2.base, 0, 0, 0, 0, 0, 0,
+                              S0x, S1x, S0y, S1y, S0z, S1z, s);
+}
+
+// Whether the start and end stencils of a move begin at the same node in
+// every dimension (then the stencil-sized window holds the whole deposit).
+template <int DIM, int ORDER>
+__device__ inline bool same_stencils(const int* lc, const float* f, const int* ce, const float* fe) {
+    bool same = true;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) same &= NodeW<ORDER>(lc[d], f[d]).base == NodeW<ORDER>(ce[d], fe[d]).base;
+    return same;
 }
 
 // Integer charge of one particle (the Q of the deposit: same levels, same
@@ -388,7 +435,7 @@ __device__ inline void charge_int(unsigned long long* rho, const Geo& g, const i
             int q[WN], sum = 0;
             const float fab = (float)qxy[a][b];
 #pragma unroll
-            for (int c = 0; c < WN; ++c) { q[c] = rint22(__fmul_rn(fab, Sz[c])); sum += q[c]; }
+            for (int c = 0; c < WN; ++c) { q[c] = rint22_mul(fab, Sz[c]); sum += q[c]; }
             q[1] += qxy[a][b] - sum;
 #pragma unroll
             for (int c = 0; c <= ORDER; ++c) {
@@ -399,18 +446,100 @@ __device__ inline void charge_int(unsigned long long* rho, const Geo& g, const i
         }
 }
 
+// ----------------------------------------------------------- gather
+// Interpolates the six Yee components at the particle: staggering E_x (h,n,n),
+// E_y (n,h,n), E_z (n,n,h), B_x (n,h,h), B_y (h,n,h), B_z (h,h,n) with h the
+// half-node and n the node weights of each dimension.  The sum is separable:
+// rows along x first, then along y, then z, with explicit roundings so that
+// the tile kernel (fields staged in shared memory) and the global-memory path
+// for escaped particles give identical bits.  ld(comp, x, y, z) returns the
+// component at node (x, y, z) of the particle's local frame (z = 0 in 2D).
+template <int DIM, int ORDER, class Load>
+__device__ __forceinline__ void gather32(const Load& ld, const NodeW<ORDER>& nx_, const NodeW<ORDER>& ny_,
+                                         const NodeW<ORDER>& nz_, const HalfW<ORDER>& hx_,
+                                         const HalfW<ORDER>& hy_, const HalfW<ORDER>& hz_, float (&fld)[6]) {
+#pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+        const bool hx = (comp == 0 || comp == 4 || comp == 5);
+        const bool hy = (comp == 1 || comp == 3 || comp == 5);
+        const bool hz = (comp == 2 || comp == 3 || comp == 4);
+        const int bx = hx ? hx_.base : nx_.base, by = hy ? hy_.base : ny_.base;
+        const int bz = (DIM == 3) ? (hz ? hz_.base : nz_.base) : 0;
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < (DIM == 3 ? ORDER + 1 : 1); ++c) {
+            float accb = 0.0f;
+#pragma unroll
+            for (int b = 0; b <= ORDER; ++b) {
+                float r = 0.0f;
+#pragma unroll
+                for (int a = 0; a <= ORDER; ++a) {
+                    const float wx = hx ? hx_.w[a] : nx_.w[a];
+                    const float v = ld(comp, bx + a, by + b, DIM == 3 ? bz + c : 0);
+                    r = (a == 0) ? __fmul_rn(v, wx) : __fmaf_rn(v, wx, r);
+                }
+                const float wy = hy ? hy_.w[b] : ny_.w[b];
+                accb = (b == 0) ? __fmul_rn(r, wy) : __fmaf_rn(r, wy, accb);
+            }
+            if (DIM == 3) {
+                const float wz = hz ? hz_.w[c] : nz_.w[c];
+                acc = (c == 0) ? __fmul_rn(accb, wz) : __fmaf_rn(accb, wz, acc);
+            } else {
+                acc = accb;
+            }
+        }
+        fld[comp] = acc;
+    }
+}
+
+// Field components staged in shared memory: box of G0 x G1 (x G2) nodes per
+// component with a halo of 2, local node (x, y, z) at ((z+2) G1 + y+2) G0 + x+2
+// (2D: y+2) G0 + x+2).
+template <int DIM>
+struct LoadShared {
+    const float* sF;
+    int fsz, G0, G1;
+    __device__ inline float operator()(int comp, int x, int y, int z) const {
+        return sF[comp * fsz + ((DIM == 3 ? z + 2 : 0) * G1 + (y + 2)) * G0 + (x + 2)];
+    }
+};
+
+// Field components read from global memory around a particle whose cell is
+// gc, local frame with the particle's cell at 2; nodes outside the grid
+// (absorbing x) read 0 and raise the flag.
+template <int DIM>
+struct LoadGlobal {
+    const Geo* g;
+    const float* F[6];
+    int gc[3];
+    bool* outside;
+    __device__ inline float operator()(int comp, int x, int y, int z) const {
+        const long long m = fidx(*g, gc[0] + x - 2, gc[1] + y - 2, DIM == 3 ? gc[2] + z - 2 : 0);
+        if (m < 0) { *outside = true; return 0.0f; }
+        return F[comp][m];
+    }
+};
+
 // ----------------------------------------------------------- the tile kernel
 // Shared memory: 6 field boxes (T+4 per dimension, halo 2 below and 2 above),
-// an int32 round box and an int64 total box for J (T+5 per dimension).
+// an int64 total box and an int32 round box for J (T+5 per dimension), and in
+// 3D the deposit staging of one round.
 // Blocks per SM the register allocation targets (2D: the kernel fits 80
 // registers with negligible spills; 3D: 128 registers, a few spills, measured
 // 1.57x faster than one block per SM at 255 registers).
 #ifndef LPIC_GPD2D_MINB
-#define LPIC_GPD2D_MINB 3
+#define LPIC_GPD2D_MINB 4
 #endif
 #ifndef LPIC_GPD3D_MINB
 #define LPIC_GPD3D_MINB 2
 #endif
+
+// Threads per block of the tile kernel, and the 3D deposit staging of one
+// round in shared memory (words per slot: packed start cell, packed end-cell
+// carries, start offsets, end offsets, charge).
+constexpr int kGpdThreads = 256;
+constexpr int kStageWords = 9;
+constexpr int kStageBytes = (kStageWords * kGpdThreads + 4) * 4;
 
 // Everything the fused kernel needs for one species of one grid.
 struct GpdArgs {
@@ -451,9 +580,15 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     const int G0 = Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
     const int H0 = Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
     const int fsz = G0 * G1 * G2, jsz = H0 * H1 * H2;
+    const int n4 = (3 * jsz + 3) >> 2;     // the J boxes in groups of 4 nodes
     float* sF = reinterpret_cast<float*>(smem4);
     long long* sJ = reinterpret_cast<long long*>(sF + ((6 * fsz + 3) & ~3));
-    int* sR = reinterpret_cast<int*>(sJ + 3 * jsz);
+    int* sR = reinterpret_cast<int*>(sJ + 4 * n4);
+    longlong2* sJ2 = reinterpret_cast<longlong2*>(sJ);
+    int4* sR4 = reinterpret_cast<int4*>(sR);
+    // 3D deposit staging: kStageWords words per slot, then the two slot counters
+    int* sSt = sR + 4 * n4;
+    int* sCnt = sSt + kStageWords * kGpdThreads;
 
     for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
         const int c = idx / fsz, r = idx - c * fsz;
@@ -463,16 +598,25 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                          : c == 3 ? B.p[0] : c == 4 ? B.p[1] : B.p[2];
         sF[idx] = (m < 0) ? 0.0f : src[m];
     }
-    for (int idx = threadIdx.x; idx < 3 * jsz; idx += blockDim.x) { sJ[idx] = 0; sR[idx] = 0; }
+    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+        sJ2[2 * q] = make_longlong2(0, 0);
+        sJ2[2 * q + 1] = make_longlong2(0, 0);
+        sR4[q] = make_int4(0, 0, 0, 0);
+    }
+    if (DIM == 3 && threadIdx.x == 0) { sCnt[0] = 0; sCnt[1] = 0; }
     __syncthreads();
 
     const float dth[3] = {dth0, dth1, dth2};
     const Acc32<DIM == 2> acc{sR};
-    const int nround = (end - beg + blockDim.x - 1) / blockDim.x;
+    const int nround = (end - beg + kGpdThreads - 1) / kGpdThreads;
     for (int rnd = 0; rnd < nround; ++rnd) {
-        const int i = beg + rnd * blockDim.x + threadIdx.x;
+        const int i = beg + rnd * kGpdThreads + threadIdx.x;
         const int cell = (i < end) ? p.cell[i] : -1;
         int cell_out = cell;      // the particle's cell after this round (-1: removed)
+        // 3D: the move this particle deposits (if dep), staged below
+        bool dep = false, same = false;
+        int mlc[3] = {0, 0, 0}, mce[3] = {0, 0, 0};
+        float mf0[3] = {0.0f, 0.0f, 0.0f}, mf1[3] = {0.0f, 0.0f, 0.0f}, ms = 0.0f;
         if (cell >= 0) {
             int gc[3];
             dec(cell, gc);
@@ -503,29 +647,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
                 const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
                 float fld[6];
-#pragma unroll
-                for (int comp = 0; comp < 6; ++comp) {
-                    // staggering: E_x (h,n,n) E_y (n,h,n) E_z (n,n,h) B_x (n,h,h) B_y (h,n,h) B_z (h,h,n)
-                    const bool hx = (comp == 0 || comp == 4 || comp == 5);
-                    const bool hy = (comp == 1 || comp == 3 || comp == 5);
-                    const bool hz = (comp == 2 || comp == 3 || comp == 4);
-                    const int bx = hx ? hx_.base : nx_.base, by = hy ? hy_.base : ny_.base;
-                    const int bz = (DIM == 3) ? (hz ? hz_.base : nz_.base) : -2;
-                    const float* F = sF + comp * fsz;
-                    float accv = 0.0f;
-#pragma unroll
-                    for (int c = 0; c < (DIM == 3 ? ORDER + 1 : 1); ++c) {
-                        const float wzv = (DIM == 3) ? (hz ? hz_.w[c] : nz_.w[c]) : 1.0f;
-#pragma unroll
-                        for (int b = 0; b <= ORDER; ++b) {
-                            const float wyz = (hy ? hy_.w[b] : ny_.w[b]) * wzv;
-                            const float* row = F + ((bz + c + 2) * G1 + (by + b + 2)) * G0 + (bx + 2);
-#pragma unroll
-                            for (int a = 0; a <= ORDER; ++a) accv += row[a] * ((hx ? hx_.w[a] : nx_.w[a]) * wyz);
-                        }
-                    }
-                    fld[comp] = accv;
-                }
+                gather32<DIM, ORDER>(LoadShared<DIM>{sF, fsz, G0, G1}, nx_, ny_, nz_, hx_, hy_, hz_, fld);
                 boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
                 if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
                     set_status(st, LPIC_ST_NAN);
@@ -553,16 +675,18 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                         p.cell[i] = -1;
                         cell_out = -1;
                     } else {
-                        const float s = sq * w;
-                        if (DIM == 3) {
-                            deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
-                        } else {
+                        same = same_stencils<DIM, ORDER>(lc, f, ce, fe);
+                        if constexpr (DIM == 2) {
                             // the stencil-sized window when every converged lane allows it
-                            const bool same = same_stencils2d<ORDER>(lc, f, ce, fe);
                             if (__all_sync(__activemask(), same))
-                                deposit2d_same<ORDER>(acc, jsz, H0, lc, f, ce, fe, s, uz * ig);
+                                deposit2d_same<ORDER>(acc, jsz, H0, lc, f, ce, fe, sq * w, uz * ig);
                             else
-                                deposit2d<ORDER>(acc, jsz, H0, lc, f, ce, fe, s, uz * ig);
+                                deposit2d<ORDER>(acc, jsz, H0, lc, f, ce, fe, sq * w, uz * ig);
+                        } else {
+                            dep = true;
+#pragma unroll
+                            for (int d = 0; d < 3; ++d) { mlc[d] = lc[d]; mce[d] = ce[d]; mf0[d] = f[d]; mf1[d] = fe[d]; }
+                            ms = sq * w;
                         }
                         // store x^{n+3/2} and u^{n+1}
                         int ng[3];
@@ -594,11 +718,64 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
             if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
                 atomicAdd(t.next_count + key, __popc(peers));
         }
-        // fold the round's int32 box into the int64 box
+        // 3D: stage the round's moves, same-stencil ones from the front slots
+        // and the others from the back, so that the warps below each run one
+        // form of the deposit (most particles keep their stencil, but few
+        // warps are uniform; the slot order does not matter: integer sums)
+        if constexpr (DIM == 3) {
+            const unsigned lane = threadIdx.x & 31u;
+            const unsigned mfast = __ballot_sync(0xffffffffu, dep && same);
+            const unsigned mgen = __ballot_sync(0xffffffffu, dep && !same);
+            int bf = 0, bg = 0;
+            if (lane == 0) {
+                if (mfast) bf = atomicAdd(sCnt, __popc(mfast));
+                if (mgen) bg = atomicAdd(sCnt + 1, __popc(mgen));
+            }
+            bf = __shfl_sync(0xffffffffu, bf, 0);
+            bg = __shfl_sync(0xffffffffu, bg, 0);
+            if (dep) {
+                const unsigned below = (1u << lane) - 1u;
+                const int slot = same ? bf + __popc(mfast & below) : kGpdThreads - 1 - (bg + __popc(mgen & below));
+                int* w = sSt + slot;
+                w[0 * kGpdThreads] = mlc[0] | (mlc[1] << 16);
+                w[1 * kGpdThreads] = mlc[2] | (((mce[0] - mlc[0] + 1) | ((mce[1] - mlc[1] + 1) << 2) |
+                                                ((mce[2] - mlc[2] + 1) << 4)) << 16);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    w[(2 + d) * kGpdThreads] = __float_as_int(mf0[d]);
+                    w[(5 + d) * kGpdThreads] = __float_as_int(mf1[d]);
+                }
+                w[8 * kGpdThreads] = __float_as_int(ms);
+            }
+            __syncthreads();
+            const int slot = threadIdx.x;
+            const bool fast = slot < sCnt[0];
+            if (fast || slot >= kGpdThreads - sCnt[1]) {
+                const int* w = sSt + slot;
+                const int w0 = w[0], w1 = w[kGpdThreads];
+                const int lc[3] = {w0 & 0xffff, (int)((unsigned)w0 >> 16), w1 & 0xffff};
+                const int cc = (int)((unsigned)w1 >> 16);
+                const int ce[3] = {lc[0] + (cc & 3) - 1, lc[1] + ((cc >> 2) & 3) - 1, lc[2] + ((cc >> 4) & 3) - 1};
+                const float f[3] = {__int_as_float(w[2 * kGpdThreads]), __int_as_float(w[3 * kGpdThreads]),
+                                    __int_as_float(w[4 * kGpdThreads])};
+                const float fe[3] = {__int_as_float(w[5 * kGpdThreads]), __int_as_float(w[6 * kGpdThreads]),
+                                     __int_as_float(w[7 * kGpdThreads])};
+                const float s = __int_as_float(w[8 * kGpdThreads]);
+                if (fast) deposit3d_same<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
+                else      deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
+            }
+        }
+        // fold the round's int32 box into the int64 box, four nodes at a time
         __syncthreads();
-        for (int idx = threadIdx.x; idx < 3 * jsz; idx += blockDim.x) {
-            const int v = sR[idx];
-            if (v != 0) { sJ[idx] += v; sR[idx] = 0; }
+        if (DIM == 3 && threadIdx.x == 0) { sCnt[0] = 0; sCnt[1] = 0; }
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+            const int4 v = sR4[q];
+            if ((v.x | v.y | v.z | v.w) != 0) {
+                longlong2 a = sJ2[2 * q], b = sJ2[2 * q + 1];
+                a.x += v.x; a.y += v.y; b.x += v.z; b.y += v.w;
+                sJ2[2 * q] = a; sJ2[2 * q + 1] = b;
+                sR4[q] = make_int4(0, 0, 0, 0);
+            }
         }
         __syncthreads();
     }
@@ -677,10 +854,16 @@ struct AccGlobal {
 // global memory, current added with global integer atomics (same integer
 // quantisation, so the result is identical to the shared-memory path).
 template <int DIM, int ORDER>
-__global__ void __launch_bounds__(256) k_gpd32_escape(Geo g, Ptr3<const float> E, Ptr3<const float> B,
-                                                      Ptr3<unsigned long long> J, P32 p, Tiles t,
-                                                      CellDecode dec, float k, float sq, float dth0,
-                                                      float dth1, float dth2, unsigned* st) {
+__global__ void __launch_bounds__(256) k_gpd32_escape(GpdArgs A) {
+    const Geo& g = A.g;
+    const Ptr3<const float>& E = A.E;
+    const Ptr3<const float>& B = A.B;
+    const Ptr3<unsigned long long>& J = A.J;
+    const P32& p = A.p;
+    const Tiles& t = A.t;
+    const CellDecode& dec = A.dec;
+    const float k = A.k, sq = A.sq, dth0 = A.dth0, dth1 = A.dth1, dth2 = A.dth2;
+    unsigned* st = A.st;
     const int nesc = *t.nesc;
     const float dth[3] = {dth0, dth1, dth2};
     const int stride = gridDim.x * blockDim.x;
@@ -702,33 +885,9 @@ __global__ void __launch_bounds__(256) k_gpd32_escape(Geo g, Ptr3<const float> E
             const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
             float fld[6];
             bool outside = false;
-#pragma unroll
-            for (int comp = 0; comp < 6; ++comp) {
-                const bool hx = (comp == 0 || comp == 4 || comp == 5);
-                const bool hy = (comp == 1 || comp == 3 || comp == 5);
-                const bool hz = (comp == 2 || comp == 3 || comp == 4);
-                const int bx = hx ? hx_.base : nx_.base, by = hy ? hy_.base : ny_.base;
-                const int bz = (DIM == 3) ? (hz ? hz_.base : nz_.base) : 0;
-                const float* F = comp == 0 ? E.p[0] : comp == 1 ? E.p[1] : comp == 2 ? E.p[2]
-                               : comp == 3 ? B.p[0] : comp == 4 ? B.p[1] : B.p[2];
-                float accv = 0.0f;
-#pragma unroll
-                for (int c = 0; c < (DIM == 3 ? ORDER + 1 : 1); ++c) {
-                    const float wzv = (DIM == 3) ? (hz ? hz_.w[c] : nz_.w[c]) : 1.0f;
-#pragma unroll
-                    for (int b = 0; b <= ORDER; ++b) {
-                        const float wyz = (hy ? hy_.w[b] : ny_.w[b]) * wzv;
-#pragma unroll
-                        for (int a = 0; a <= ORDER; ++a) {
-                            const long long m = fidx(g, gc[0] + bx + a - 2, gc[1] + by + b - 2,
-                                                     DIM == 3 ? gc[2] + bz + c - 2 : 0);
-                            if (m < 0) { outside = true; continue; }
-                            accv += F[m] * ((hx ? hx_.w[a] : nx_.w[a]) * wyz);
-                        }
-                    }
-                }
-                fld[comp] = accv;
-            }
+            const LoadGlobal<DIM> ld{&g, {E.p[0], E.p[1], E.p[2], B.p[0], B.p[1], B.p[2]},
+                                     {gc[0], gc[1], gc[2]}, &outside};
+            gather32<DIM, ORDER>(ld, nx_, ny_, nz_, hx_, hy_, hz_, fld);
             if (outside) set_status(st, LPIC_ST_OUTSIDE);
             boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
             if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
@@ -758,8 +917,15 @@ __global__ void __launch_bounds__(256) k_gpd32_escape(Geo g, Ptr3<const float> E
                     const AccGlobal<DIM> acc{&g, J, {gc[0], gc[1], gc[2]}, st};
                     constexpr int HV = AccGlobal<DIM>::HV;
                     const float s = sq * w;
-                    if (DIM == 3) deposit3d<ORDER>(acc, HV * HV * HV, HV, HV, lc, f, ce, fe, s);
-                    else          deposit2d<ORDER>(acc, HV * HV, HV, lc, f, ce, fe, s, uz * ig);
+                    // the same form of the deposit as the tile kernel takes
+                    const bool same = same_stencils<DIM, ORDER>(lc, f, ce, fe);
+                    if (DIM == 3) {
+                        if (same) deposit3d_same<ORDER>(acc, HV * HV * HV, HV, HV, lc, f, ce, fe, s);
+                        else      deposit3d<ORDER>(acc, HV * HV * HV, HV, HV, lc, f, ce, fe, s);
+                    } else {
+                        if (same) deposit2d_same<ORDER>(acc, HV * HV, HV, lc, f, ce, fe, s, uz * ig);
+                        else      deposit2d<ORDER>(acc, HV * HV, HV, lc, f, ce, fe, s, uz * ig);
+                    }
                     int ng[3];
 #pragma unroll
                     for (int d = 0; d < 3; ++d) ng[d] = (d < DIM) ? gc[d] + ce[d] - lc[d] : 0;

@@ -1,0 +1,28 @@
+// lpic_gpd32.h -- host-side launchers of the FP32 tile kernels.
+//
+// Each (dimension, shape order) instance of the fused kernel, its persistent
+// ensemble form and its escape kernel is compiled in a translation unit of its
+// own (lpic_gpd32_<dim><order>.cu), so the heavy instances build in parallel;
+// the rest of the library calls them through these declarations.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lpic_fp32.cuh"
+
+namespace lpic {
+
+template <int DIM, int ORDER>
+struct Gpd32 {
+    // raises the dynamic shared-memory limit of the tile and queue kernels
+    static cudaError_t set_smem(size_t bytes);
+    // one block per work item
+    static void tile(const GpdArgs& A, unsigned blocks, size_t smem, cudaStream_t st);
+    // the particles the tile kernel queued beyond its drift margin
+    static void escape(const GpdArgs& A, unsigned blocks, cudaStream_t st);
+    // persistent blocks over the device queue of a batch of grids
+    static void queue(const GpdArgs* slots, const int* order, const int* prefix, int nslots, int* head,
+                      unsigned blocks, size_t smem, cudaStream_t st);
+    static const void* queue_fn();
+};
+
+}  // namespace lpic
