@@ -98,6 +98,7 @@ struct lpic_grid {
     size_t smem32 = 0;
     long long launches = 0;
     int P = 4096;                              // particles per work item (FP32 path)
+    int R = 1;                                 // rounds of 256 moves between int32-box folds
     int K = 1;                                 // sort interval (steps)
     int m[3] = {0, 0, 0};                      // drift margin of the tiles (cells)
     CellDecode dec{};
@@ -190,6 +191,7 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_n
     t.items = s.d_items;
     t.nitems = s.d_nitems;
     t.P = g->P;
+    t.R = g->R;
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
     GpdArgs A{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
@@ -320,6 +322,27 @@ lpic_status check_species(lpic_grid_t g, int sid) {
     return LPIC_OK;
 }
 
+// Rounds of 256 moves the int32 current box can take between folds into the
+// int64 box.  One move adds at most S b + 1024 to a node: S <= 2^22 is the
+// particle's integer charge (the shift F guarantees it), the 1024 units cover
+// the roundings and closures, and b bounds the current of one move in units
+// of S.  J_d along d is s (C1 - C0) K with C the running sum of the shape
+// weights (|C1 - C0| <= the displacement nu <= c dt / h cells, since the
+// running sum of a B-spline's weights moves with slope at most 1) and K the
+// transverse factor: 2D A_y <= k, 3D A_y A_z + DS_y DS_z / 12 <= k^2 + 1/12
+// (k = 0.75 TSC, 1 CIC).  2D J_z = s v_z W_z, |v_z| < 1, W_z <= k^2 + 1/12.
+int fold_rounds(const lpic_grid_desc& d) {
+    double nu = std::max(d.dt / d.dx, d.dt / d.dy);
+    if (d.dim == 3) nu = std::max(nu, d.dt / d.dz);
+    nu = std::min(nu, 1.0);                     // the kernel rejects longer moves
+    const double k = d.shape_order == 2 ? 0.75 : 1.0;
+    double b = nu * (d.dim == 3 ? k * k + 1.0 / 12.0 : k);
+    if (d.dim == 2) b = std::max(b, k * k + 1.0 / 12.0);
+    const double per_move = 4194304.0 * b + 1024.0;
+    const int R = (int)std::floor(2147483647.0 / (256.0 * per_move));
+    return std::max(1, std::min(R, 64));
+}
+
 void recompute_shift(lpic_grid* g) {
     double total = 0.0, mx = 0.0;
     for (const auto& s : g->sp) {
@@ -416,6 +439,7 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     for (int k = 0; k < 3; ++k) g->fT[k] = make_fastdiv((unsigned)g->T[k]);
     g->dec = CellDecode{make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny)};
     if (d.block_particles > 0) g->P = d.block_particles;
+    g->R = fold_rounds(d);
     g->K = d.sort_interval > 1 ? d.sort_interval : 1;
     {
         // a particle moves less than c dt / h cells per step (Courant limit)
@@ -1017,7 +1041,7 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
                 so.mv[b] = MoveFP32{src, dst, g->d.dim};
                 Tiles t{};
                 for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; t.m[d] = g->m[d]; t.fT[d] = g->fT[d]; }
-                t.start = s.d_start; t.items = s.d_items; t.nitems = s.d_nitems; t.P = g->P;
+                t.start = s.d_start; t.items = s.d_items; t.nitems = s.d_nitems; t.P = g->P; t.R = g->R;
                 t.next_count = s.d_count; t.esc = s.d_esc; t.nesc = s.d_nesc;
                 // the push runs after the step's sort flipped the parity: it
                 // reads the buffer the particles were sorted into

@@ -10,11 +10,12 @@
 // int64 J with integer atomics.  Integer sums do not depend on the order of
 // the additions, so the result is bitwise deterministic.
 //
-// Shared-memory accumulation: each round of blockDim particles adds into an
-// int32 box with native 32-bit atomics; after the round the box is folded
-// into an int64 box.  The shift F keeps every particle's integer charge
-// S <= 2^22, so a per-node value is below 1.1 * 2^22 and one round of 256
-// particles cannot overflow int32.
+// Shared-memory accumulation: rounds of 256 particles add into an int32 box
+// with native 32-bit atomics; every R rounds the box is folded into an int64
+// box.  The shift F keeps every particle's integer charge S <= 2^22, and the
+// host derives R from a bound on one move's current per node (a fraction of
+// S set by the Courant number and the shape), so the int32 box cannot
+// overflow between folds.
 //
 // Exact charge conservation in integers.  The unit of charge is 2^-F.  A
 // particle of charge s = 2^F q w carries the integer charge S = rint(s),
@@ -60,6 +61,7 @@ struct Tiles {
     const int2* items;   // (tile, chunk) work items
     const int* nitems;   // device count of work items
     int P;               // particles per chunk
+    int R;               // rounds between folds of the int32 current box
     FastDiv fT[3];       // division by T (tile keys of the next sort)
     int* next_count;     // if set: histogram of the new tile keys for the next sort
     int* esc;            // indices of particles beyond the tile's margin ...
@@ -588,7 +590,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     int4* sR4 = reinterpret_cast<int4*>(sR);
     // 3D deposit staging: kStageWords words per slot, then the two slot counters
     int* sSt = sR + 4 * n4;
-    int* sCnt = sSt + kStageWords * kGpdThreads;
+    int* sCnt = sSt + kStageWords * kGpdThreads;   // [2 * (round & 1)], by round parity
 
     for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
         const int c = idx / fsz, r = idx - c * fsz;
@@ -603,7 +605,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
         sJ2[2 * q + 1] = make_longlong2(0, 0);
         sR4[q] = make_int4(0, 0, 0, 0);
     }
-    if (DIM == 3 && threadIdx.x == 0) { sCnt[0] = 0; sCnt[1] = 0; }
+    if (DIM == 3 && threadIdx.x < 4) sCnt[threadIdx.x] = 0;
     __syncthreads();
 
     const float dth[3] = {dth0, dth1, dth2};
@@ -723,13 +725,14 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
         // form of the deposit (most particles keep their stencil, but few
         // warps are uniform; the slot order does not matter: integer sums)
         if constexpr (DIM == 3) {
+            int* cnt = sCnt + 2 * (rnd & 1);
             const unsigned lane = threadIdx.x & 31u;
             const unsigned mfast = __ballot_sync(0xffffffffu, dep && same);
             const unsigned mgen = __ballot_sync(0xffffffffu, dep && !same);
             int bf = 0, bg = 0;
             if (lane == 0) {
-                if (mfast) bf = atomicAdd(sCnt, __popc(mfast));
-                if (mgen) bg = atomicAdd(sCnt + 1, __popc(mgen));
+                if (mfast) bf = atomicAdd(cnt, __popc(mfast));
+                if (mgen) bg = atomicAdd(cnt + 1, __popc(mgen));
             }
             bf = __shfl_sync(0xffffffffu, bf, 0);
             bg = __shfl_sync(0xffffffffu, bg, 0);
@@ -748,9 +751,11 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 w[8 * kGpdThreads] = __float_as_int(ms);
             }
             __syncthreads();
+            // the other parity's counters were last read before this barrier
+            if (threadIdx.x < 2) sCnt[2 * ((rnd + 1) & 1) + threadIdx.x] = 0;
             const int slot = threadIdx.x;
-            const bool fast = slot < sCnt[0];
-            if (fast || slot >= kGpdThreads - sCnt[1]) {
+            const bool fast = slot < cnt[0];
+            if (fast || slot >= kGpdThreads - cnt[1]) {
                 const int* w = sSt + slot;
                 const int w0 = w[0], w1 = w[kGpdThreads];
                 const int lc[3] = {w0 & 0xffff, (int)((unsigned)w0 >> 16), w1 & 0xffff};
@@ -764,10 +769,13 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 if (fast) deposit3d_same<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
                 else      deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
             }
+            // the staging slots are rewritten by the next round
+            __syncthreads();
         }
-        // fold the round's int32 box into the int64 box, four nodes at a time
-        __syncthreads();
-        if (DIM == 3 && threadIdx.x == 0) { sCnt[0] = 0; sCnt[1] = 0; }
+        // every R rounds (and at the end) fold the int32 box into the int64
+        // box, four nodes at a time (block-uniform condition)
+        if ((rnd + 1) % t.R != 0 && rnd + 1 != nround) continue;
+        if constexpr (DIM == 2) __syncthreads();
         for (int q = threadIdx.x; q < n4; q += blockDim.x) {
             const int4 v = sR4[q];
             if ((v.x | v.y | v.z | v.w) != 0) {

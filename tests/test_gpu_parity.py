@@ -157,6 +157,46 @@ def test_fp32_exact_integer_continuity_over_steps(dim, order):
     assert G.check_status() == 0
 
 
+@pytest.mark.parametrize("dim,order,direction", [(2, 2, "z"), (2, 2, "x"), (2, 1, "z"), (3, 2, "xyz"),
+                                                 (3, 1, "xyz")])
+def test_int32_round_box_holds_identical_relativistic_particles(dim, order, direction):
+    """4096 identical particles of the largest integer charge moving at nearly
+    c through one cell: every node of their stencil gets the same contribution
+    from all of them, R rounds of 256 between folds of the int32 box (R from
+    the per-move current bound).  An overflow would be off by 2^32 units:
+    exact continuity and the oracle's current both catch it."""
+    from paper_2607_13507_b300 import lpic
+    n = 4096
+    if dim == 2:
+        wl = W.thermal2d(n=16, ppc=1, vth=0.0, order=order, precision="fp32")
+    else:
+        wl = W.thermal3d(n=12, ppc=1, vth=0.0, order=order, precision="fp32")
+    u0 = {"z": (0.0, 0.0, 40.0), "x": (40.0, 0.0, 0.0), "xyz": (23.0, 23.0, 23.0)}[direction]
+    p = W.Particles(-1.0, 1.0,
+                    np.full((dim, n), 6, dtype=np.int32),
+                    np.array([0.3, 0.6, 0.45][:dim], dtype=np.float32)[:, None].repeat(n, 1),
+                    np.array(u0, dtype=np.float32)[:, None].repeat(n, 1),
+                    np.full(n, 0.999, dtype=np.float32), np.arange(n, dtype=np.int32))
+    G = gpu_case(wl, [p], lpic.FP32_FIXED)
+    g, sps = oracle_case(wl, [p])
+    sp = G.species[0]
+    prev = sp.charge()
+    for s in range(3):
+        G.step(s * G.dt)
+        O.step(g, sps, s * wl.dt)
+        rho = sp.charge()
+        assert torch.equal(rho - prev + _div_int(G), torch.zeros_like(rho)), s
+        prev = rho
+        # the fixed-point error is absolute (units of 2^-F per node), so each
+        # component is measured against the dominant one (the others are the
+        # small currents of the self-fields' push)
+        Jg = G.current()
+        scale = max(np.linalg.norm(g.J[c]) for c in range(3))
+        for c in range(3):
+            assert np.linalg.norm(Jg[c].cpu().numpy() - g.J[c]) < 1e-4 * scale, (s, c)
+    assert G.check_status() == 0
+
+
 def test_fp32_deposit_is_deterministic_under_permutation():
     from paper_2607_13507_b300 import lpic
     wl = W.thermal2d(n=32, ppc=8, vth=0.1, order=2, precision="fp32")
