@@ -536,12 +536,42 @@ struct LoadGlobal {
 #define LPIC_GPD3D_MINB 2
 #endif
 
-// Threads per block of the tile kernel, and the 3D deposit staging of one
-// round in shared memory (words per slot: packed start cell, packed end-cell
-// carries, start offsets, end offsets, charge).
+// Threads per block of the tile kernel, and the 3D deposit staging in shared
+// memory (words per slot: packed start cell, packed end-cell carries, start
+// offsets, end offsets, charge): 256 slots for a round's same-stencil moves
+// and a ring of 512 for the other moves, deposited 256 at a time.
 constexpr int kGpdThreads = 256;
 constexpr int kStageWords = 9;
-constexpr int kStageBytes = (kStageWords * kGpdThreads + 4) * 4;
+constexpr int kRing = 2 * kGpdThreads;
+constexpr int kStageBytes = (kStageWords * (kGpdThreads + kRing) + 4) * 4;
+
+// One staged move: write / read kStageWords words at slot stride `stride`.
+__device__ inline void stage_move(int* w, int stride, const int* lc, const int* ce, const float* f0,
+                                  const float* f1, float s) {
+    w[0] = lc[0] | (lc[1] << 16);
+    w[stride] = lc[2] | (((ce[0] - lc[0] + 1) | ((ce[1] - lc[1] + 1) << 2) | ((ce[2] - lc[2] + 1) << 4)) << 16);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        w[(2 + d) * stride] = __float_as_int(f0[d]);
+        w[(5 + d) * stride] = __float_as_int(f1[d]);
+    }
+    w[8 * stride] = __float_as_int(s);
+}
+
+template <int ORDER, bool SAME, class Acc>
+__device__ inline void deposit_staged3d(const Acc& acc, int jsz, int H0, int H1, const int* w, int stride) {
+    const int w0 = w[0], w1 = w[stride];
+    const int lc[3] = {w0 & 0xffff, (int)((unsigned)w0 >> 16), w1 & 0xffff};
+    const int cc = (int)((unsigned)w1 >> 16);
+    const int ce[3] = {lc[0] + (cc & 3) - 1, lc[1] + ((cc >> 2) & 3) - 1, lc[2] + ((cc >> 4) & 3) - 1};
+    const float f[3] = {__int_as_float(w[2 * stride]), __int_as_float(w[3 * stride]),
+                        __int_as_float(w[4 * stride])};
+    const float fe[3] = {__int_as_float(w[5 * stride]), __int_as_float(w[6 * stride]),
+                         __int_as_float(w[7 * stride])};
+    const float s = __int_as_float(w[8 * stride]);
+    if (SAME) deposit3d_same<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
+    else      deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
+}
 
 // Everything the fused kernel needs for one species of one grid.
 struct GpdArgs {
@@ -588,9 +618,11 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     int* sR = reinterpret_cast<int*>(sJ + 4 * n4);
     longlong2* sJ2 = reinterpret_cast<longlong2*>(sJ);
     int4* sR4 = reinterpret_cast<int4*>(sR);
-    // 3D deposit staging: kStageWords words per slot, then the two slot counters
+    // 3D deposit staging: same-stencil slots, the ring, then the counters:
+    // [round & 1] same-stencil moves of the round, [2] moves ever queued
     int* sSt = sR + 4 * n4;
-    int* sCnt = sSt + kStageWords * kGpdThreads;   // [2 * (round & 1)], by round parity
+    int* sRing = sSt + kStageWords * kGpdThreads;
+    int* sCnt = sRing + kStageWords * kRing;
 
     for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
         const int c = idx / fsz, r = idx - c * fsz;
@@ -610,6 +642,22 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 
     const float dth[3] = {dth0, dth1, dth2};
     const Acc32<DIM == 2> acc{sR};
+    // adds the int32 box into the int64 box, four nodes at a time, and clears
+    // it (callers place the barriers)
+    auto fold = [&]() {
+        for (int q = threadIdx.x; q < n4; q += kGpdThreads) {
+            const int4 v = sR4[q];
+            if ((v.x | v.y | v.z | v.w) != 0) {
+                longlong2 a = sJ2[2 * q], b = sJ2[2 * q + 1];
+                a.x += v.x; a.y += v.y; b.x += v.z; b.y += v.w;
+                sJ2[2 * q] = a; sJ2[2 * q + 1] = b;
+                sR4[q] = make_int4(0, 0, 0, 0);
+            }
+        }
+    };
+    // 3D (block-uniform): moves deposited since the last fold, moves queued in
+    // and taken from the ring
+    int moves = 0, queued = 0, consumed = 0;
     const int nround = (end - beg + kGpdThreads - 1) / kGpdThreads;
     for (int rnd = 0; rnd < nround; ++rnd) {
         const int i = beg + rnd * kGpdThreads + threadIdx.x;
@@ -720,71 +768,66 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
             if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
                 atomicAdd(t.next_count + key, __popc(peers));
         }
-        // 3D: stage the round's moves, same-stencil ones from the front slots
-        // and the others from the back, so that the warps below each run one
-        // form of the deposit (most particles keep their stencil, but few
-        // warps are uniform; the slot order does not matter: integer sums)
         if constexpr (DIM == 3) {
-            int* cnt = sCnt + 2 * (rnd & 1);
+            // 3D: same-stencil moves go to this round's slots; the others to
+            // the ring, deposited 256 at a time, so that each warp runs one
+            // form of the deposit with full lanes (most particles keep their
+            // stencil, but few warps are uniform; the order of the integer
+            // sums does not matter)
+            int* cf = sCnt + (rnd & 1);
             const unsigned lane = threadIdx.x & 31u;
             const unsigned mfast = __ballot_sync(0xffffffffu, dep && same);
             const unsigned mgen = __ballot_sync(0xffffffffu, dep && !same);
             int bf = 0, bg = 0;
             if (lane == 0) {
-                if (mfast) bf = atomicAdd(cnt, __popc(mfast));
-                if (mgen) bg = atomicAdd(cnt + 1, __popc(mgen));
+                if (mfast) bf = atomicAdd(cf, __popc(mfast));
+                if (mgen) bg = atomicAdd(sCnt + 2, __popc(mgen));
             }
             bf = __shfl_sync(0xffffffffu, bf, 0);
             bg = __shfl_sync(0xffffffffu, bg, 0);
             if (dep) {
                 const unsigned below = (1u << lane) - 1u;
-                const int slot = same ? bf + __popc(mfast & below) : kGpdThreads - 1 - (bg + __popc(mgen & below));
-                int* w = sSt + slot;
-                w[0 * kGpdThreads] = mlc[0] | (mlc[1] << 16);
-                w[1 * kGpdThreads] = mlc[2] | (((mce[0] - mlc[0] + 1) | ((mce[1] - mlc[1] + 1) << 2) |
-                                                ((mce[2] - mlc[2] + 1) << 4)) << 16);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    w[(2 + d) * kGpdThreads] = __float_as_int(mf0[d]);
-                    w[(5 + d) * kGpdThreads] = __float_as_int(mf1[d]);
-                }
-                w[8 * kGpdThreads] = __float_as_int(ms);
+                if (same) stage_move(sSt + bf + __popc(mfast & below), kGpdThreads, mlc, mce, mf0, mf1, ms);
+                else      stage_move(sRing + ((bg + __popc(mgen & below)) & (kRing - 1)), kRing, mlc, mce, mf0,
+                                     mf1, ms);
             }
             __syncthreads();
-            // the other parity's counters were last read before this barrier
-            if (threadIdx.x < 2) sCnt[2 * ((rnd + 1) & 1) + threadIdx.x] = 0;
-            const int slot = threadIdx.x;
-            const bool fast = slot < cnt[0];
-            if (fast || slot >= kGpdThreads - cnt[1]) {
-                const int* w = sSt + slot;
-                const int w0 = w[0], w1 = w[kGpdThreads];
-                const int lc[3] = {w0 & 0xffff, (int)((unsigned)w0 >> 16), w1 & 0xffff};
-                const int cc = (int)((unsigned)w1 >> 16);
-                const int ce[3] = {lc[0] + (cc & 3) - 1, lc[1] + ((cc >> 2) & 3) - 1, lc[2] + ((cc >> 4) & 3) - 1};
-                const float f[3] = {__int_as_float(w[2 * kGpdThreads]), __int_as_float(w[3 * kGpdThreads]),
-                                    __int_as_float(w[4 * kGpdThreads])};
-                const float fe[3] = {__int_as_float(w[5 * kGpdThreads]), __int_as_float(w[6 * kGpdThreads]),
-                                     __int_as_float(w[7 * kGpdThreads])};
-                const float s = __int_as_float(w[8 * kGpdThreads]);
-                if (fast) deposit3d_same<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
-                else      deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
+            const int nf = *cf;
+            queued = sCnt[2];
+            // the other parity's counter was last read before this barrier
+            if (threadIdx.x == 0) sCnt[(rnd + 1) & 1] = 0;
+            if (moves + nf > kGpdThreads * t.R) { fold(); moves = 0; __syncthreads(); }
+            if ((int)threadIdx.x < nf)
+                deposit_staged3d<ORDER, true>(acc, jsz, H0, H1, sSt + threadIdx.x, kGpdThreads);
+            moves += nf;
+            if (queued - consumed >= kGpdThreads) {
+                if (moves + kGpdThreads > kGpdThreads * t.R) {
+                    __syncthreads(); fold(); moves = 0; __syncthreads();
+                }
+                deposit_staged3d<ORDER, false>(acc, jsz, H0, H1,
+                                               sRing + ((consumed + threadIdx.x) & (kRing - 1)), kRing);
+                consumed += kGpdThreads;
+                moves += kGpdThreads;
             }
             // the staging slots are rewritten by the next round
             __syncthreads();
+        } else {
+            // 2D: every R rounds (and at the end) fold the int32 box into the
+            // int64 box (block-uniform condition)
+            if ((rnd + 1) % t.R == 0 || rnd + 1 == nround) { __syncthreads(); fold(); __syncthreads(); }
         }
-        // every R rounds (and at the end) fold the int32 box into the int64
-        // box, four nodes at a time (block-uniform condition)
-        if ((rnd + 1) % t.R != 0 && rnd + 1 != nround) continue;
-        if constexpr (DIM == 2) __syncthreads();
-        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-            const int4 v = sR4[q];
-            if ((v.x | v.y | v.z | v.w) != 0) {
-                longlong2 a = sJ2[2 * q], b = sJ2[2 * q + 1];
-                a.x += v.x; a.y += v.y; b.x += v.z; b.y += v.w;
-                sJ2[2 * q] = a; sJ2[2 * q + 1] = b;
-                sR4[q] = make_int4(0, 0, 0, 0);
-            }
+    }
+    if constexpr (DIM == 3) {
+        // the moves still in the ring, then the last fold
+        const int rest = queued - consumed;
+        if (rest > 0) {
+            if (moves + rest > kGpdThreads * t.R) { fold(); __syncthreads(); }
+            if ((int)threadIdx.x < rest)
+                deposit_staged3d<ORDER, false>(acc, jsz, H0, H1,
+                                               sRing + ((consumed + threadIdx.x) & (kRing - 1)), kRing);
+            __syncthreads();
         }
+        fold();
         __syncthreads();
     }
 
