@@ -39,6 +39,9 @@ WORKLOADS = {
     "thermal3d": ("3D3V periodic thermal plasma 256^3, 8 electrons/cell (134M), v_th=0.05c, TSC, "
                   "FP32 cell+offset positions, int64 fixed-point deposit", 0),
     "thermal2d": ("2D3V periodic thermal plasma 64x64, 16 electrons/cell, v_th=0.01c, CIC", 0),
+    "laser3d": ("3D3V laser-target 512x256x256, dx=lambda/32, a0=20 w0=2lambda 8-cycle laser through "
+                "an absorbing x-min edge, e-+p slab 30 n_c at x in [4,6] lambda, 16+16 particles/cell "
+                "(134M), CIC, re-sorted every 10 steps, FP32 push + int64 fixed-point deposit", 400),
     "ensemble": ("96 independent 2D3V periodic plasmas in one ensemble (batched kernels, persistent "
                  "work-queue particle kernel, one CUDA graph per step): sides 128-768, 4-64 "
                  "particles/cell, v_th 0.005-0.1c, CIC, FP32 + fixed point", 0),
@@ -53,6 +56,8 @@ def make_workload(name, precision, seed_offset=0, ny=None, n3=None):
         wl = W.thermal3d(precision=precision, n=n3 or 256)
     elif name == "thermal2d":
         wl = W.thermal2d(precision=precision)
+    elif name == "laser3d":
+        wl = W.laser3d(precision=precision, nx=n3 or 512, ny=(n3 or 512) // 2, nz=(n3 or 512) // 2)
     else:
         raise SystemExit(f"unknown workload {name}")
     wl.seed += seed_offset
@@ -163,8 +168,9 @@ def tuned_choice(args, wl):
     if args.precision != "fp32":
         return ch
     if args.autotune:
-        best, _ = A.autotune(wl, cache=TUNED if args.autotune_save else None,
-                             log=lambda m: print(m, file=sys.stderr))
+        pre = WORKLOADS[args.workload][1] if args.pre_steps is None else args.pre_steps
+        best, _ = A.autotune(wl, cache=TUNED if args.autotune_save else None, refresh=True,
+                             log=lambda m: print(m, file=sys.stderr), pre_steps=pre)
         ch = {"tile": list(best.tile), "block_particles": best.block_particles,
               "sort_interval": best.sort_interval, "source": "autotune"}
     elif os.path.exists(TUNED):
@@ -173,6 +179,8 @@ def tuned_choice(args, wl):
             c = rec["choice"]
             ch = {"tile": list(c["tile"]), "block_particles": c["block_particles"],
                   "sort_interval": c["sort_interval"], "source": "autotuner results"}
+    if ch["source"] == "defaults" and args.workload == "laser3d":
+        ch.update(sort_interval=10, source="configuration (re-sort every 10 steps)")
     if args.tile:
         ch.update(tile=[int(v) for v in args.tile.split("x")], source="command line")
     if args.block_particles:
@@ -423,14 +431,18 @@ def run_e2e(args, st):
 # ------------------------------------------------------------------ the oracle
 def oracle_sample(args, budget_s, max_steps):
     """Time the FP64 CPU oracle, as it stands (one thread), on a bounded
-    sample of the workload: the full x extent with the first 16 rows (2D) or
-    a 32^3 box (3D), same cell size, density profile and particles per cell."""
+    sample of the workload: the full x extent with the first 16 rows (2D),
+    the full x extent with 8 x 8 cells across (3D laser-target: the slab lies
+    along x) or a 32^3 box (3D thermal), same cell size, density profile and
+    particles per cell."""
     import numpy as np
     from oracle import oracle as O
     from paper_2607_13507_b300 import workloads as W
     wl = make_workload(args.workload, "fp64")
     if wl.dim == 2:
         sample = dict(n=(wl.n[0], min(16, wl.n[1])))
+    elif wl.laser is not None:
+        sample = dict(n=(wl.n[0], 8, 8))
     else:
         sample = dict(n=(32, 32, 32))
     wl.n = sample["n"]

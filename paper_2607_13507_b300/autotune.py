@@ -2,11 +2,14 @@
 sort interval.
 
 Each candidate is timed on the actual workload for a few full steps
-(CUDA events on the stepping stream, after warm-up); the fastest wins.  The
-search is staged to keep it short: tile shape x sort interval at the default
-block size, then the block size for the best pair.  Results can be cached in
-a JSON file keyed by the workload's signature (grid, cell sizes, shape order,
-species, particles per cell, boundaries).
+(CUDA events on the stepping stream, after warm-up); the fastest wins.  With
+pre_steps > 0 the workload is first advanced that many steps (for a laser,
+until the pulse is on the target) and every candidate starts from that
+snapshot of particles and fields, so the choice fits the state the benchmark
+times.  The search is staged to keep it short: tile shape x sort interval at
+the default block size, then the block size for the best pair.  Results can
+be cached in a JSON file keyed by the workload's signature (grid, cell sizes,
+shape order, species, particles per cell, boundaries).
 """
 from __future__ import annotations
 
@@ -15,6 +18,7 @@ import json
 import os
 from dataclasses import asdict, dataclass
 
+import numpy as np
 import torch
 
 from . import lpic
@@ -41,20 +45,60 @@ def default_tiles(dim: int, n: tuple) -> list:
     return [t for t in cands if all(t[d] <= n[d] for d in range(dim))]
 
 
-def time_choice(wl, parts, ch: Choice, steps=6, warmup=2, stream=None, device="cuda") -> float:
-    """Milliseconds per full step of the workload with this choice."""
+def snapshot(wl, parts, pre_steps, stream, device="cuda"):
+    """Advances the workload pre_steps steps (default launch choice) and
+    returns its particles (leapfrog-staggered state) and fields."""
+    G = lpic.grid_for(wl, lpic.FP32_FIXED, device=device)
+    try:
+        for p in parts:
+            G.add_species(p, stream=stream)
+        for s in range(pre_steps):
+            G.step(s * G.dt, stream)
+        stream.synchronize()
+        n = wl.n
+        out = []
+        for sp, p in zip(G.species, parts):
+            st = sp.state(stream)
+            c = st["cell"].astype(np.int64)
+            coords = [c % n[0], (c // n[0]) % n[1]] + ([c // (n[0] * n[1])] if wl.dim == 3 else [])
+            out.append(W.Particles(p.q, p.m, np.stack(coords).astype(np.int32), st["off"], st["u"],
+                                   st["w"], st["id"]))
+        fields = {"E": [t.clone() for t in G.E], "B": [t.clone() for t in G.B],
+                  "J": [t.clone() for t in G.J], "F": G.info().fixed_shift, "step": pre_steps}
+        return out, fields
+    finally:
+        G.close()
+        del G
+        torch.cuda.empty_cache()
+
+
+def time_choice(wl, parts, ch: Choice, steps=6, warmup=2, stream=None, device="cuda", fields=None) -> float:
+    """Milliseconds per full step of the workload with this choice (from a
+    snapshot when `fields` is given)."""
     st = stream or torch.cuda.current_stream()
     G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=ch.tile, device=device,
                       block_particles=ch.block_particles, sort_interval=ch.sort_interval)
     try:
+        s0 = 0
         for p in parts:
-            G.add_species(p, stream=st)
-        for s in range(warmup):
+            G.add_species(p, staggered=fields is not None, stream=st)
+        if fields is not None:
+            s0 = fields["step"]
+            for name in ("E", "B"):
+                for dst, src in zip(getattr(G, name), fields[name]):
+                    dst.copy_(src)
+            if G.info().fixed_shift == fields["F"]:
+                for dst, src in zip(G.J, fields["J"]):
+                    dst.copy_(src)
+        for s in range(s0, s0 + warmup):
             G.step(s * G.dt, st)
+        # a whole number of sort intervals, so every choice pays its sorts
+        k = max(1, ch.sort_interval)
+        steps = k * ((steps + k - 1) // k)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st.synchronize()
         a.record(st)
-        for s in range(warmup, warmup + steps):
+        for s in range(s0 + warmup, s0 + warmup + steps):
             G.step(s * G.dt, st)
         b.record(st)
         st.synchronize()
@@ -67,11 +111,13 @@ def time_choice(wl, parts, ch: Choice, steps=6, warmup=2, stream=None, device="c
         torch.cuda.empty_cache()
 
 
-def autotune(wl: W.Workload, tiles=None, intervals=(1, 2, 3), block_sizes=(2048, 4096, 8192),
-             steps=6, warmup=2, cache: str | None = None, log=None) -> tuple:
-    """Returns (best Choice, list of (Choice, ms per step))."""
+def autotune(wl: W.Workload, tiles=None, intervals=(1, 2, 4, 8), block_sizes=(2048, 4096, 8192),
+             steps=6, warmup=2, cache: str | None = None, log=None, pre_steps=0,
+             refresh=False) -> tuple:
+    """Returns (best Choice, list of (Choice, ms per step)); a cached result
+    is used unless refresh is set."""
     key = signature(wl)
-    if cache and os.path.exists(cache):
+    if cache and not refresh and os.path.exists(cache):
         try:
             rec = json.load(open(cache)).get(key)
             if rec:
@@ -82,9 +128,12 @@ def autotune(wl: W.Workload, tiles=None, intervals=(1, 2, 3), block_sizes=(2048,
     parts = W.load_all(wl)
     stream = torch.cuda.Stream()
     table = []
+    fields = None
+    if pre_steps > 0:
+        parts, fields = snapshot(wl, parts, pre_steps, stream)
 
     def measure(ch):
-        ms = time_choice(wl, parts, ch, steps, warmup, stream)
+        ms = time_choice(wl, parts, ch, steps, warmup, stream, fields=fields)
         table.append((ch, ms))
         if log:
             log(f"autotune {ch} -> {ms:.3f} ms/step")

@@ -71,6 +71,12 @@ def test_fp64_laser2d_absorbing_small():
     _fp64_parity(wl, 80, 1e-10)
 
 
+def test_fp64_laser3d_absorbing_small():
+    """3D laser-target (a0 = 20, 30 n_c slab, CIC) through the Mur x edges."""
+    wl = W.laser3d(nx=64, ny=16, nz=16, ppc=1, precision="fp64")
+    _fp64_parity(wl, 60, 1e-10)
+
+
 def _fp32_case(wl, steps, tile=None):
     from paper_2607_13507_b300 import lpic
     parts = W.load_all(wl)
@@ -119,6 +125,30 @@ def test_fp32_laser2d_small_against_oracle():
         eb = rel_l2(G.B[c].cpu().numpy(), g.B[c])
         assert ee < 1e-3, ("E", c, ee)
         assert eb < 1e-3, ("B", c, eb)
+
+
+def test_fp32_laser3d_small_against_oracle():
+    """3D laser-target, CIC, re-sorted every 10 steps as in the full-size
+    configuration: 60 steps against the oracle (same random-walk bound as the
+    2D laser case)."""
+    from paper_2607_13507_b300 import lpic
+    wl = W.laser3d(nx=64, ny=16, nz=16, ppc=1, precision="fp32")
+    steps = 60
+    parts = W.load_all(wl)
+    g, sps = oracle_case(wl, parts)
+    G = lpic.grid_for(wl, lpic.FP32_FIXED, sort_interval=10)
+    for p in parts:
+        G.add_species(p)
+    run_oracle(g, sps, steps)
+    run_gpu(G, steps)
+    assert G.check_status() == 0
+    for c in range(3):
+        ee = rel_l2(G.E[c].cpu().numpy(), g.E[c])
+        eb = rel_l2(G.B[c].cpu().numpy(), g.B[c])
+        assert ee < 1e-3, ("E", c, ee)
+        assert eb < 1e-3, ("B", c, eb)
+    xg, xo, ug, uo = match_particles(G, G.species[0], sps[0], wl)
+    assert rel_l2(ug, uo) < 1e-3
 
 
 def _div_int(G):
@@ -335,7 +365,7 @@ def test_graph_replay_with_laser_clock():
         assert rel_l2(Gb.E[c].cpu().numpy(), Ga.E[c].cpu().numpy()) < 1e-5
 
 
-@pytest.mark.parametrize("case", ["thermal2d", "laser2d", "thermal3d", "thermal3d_escape"])
+@pytest.mark.parametrize("case", ["thermal2d", "laser2d", "thermal3d", "thermal3d_escape", "laser3d"])
 def test_sort_interval_gives_bitwise_identical_state(case):
     """Sorting every K steps instead of every step changes only the order in
     which particles are visited: every particle's update depends on the
@@ -355,9 +385,12 @@ def test_sort_interval_gives_bitwise_identical_state(case):
     elif case == "thermal3d":
         wl = W.thermal3d(n=16, ppc=2, vth=0.3, order=2)
         tile = (4, 4, 4)            # the drift margin enlarges the boxes
-    else:
+    elif case == "thermal3d_escape":
         wl = W.thermal3d(n=16, ppc=2, vth=0.5, order=2)
         tile, K = (8, 8, 8), 10
+    else:
+        wl = W.laser3d(nx=64, ny=16, nz=16, ppc=1, precision="fp32")
+        K = 10
     parts = W.load_all(wl)
     G1 = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile)
     GK = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile, sort_interval=K)
