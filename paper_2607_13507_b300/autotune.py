@@ -7,7 +7,7 @@ pre_steps > 0 the workload is first advanced that many steps (for a laser,
 until the pulse is on the target) and every candidate starts from that
 snapshot of particles and fields, so the choice fits the state the benchmark
 times.  The search is staged to keep it short: tile shape x sort interval at
-the default block size, then the block size for the best pair.  Results can
+the default block size, then the other block sizes for the three best pairs.  Results can
 be cached in a JSON file keyed by the workload's signature (grid, cell sizes,
 shape order, species, particles per cell, boundaries).
 """
@@ -141,12 +141,14 @@ def autotune(wl: W.Workload, tiles=None, intervals=(1, 2, 4, 8), block_sizes=(20
 
     tiles = tiles or default_tiles(wl.dim, wl.n)
     first = [Choice(t, 4096, k) for t, k in itertools.product(tiles, intervals)]
-    best = min(first, key=measure)
-    for P in block_sizes:
-        if P != best.block_particles:
-            ch = Choice(best.tile, P, best.sort_interval)
-            if measure(ch) < min(ms for c, ms in table if c == best):
-                best = ch
+    for ch in first:
+        measure(ch)
+    # the other block sizes for the three best (tile, interval) pairs
+    for c0, _ in sorted(table, key=lambda e: e[1])[:3]:
+        for P in block_sizes:
+            if P != c0.block_particles:
+                measure(Choice(c0.tile, P, c0.sort_interval))
+    best = min(table, key=lambda e: e[1])[0]
     if cache:
         data = {}
         if os.path.exists(cache):
