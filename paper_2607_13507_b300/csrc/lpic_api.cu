@@ -173,6 +173,18 @@ __global__ void k_absmax_f64(const double* w, const int* n, unsigned long long* 
     atomicMax(out, m);
 }
 
+// Divisors of the tile kernel's field and current boxes (T + 2m + 4 and
+// T + 2m + 5 nodes per dimension).
+void box_divisors(const lpic_grid* g, Tiles& t) {
+    const int G0 = g->T[0] + 2 * g->m[0] + 4, G1 = g->T[1] + 2 * g->m[1] + 4;
+    const int G2 = g->d.dim == 3 ? g->T[2] + 2 * g->m[2] + 4 : 1;
+    const int H0 = G0 + 1, H1 = G1 + 1, H2 = g->d.dim == 3 ? G2 + 1 : 1;
+    t.fG0 = make_fastdiv((unsigned)G0); t.fG1 = make_fastdiv((unsigned)G1);
+    t.fF = make_fastdiv((unsigned)(G0 * G1 * G2));
+    t.fH0 = make_fastdiv((unsigned)H0); t.fH1 = make_fastdiv((unsigned)H1);
+    t.fJ = make_fastdiv((unsigned)(H0 * H1 * H2));
+}
+
 // tile-kernel instance and its dynamic shared memory
 template <int DIM, int ORDER>
 lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
@@ -192,6 +204,7 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_n
     t.nitems = s.d_nitems;
     t.P = g->P;
     t.R = g->R;
+    box_divisors(g, t);
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
     GpdArgs A{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
@@ -1042,6 +1055,7 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
                 Tiles t{};
                 for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; t.m[d] = g->m[d]; t.fT[d] = g->fT[d]; }
                 t.start = s.d_start; t.items = s.d_items; t.nitems = s.d_nitems; t.P = g->P; t.R = g->R;
+                box_divisors(g, t);
                 t.next_count = s.d_count; t.esc = s.d_esc; t.nesc = s.d_nesc;
                 // the push runs after the step's sort flipped the parity: it
                 // reads the buffer the particles were sorted into

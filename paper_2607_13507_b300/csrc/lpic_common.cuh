@@ -20,6 +20,13 @@ __host__ __device__ inline int wrapi(int i, int n) { return i < 0 ? i + n : (i >
 // Wrap any index into [0, n).
 __host__ __device__ inline int wrapm(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
+// wrapm with a cheap path for indices off by less than one period.
+__host__ __device__ inline int wrapn(int i, int n) {
+    if (i < 0) { i += n; if (i < 0) i = wrapm(i, n); }
+    else if (i >= n) { i -= n; if (i >= n) i = wrapm(i, n); }
+    return i;
+}
+
 // Linear field index of node (i, j, k); periodic dimensions wrap, an
 // absorbing x index outside [0, fx) yields -1.
 __device__ inline long long fidx(const Geo& g, int i, int j, int k) {
@@ -30,6 +37,19 @@ __device__ inline long long fidx(const Geo& g, int i, int j, int k) {
     }
     j = wrapm(j, g.ny);
     k = (g.dim == 3) ? wrapm(k, g.nz) : 0;
+    return ((long long)k * g.ny + j) * g.fx + i;
+}
+
+// fidx for the loops over a tile's boxes, whose indices are mostly within
+// one period of the grid.
+__device__ inline long long fidx_near(const Geo& g, int i, int j, int k) {
+    if (g.absorb) {
+        if (i < 0 || i >= g.fx) return -1;
+    } else {
+        i = wrapn(i, g.nx);
+    }
+    j = wrapn(j, g.ny);
+    k = (g.dim == 3) ? wrapn(k, g.nz) : 0;
     return ((long long)k * g.ny + j) * g.fx + i;
 }
 

@@ -63,6 +63,8 @@ struct Tiles {
     int P;               // particles per chunk
     int R;               // rounds between folds of the int32 current box
     FastDiv fT[3];       // division by T (tile keys of the next sort)
+    FastDiv fG0, fG1, fF;  // division by the field box rows, planes, size
+    FastDiv fH0, fH1, fJ;  // and by those of the current box
     int* next_count;     // if set: histogram of the new tile keys for the next sort
     int* esc;            // indices of particles beyond the tile's margin ...
     int* nesc;           // ... and their count (pushed by k_gpd32_escape)
@@ -625,9 +627,10 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     int* sCnt = sRing + kStageWords * kRing;
 
     for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
-        const int c = idx / fsz, r = idx - c * fsz;
-        const int lx = r % G0, ly = (r / G0) % G1, lz = r / (G0 * G1);
-        const long long m = fidx(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
+        const int c = fdiv(idx, t.fF), r = idx - c * fsz;
+        const int q = fdiv(r, t.fG0), lx = r - q * G0;
+        const int lz = (DIM == 3) ? fdiv(q, t.fG1) : 0, ly = q - lz * G1;
+        const long long m = fidx_near(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
         const float* src = c == 0 ? E.p[0] : c == 1 ? E.p[1] : c == 2 ? E.p[2]
                          : c == 3 ? B.p[0] : c == 4 ? B.p[1] : B.p[2];
         sF[idx] = (m < 0) ? 0.0f : src[m];
@@ -836,9 +839,10 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     for (int idx = threadIdx.x; idx < 3 * jsz; idx += blockDim.x) {
         const long long v = sJ[idx];
         if (v == 0) continue;
-        const int c = idx / jsz, r = idx - c * jsz;
-        const int lx = r % H0, ly = (r / H0) % H1, lz = r / (H0 * H1);
-        const long long m = fidx(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
+        const int c = fdiv(idx, t.fJ), r = idx - c * jsz;
+        const int q = fdiv(r, t.fH0), lx = r - q * H0;
+        const int lz = (DIM == 3) ? fdiv(q, t.fH1) : 0, ly = q - lz * H1;
+        const long long m = fidx_near(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
         if (m < 0) { outside = true; continue; }
         unsigned long long* dst = c == 0 ? J.p[0] : c == 1 ? J.p[1] : J.p[2];
         atomicAdd(dst + m, static_cast<unsigned long long>(v));
