@@ -464,7 +464,7 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     auto smem_for = [&](const int* m) {
         long long G = 1, H = 1;
         for (int k = 0; k < d.dim; ++k) { G *= g->T[k] + 2 * m[k] + 4; H *= g->T[k] + 2 * m[k] + 5; }
-        return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)((3 * H + 3) & ~3LL) * 12 + (d.dim == 3 ? (size_t)kStageBytes : 0);
+        return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)((3 * H + 3) & ~3LL) * 12 + (d.dim == 3 ? (size_t)kStageBytes : (size_t)kPrefBytes);
     };
     while (smem_for(g->m) > 227 * 1024 && (g->m[0] > 0 || g->m[1] > 0 || g->m[2] > 0))
         for (int k = 0; k < 3; ++k) g->m[k] = g->m[k] > 0 ? g->m[k] - 1 : 0;

@@ -526,8 +526,8 @@ struct LoadGlobal {
 
 // ----------------------------------------------------------- the tile kernel
 // Shared memory: 6 field boxes (T+4 per dimension, halo 2 below and 2 above),
-// an int64 total box and an int32 round box for J (T+5 per dimension), and in
-// 3D the deposit staging of one round.
+// an int64 total box and an int32 round box for J (T+5 per dimension), then in
+// 3D the deposit staging and in 2D the particle prefetch buffers.
 // Blocks per SM the register allocation targets (2D: the kernel fits 80
 // registers with negligible spills; 3D: 128 registers, a few spills, measured
 // 1.57x faster than one block per SM at 255 registers).
@@ -546,6 +546,18 @@ constexpr int kGpdThreads = 256;
 constexpr int kStageWords = 9;
 constexpr int kRing = 2 * kGpdThreads;
 constexpr int kStageBytes = (kStageWords * (kGpdThreads + kRing) + 4) * 4;
+// 2D: the next round's particles (cell, 2 offsets, 3 momenta, weight) are
+// copied into shared memory asynchronously while the current round runs, two
+// buffers of one word per thread and array.
+constexpr int kPrefWords = 7;
+constexpr int kPrefBytes = 2 * kPrefWords * kGpdThreads * 4;
+
+__device__ inline void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // One staged move: write / read kStageWords words at slot stride `stride`.
 __device__ inline void stage_move(int* w, int stride, const int* lc, const int* ce, const float* f0,
@@ -662,9 +674,39 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     // and taken from the ring
     int moves = 0, queued = 0, consumed = 0;
     const int nround = (end - beg + kGpdThreads - 1) / kGpdThreads;
+    // 2D: this thread's particle of round r, prefetched into buffer r & 1
+    int* sPf = sR + 4 * n4;
+    auto prefetch = [&](int r) {
+        const int ii = beg + r * kGpdThreads + threadIdx.x;
+        if (r < nround && ii < end) {
+            int* b = sPf + (r & 1) * kPrefWords * kGpdThreads + threadIdx.x;
+            cp_async4(b, p.cell + ii);
+            cp_async4(b + 1 * kGpdThreads, p.off[0] + ii);
+            cp_async4(b + 2 * kGpdThreads, p.off[1] + ii);
+            cp_async4(b + 3 * kGpdThreads, p.u[0] + ii);
+            cp_async4(b + 4 * kGpdThreads, p.u[1] + ii);
+            cp_async4(b + 5 * kGpdThreads, p.u[2] + ii);
+            cp_async4(b + 6 * kGpdThreads, p.w + ii);
+        }
+        cp_async_commit();
+    };
+    if constexpr (DIM == 2) prefetch(0);
     for (int rnd = 0; rnd < nround; ++rnd) {
         const int i = beg + rnd * kGpdThreads + threadIdx.x;
-        const int cell = (i < end) ? p.cell[i] : -1;
+        int cell = -1;
+        float pf[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // 2D: off0, off1, u0, u1, u2, w
+        if constexpr (DIM == 2) {
+            cp_async_wait_all();
+            const int* b = sPf + (rnd & 1) * kPrefWords * kGpdThreads + threadIdx.x;
+            if (i < end) {
+                cell = b[0];
+#pragma unroll
+                for (int k2 = 0; k2 < 6; ++k2) pf[k2] = __int_as_float(b[(1 + k2) * kGpdThreads]);
+            }
+            prefetch(rnd + 1);
+        } else {
+            cell = (i < end) ? p.cell[i] : -1;
+        }
         int cell_out = cell;      // the particle's cell after this round (-1: removed)
         // 3D: the move this particle deposits (if dep), staged below
         bool dep = false, same = false;
@@ -692,9 +734,14 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 t.esc[atomicAdd(t.nesc, 1)] = i;
                 cell_out = -1;
             } else {
-                float f[3] = {p.off[0][i], p.off[1][i], DIM == 3 ? p.off[2][i] : 0.0f};
-                float ux = p.u[0][i], uy = p.u[1][i], uz = p.u[2][i];
-                const float w = p.w[i];
+                float f[3], ux, uy, uz, w;
+                if constexpr (DIM == 2) {
+                    f[0] = pf[0]; f[1] = pf[1]; f[2] = 0.0f;
+                    ux = pf[2]; uy = pf[3]; uz = pf[4]; w = pf[5];
+                } else {
+                    f[0] = p.off[0][i]; f[1] = p.off[1][i]; f[2] = p.off[2][i];
+                    ux = p.u[0][i]; uy = p.u[1][i]; uz = p.u[2][i]; w = p.w[i];
+                }
 
                 // gather at x^{n+1/2} from the shared-memory halo
                 const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
