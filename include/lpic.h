@@ -145,8 +145,9 @@ size_t lpic_species_bytes(int dim, int precision, long long capacity);
 
 /* Create a grid from a descriptor (Sec. 3.2 grid; Sec. 2.1 Patches
  * replaced by one guard-less global grid per instance).  Checks the
- * descriptor (dimensions, Courant limit, shape order, laser needs absorbing
- * x, tile shape) and allocates the library's scratch.  Synchronous. */
+ * descriptor (dimensions: at least 4 cells each and field arrays of fewer
+ * than 2^31 nodes; Courant limit, shape order, laser needs absorbing x, tile
+ * shape) and allocates the library's scratch.  Synchronous. */
 lpic_status lpic_create_grid(const lpic_grid_desc *desc, lpic_grid_t *out);
 
 /* Free the library's scratch (not the caller's buffers).  Synchronises the

@@ -91,6 +91,7 @@ struct lpic_grid {
     std::vector<Species> sp;
     unsigned* d_status = nullptr;
     void* d_mur = nullptr;
+    double* d_lprof = nullptr;   // transverse laser profile on the x-min plane
     double* d_acc = nullptr;
     unsigned long long* d_cnt = nullptr;
     bool started = false;
@@ -247,6 +248,8 @@ lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st, cons
     a.rdz = (R)(DIM == 3 ? 1.0 / g->d.dz : 0.0);
     a.tau = (R)tau;
     for (int c = 0; c < 3; ++c) a.jfac[c] = tau * (g->d.precision == LPIC_FP32_FIXED ? g->jscale[c] : 1.0);
+    a.dfx = make_fastdiv((unsigned)g->geo.fx);
+    a.dny = make_fastdiv((unsigned)g->d.ny);
     const int nb = grid_blocks(g->nfield, g->nsm, 16);
     const int plane = g->d.ny * (DIM == 3 ? g->d.nz : 1);
     Ptr3<R> Ep;
@@ -260,7 +263,7 @@ lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st, cons
         LPIC_LAUNCHED("k_update_E");
         if (g->geo.absorb) {
             k_mur_apply<R><<<grid_blocks(2LL * plane, g->nsm), 256, 0, st>>>(
-                g->geo, Ep, static_cast<const R*>(g->d_mur), g->laser, t, clock, tau);
+                g->geo, Ep, static_cast<const R*>(g->d_mur), g->laser, g->d_lprof, t, clock, tau);
             LPIC_LAUNCHED("k_mur_apply");
         }
         return LPIC_OK;
@@ -406,7 +409,8 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     const int nz = (d.dim == 3) ? d.nz : 1;
     if (d.nx < 4 || d.ny < 4 || nz < 1 || (d.dim == 3 && d.nz < 4))
         return fail(LPIC_EINVAL, "grid too small (%d x %d x %d), need >= 4 cells per dimension", d.nx, d.ny, nz);
-    if ((long long)d.nx * d.ny * nz >= (1LL << 31)) return fail(LPIC_EINVAL, "more than 2^31 cells");
+    if ((long long)(d.nx + 1) * d.ny * nz >= (1LL << 31))
+        return fail(LPIC_EINVAL, "field arrays of 2^31 nodes or more (%d x %d x %d cells)", d.nx, d.ny, nz);
     if (!(d.dx > 0) || !(d.dy > 0) || (d.dim == 3 && !(d.dz > 0)) || !(d.dt > 0))
         return fail(LPIC_EINVAL, "cell sizes and dt must be positive");
     double s2 = 1.0 / (d.dx * d.dx) + 1.0 / (d.dy * d.dy) + (d.dim == 3 ? 1.0 / (d.dz * d.dz) : 0.0);
@@ -487,9 +491,14 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         cudaMalloc(&g->d_clock, 64) != cudaSuccess ||
         cudaMalloc(&g->d_acc, 64) != cudaSuccess ||
         cudaMalloc(&g->d_cnt, 64) != cudaSuccess ||
-        (d.absorb_x && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess)) {
+        (d.absorb_x && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess) ||
+        (g->laser.on && cudaMalloc(&g->d_lprof, sizeof(double) * plane) != cudaSuccess)) {
         lpic_destroy_grid(g);
         return fail(LPIC_ENOMEM, "scratch allocation failed");
+    }
+    if (g->laser.on) {
+        k_laser_profile<<<grid_blocks(plane, g->nsm), 256>>>(g->geo, g->laser, g->d_lprof);
+        if (cudaGetLastError() != cudaSuccess) { lpic_destroy_grid(g); return fail(LPIC_ECUDA, "laser profile"); }
     }
     if (cudaMemset(g->d_status, 0, 64) != cudaSuccess || cudaMemset(g->d_clock, 0, 64) != cudaSuccess) {
         lpic_destroy_grid(g);
@@ -515,7 +524,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     }
     for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : g->ev) cudaEventDestroy(e);
-    cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur);
+    cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur); cudaFree(g->d_lprof);
     cudaFree(g->d_clock);
     delete g;
     return LPIC_OK;
@@ -1040,6 +1049,8 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
         f.a.rdz = (float)(g->d.dim == 3 ? 1.0 / g->d.dz : 0.0);
         f.a.tau = (float)tau;
         for (int c = 0; c < 3; ++c) f.a.jfac[c] = tau * g->jscale[c];
+        f.a.dfx = make_fastdiv((unsigned)g->geo.fx);
+        f.a.dny = make_fastdiv((unsigned)g->d.ny);
         f.nfield = g->nfield;
         e->max_field = std::max(e->max_field, g->nfield);
         e->max_ntiles = std::max(e->max_ntiles, g->ntiles);

@@ -205,14 +205,19 @@ struct Laser {
     int on; double a0, w0, tau, omega, yc, zc;
 };
 
-__device__ inline double laser_ey(const Laser& L, int dim, double x, double y, double z, double t) {
-    const double s = t - x;
-    if (!L.on || s <= 0.0 || s >= L.tau) return 0.0;
+// The laser's E_y = a0 env(s) exp(-r^2 / w0^2) sin(omega s), s = t - x, split
+// into its time factors (a0 env, sin) and its transverse profile.
+__device__ inline void laser_time(const Laser& L, double s, double& a0env, double& sn) {
+    if (!L.on || s <= 0.0 || s >= L.tau) { a0env = 0.0; sn = 0.0; return; }
     double env = sin(3.14159265358979323846 * s / L.tau);
     env *= env;
+    a0env = L.a0 * env;
+    sn = sin(L.omega * s);
+}
+__device__ inline double laser_profile(const Laser& L, int dim, double y, double z) {
     double r2 = (y - L.yc) * (y - L.yc);
     if (dim == 3) r2 += (z - L.zc) * (z - L.zc);
-    return L.a0 * env * exp(-r2 / (L.w0 * L.w0)) * sin(L.omega * s);
+    return exp(-r2 / (L.w0 * L.w0));
 }
 
 }  // namespace lpic

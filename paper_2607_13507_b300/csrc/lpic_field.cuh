@@ -21,16 +21,32 @@ struct FieldArgs {
     R rdx, rdy, rdz;      // 1 / h
     R tau;                // dt / 2
     double jfac[3];       // tau * (J units -> field units)
+    FastDiv dfx, dny;     // division by the stored x extent and by ny
 };
+
+// tau J in field units: FP64 fields convert exactly in double; FP32 fields
+// (J int64 fixed point) convert in single precision (one rounding of J and
+// one of the product, well inside the FP32 path's tolerance).
+template <typename R, typename JT>
+__device__ inline R jterm(JT v, double f) {
+    if constexpr (sizeof(R) == 4 && sizeof(JT) == 8) return __ll2float_rn((long long)v) * (float)f;
+    else return (R)((double)v * f);
+}
+
+// Node n = (k ny + j) fx + i of a field array (fewer than 2^31 nodes).
+__device__ inline void node_ijk(int n, const FastDiv& dfx, const FastDiv& dny, int& i, int& j, int& k) {
+    const int r = fdiv(n, dfx);
+    i = n - r * (int)dfx.d;
+    k = fdiv(r, dny);
+    j = r - k * (int)dny.d;
+}
 
 template <int DIM, typename R, typename JT>
 __device__ inline void update_E_range(const Geo& g, const FieldArgs<R, JT>& a, long long n0, long long step) {
     const long long total = (long long)g.fx * g.ny * (DIM == 3 ? g.nz : 1);
     for (long long n = n0; n < total; n += step) {
-        const int i = (int)(n % g.fx);
-        const long long r = n / g.fx;
-        const int j = (int)(r % g.ny);
-        const int k = (int)(r / g.ny);
+        int i, j, k;
+        node_ijk((int)n, a.dfx, a.dny, i, j, k);
         const long long nj = (j == 0) ? n + (long long)(g.ny - 1) * g.fx : n - g.fx;
         long long nk = n;
         if (DIM == 3) nk = (k == 0) ? n + (long long)(g.nz - 1) * g.ny * g.fx : n - (long long)g.ny * g.fx;
@@ -42,16 +58,16 @@ __device__ inline void update_E_range(const Geo& g, const FieldArgs<R, JT>& a, l
         if (!(g.absorb && i == g.nx)) {
             R cb = (a.B[2][n] - a.B[2][nj]) * a.rdy;
             if (DIM == 3) cb -= (a.B[1][n] - a.B[1][nk]) * a.rdz;
-            a.E[0][n] += a.tau * cb - (R)((double)a.J[0][n] * a.jfac[0]);
+            a.E[0][n] += a.tau * cb - jterm<R>(a.J[0][n], a.jfac[0]);
         }
         if (!edge) {
             // E_y at (i, j+1/2, k)
             R cb = -(a.B[2][n] - a.B[2][ni]) * a.rdx;
             if (DIM == 3) cb += (a.B[0][n] - a.B[0][nk]) * a.rdz;
-            a.E[1][n] += a.tau * cb - (R)((double)a.J[1][n] * a.jfac[1]);
+            a.E[1][n] += a.tau * cb - jterm<R>(a.J[1][n], a.jfac[1]);
             // E_z at (i, j, k+1/2)
             const R cz = (a.B[1][n] - a.B[1][ni]) * a.rdx - (a.B[0][n] - a.B[0][nj]) * a.rdy;
-            a.E[2][n] += a.tau * cz - (R)((double)a.J[2][n] * a.jfac[2]);
+            a.E[2][n] += a.tau * cz - jterm<R>(a.J[2][n], a.jfac[2]);
         }
     }
 }
@@ -60,10 +76,8 @@ template <int DIM, typename R, typename JT>
 __device__ inline void update_B_range(const Geo& g, const FieldArgs<R, JT>& a, long long n0, long long step) {
     const long long total = (long long)g.fx * g.ny * (DIM == 3 ? g.nz : 1);
     for (long long n = n0; n < total; n += step) {
-        const int i = (int)(n % g.fx);
-        const long long r = n / g.fx;
-        const int j = (int)(r % g.ny);
-        const int k = (int)(r / g.ny);
+        int i, j, k;
+        node_ijk((int)n, a.dfx, a.dny, i, j, k);
         const long long nj = (j == g.ny - 1) ? n - (long long)(g.ny - 1) * g.fx : n + g.fx;
         long long nk = n;
         if (DIM == 3)
@@ -112,14 +126,32 @@ __global__ void k_mur_save(Geo g, Ptr3<R> E, R* old) {
     }
 }
 
+// Transverse laser profile of each row (j, k) of the x-min plane; E_y sits
+// at y = (j + 1/2) dy, z = k dz.
+__global__ void k_laser_profile(Geo g, Laser L, double* prof) {
+    const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < plane; q += gridDim.x * blockDim.x) {
+        const int j = q % g.ny, k = q / g.ny;
+        prof[q] = laser_profile(L, g.dim, (j + 0.5) * g.dy, k * g.dz);
+    }
+}
+
 // t_old = *clock + t_arg when a device clock is given (graph replay), else t_arg.
+// The laser's time factors at x = 0 and x = dx, old and new time, are the same
+// for every row: four threads of each block evaluate them once.
 template <typename R>
-__global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, double t_arg,
+__global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, const double* prof, double t_arg,
                             const double* clock, double tau) {
+    __shared__ double s_tf[4][2];
     const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
     const double c1 = (tau - g.dx) / (tau + g.dx);
     const double t_old = clock ? *clock + t_arg : t_arg;
     const double t_new = t_old + tau;
+    if (threadIdx.x < 4) {
+        const double tt = (threadIdx.x < 2) ? t_old : t_new;
+        laser_time(L, tt - ((threadIdx.x & 1) ? g.dx : 0.0), s_tf[threadIdx.x][0], s_tf[threadIdx.x][1]);
+    }
+    __syncthreads();
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * plane; t += gridDim.x * blockDim.x) {
         const int q = t % plane;
         const int c = 1 + t / plane;
@@ -127,12 +159,11 @@ __global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, double t_ar
         const long long row = (long long)q * g.fx;
         double i0o = 0, i1o = 0, i0n = 0, i1n = 0;
         if (L.on && c == 1) {
-            const int j = q % g.ny, k = q / g.ny;
-            const double y = (j + 0.5) * g.dy, z = k * g.dz;
-            i0o = laser_ey(L, g.dim, 0.0, y, z, t_old);
-            i1o = laser_ey(L, g.dim, g.dx, y, z, t_old);
-            i0n = laser_ey(L, g.dim, 0.0, y, z, t_new);
-            i1n = laser_ey(L, g.dim, g.dx, y, z, t_new);
+            const double pr = prof[q];
+            i0o = s_tf[0][0] * pr * s_tf[0][1];
+            i1o = s_tf[1][0] * pr * s_tf[1][1];
+            i0n = s_tf[2][0] * pr * s_tf[2][1];
+            i1n = s_tf[3][0] * pr * s_tf[3][1];
         }
         const double e1n = (double)E.p[c][row + 1];
         E.p[c][row] = (R)(i0n + ((double)o[1 * plane + q] - i1o)
