@@ -217,6 +217,16 @@ lpic_status lpic_graph_steps(lpic_grid_t grid, int nsteps, cudaStream_t stream);
  * arithmetic as the deposit (rho = rho_int * rho_scale). */
 lpic_status lpic_deposit_charge(lpic_grid_t grid, int species_id, void *rho, cudaStream_t stream);
 
+/* Gauss's law diagnostic (Sec. 3.2; Sec. 4.1 checks charge conservation):
+ * the discrete divergence of the current E at the integer nodes,
+ * sum_d (E_d(i+1/2) - E_d(i-1/2)) / h_d, in double, written to the caller's
+ * device array out[nz][ny][fx] (overwritten; periodic wrap, E_x = 0 below an
+ * absorbing x-min edge).  After each step the residual
+ * div E - (rho(x^{n+3/2}) + rho(x^{n+1/2})) / 2 of the stored positions before
+ * and after the step is the same at every node, because E changes only
+ * through the current, which conserves that charge. */
+lpic_status lpic_div_e(lpic_grid_t grid, double *out, cudaStream_t stream);
+
 /* Write x^n = x^{n+1/2} - (dt/2) v^n as doubles, out[d * capacity + p] for
  * d < dim, in current-buffer order (removed particles give NaN). */
 lpic_status lpic_positions_at_step(lpic_grid_t grid, int species_id, double *out,

@@ -805,6 +805,19 @@ lpic_status lpic_deposit_charge(lpic_grid_t g, int sid, void* rho, cudaStream_t 
     return LPIC_OK;
 }
 
+lpic_status lpic_div_e(lpic_grid_t g, double* out, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (!out) return fail(LPIC_EINVAL, "out is NULL");
+    const FastDiv dfx = make_fastdiv((unsigned)g->geo.fx), dny = make_fastdiv((unsigned)g->d.ny);
+    const int nb = grid_blocks(g->nfield, g->nsm, 16);
+    if (g->d.precision == LPIC_FP32_FIXED)
+        k_div_e<float><<<nb, 256, 0, st>>>(g->geo, ptr3<const float>(g->d.E), out, dfx, dny);
+    else
+        k_div_e<double><<<nb, 256, 0, st>>>(g->geo, ptr3<const double>(g->d.E), out, dfx, dny);
+    LPIC_LAUNCHED("k_div_e");
+    return LPIC_OK;
+}
+
 lpic_status lpic_positions_at_step(lpic_grid_t g, int sid, double* out, cudaStream_t st) {
     if (lpic_status r = check_species(g, sid)) return r;
     if (!out) return fail(LPIC_EINVAL, "out is NULL");

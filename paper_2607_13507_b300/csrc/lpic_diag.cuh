@@ -132,4 +132,26 @@ __global__ void k_positions64(Geo g, P64 p, double* out, long long cap) {
     }
 }
 
+// Discrete divergence of E at the integer nodes (Gauss's law, Sec. 3.2):
+// sum_d (E_d(i+1/2) - E_d(i-1/2)) / h_d, periodic wrap; an absorbing x edge
+// takes E_x = 0 below node 0.  out[nz][ny][fx] is overwritten.
+template <typename R>
+__global__ void k_div_e(Geo g, Ptr3<const R> E, double* out, FastDiv dfx, FastDiv dny) {
+    const int total = g.fx * g.ny * (g.dim == 3 ? g.nz : 1);
+    const double rdx = 1.0 / g.dx, rdy = 1.0 / g.dy, rdz = g.dim == 3 ? 1.0 / g.dz : 0.0;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < total; n += gridDim.x * blockDim.x) {
+        const int r = fdiv(n, dfx), i = n - r * g.fx;
+        const int k = fdiv(r, dny), j = r - k * g.ny;
+        const int im = g.absorb ? i - 1 : (i == 0 ? g.nx - 1 : i - 1);
+        const int jm = j == 0 ? g.ny - 1 : j - 1;
+        const double exm = im < 0 ? 0.0 : (double)E.p[0][n - i + im];
+        double v = ((double)E.p[0][n] - exm) * rdx + ((double)E.p[1][n] - (double)E.p[1][n + (jm - j) * g.fx]) * rdy;
+        if (g.dim == 3) {
+            const int km = k == 0 ? g.nz - 1 : k - 1;
+            v += ((double)E.p[2][n] - (double)E.p[2][n + (km - k) * g.ny * g.fx]) * rdz;
+        }
+        out[n] = v;
+    }
+}
+
 }  // namespace lpic

@@ -25,7 +25,7 @@ STATUS = {0: "LPIC_OK", 1: "LPIC_EINVAL", 2: "LPIC_ENOMEM", 3: "LPIC_ECUDA", 4: 
 EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_add_species",
            "lpic_species_query", "lpic_sort_particles", "lpic_zero_current",
            "lpic_gather_push_deposit", "lpic_maxwell_half_step", "lpic_step",
-           "lpic_deposit_charge", "lpic_positions_at_step", "lpic_diagnostics",
+           "lpic_deposit_charge", "lpic_div_e", "lpic_positions_at_step", "lpic_diagnostics",
            "lpic_grid_get_info", "lpic_check_status", "lpic_last_error", "lpic_set_clock",
            "lpic_graph_steps", "lpic_sort_tiles_static", "lpic_kernel_timing",
            "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
@@ -107,6 +107,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_sort_tiles_static.argtypes = [i, i, i, i, ctypes.POINTER(i), vp, vp, ctypes.c_longlong,
                                            vp, vp, vp, st]
     lib.lpic_deposit_charge.argtypes = [vp, i, vp, st]
+    lib.lpic_div_e.argtypes = [vp, vp, st]
     lib.lpic_positions_at_step.argtypes = [vp, i, vp, st]
     lib.lpic_diagnostics.argtypes = [vp, ctypes.POINTER(Diag), st]
     lib.lpic_grid_get_info.argtypes = [vp, ctypes.POINTER(GridInfo)]
@@ -114,8 +115,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_last_error.restype = ctypes.c_char_p
     lib.lpic_last_error.argtypes = []
     for name in EXPORTS:
+        fn = getattr(lib, name)
+        # without argtypes ctypes would pass device pointers as 32-bit ints
+        if fn.argtypes is None:
+            raise RuntimeError(f"{name}: no argument types declared in the binding")
         if name != "lpic_species_bytes" and name != "lpic_last_error":
-            getattr(lib, name).restype = ctypes.c_int
+            fn.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -340,6 +345,21 @@ class Grid:
         if rc not in (0, 4):
             _check(rc)
         return bits.value
+
+    def div_e(self, stream=None) -> torch.Tensor:
+        """Discrete divergence of E at the integer nodes (float64)."""
+        out = torch.empty(self.field_shape, dtype=torch.float64, device=self.device)
+        _check(load().lpic_div_e(self.h_, out.data_ptr(), _stream(stream)))
+        return out
+
+    def rho(self, stream=None) -> torch.Tensor:
+        """Charge density of all species' stored positions (float64, field units)."""
+        inf = self.info() if self.precision != FP64 else None
+        tot = torch.zeros(self.field_shape, dtype=torch.float64, device=self.device)
+        for sp in self.species:
+            r = sp.charge(stream)
+            tot += r if inf is None else r.to(torch.float64) * inf.rho_scale
+        return tot
 
     def current(self) -> list:
         """J as float64 in field units (FP32 path: J_int * j_scale)."""

@@ -227,6 +227,36 @@ def test_int32_round_box_holds_identical_relativistic_particles(dim, order, dire
     assert G.check_status() == 0
 
 
+@pytest.mark.parametrize("precision,dim", [("fp64", 2), ("fp64", 3), ("fp32", 2), ("fp32", 3)])
+def test_gauss_law_residual_is_constant(precision, dim):
+    """div E - (rho before + rho after the step) / 2 of the stored positions
+    is the same after every step (E changes only through the current, which
+    conserves that charge); div E itself matches the oracle's operator on the
+    same E.  FP32: E is single precision, bound 1e-5 of max |rho|."""
+    from paper_2607_13507_b300 import lpic
+    if dim == 2:
+        wl = W.thermal2d(n=32, ppc=4, vth=0.2, order=2, precision=precision)
+    else:
+        wl = W.thermal3d(n=12, ppc=2, vth=0.2, order=2, precision=precision)
+    G = gpu_case(wl, W.load_all(wl), lpic.FP64 if precision == "fp64" else lpic.FP32_FIXED)
+    rho_prev = G.rho()
+    res = []
+    for s in range(6):
+        G.step(s * wl.dt)
+        rho = G.rho()
+        res.append(G.div_e() - 0.5 * (rho + rho_prev))
+        rho_prev = rho
+    scale = float(rho.abs().max())
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    for r in res[1:]:
+        assert float((r - res[0]).abs().max()) < tol * scale
+    g = O.Grid(dim, wl.n, wl.h, wl.dt, wl.order)
+    for c in range(3):
+        g.E[c][...] = G.E[c].cpu().numpy().astype(np.float64)
+    assert rel_l2(G.div_e().cpu().numpy(), O.div_e(g)) < 1e-13
+    assert G.check_status() == 0
+
+
 def test_fp32_deposit_is_deterministic_under_permutation():
     from paper_2607_13507_b300 import lpic
     wl = W.thermal2d(n=32, ppc=8, vth=0.1, order=2, precision="fp32")
