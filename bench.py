@@ -133,6 +133,19 @@ def measured_peaks():
         return {"hbm_gbs": 6400.0}, "fallback"
 
 
+def reduce_over_ranks(elapsed, psteps, device):
+    """Replicas (one independent problem per rank, no data-path collective):
+    the job's timed region is the longest rank's, its work the sum of the
+    ranks' particle-steps."""
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    sm = torch.tensor([psteps], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_13507_b300", "csrc")
@@ -260,11 +273,7 @@ def run_b300(args, rank, world, local_rank):
     launch_time = gpd_time / max(1, gpd_launches)
 
     if world > 1:
-        t = torch.tensor([elapsed, psteps], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        elapsed, psteps = float(mx[0]), float(t[1])
+        elapsed, psteps = reduce_over_ranks(elapsed, psteps, dev)
 
     result = None
     if rank == 0:
@@ -357,11 +366,7 @@ def run_ensemble(args, rank, world, local_rank):
     n_now = sum(G.species[0].query(stream)[1] for G in grids)
     psteps = 0.5 * (counts + n_now) * args.steps
     if world > 1:
-        t = torch.tensor([elapsed, psteps], dtype=torch.float64, device=dev)
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        elapsed, psteps = float(mx[0]), float(t[1])
+        elapsed, psteps = reduce_over_ranks(elapsed, psteps, dev)
     if rank != 0:
         return None
     peaks, which = measured_peaks()
