@@ -120,30 +120,55 @@ static __global__ void k_sort_items(const int* count, const int* coff, int ntile
     if (blockIdx.x == 0 && threadIdx.x == 0) *nitems = coff[ntiles];
 }
 
+// A particle's record: load() reads it (before the destination is known, so
+// the loads overlap the cursor atomic), store() writes it.
 struct MoveFP32 {
     P32 src, dst;
     int dim;
-    __device__ inline void operator()(int i, int j) const {
-        dst.cell[j] = src.cell[i];
-        dst.off[0][j] = src.off[0][i];
-        dst.off[1][j] = src.off[1][i];
-        if (dim == 3) dst.off[2][j] = src.off[2][i];
-        dst.u[0][j] = src.u[0][i]; dst.u[1][j] = src.u[1][i]; dst.u[2][j] = src.u[2][i];
-        dst.w[j] = src.w[i];
-        dst.id[j] = src.id[i];
+    struct Rec { int cell, id; float off[3], u[3], w; };
+    __device__ inline Rec load(int i) const {
+        Rec r;
+        r.cell = src.cell[i];
+        r.off[0] = src.off[0][i];
+        r.off[1] = src.off[1][i];
+        r.off[2] = (dim == 3) ? src.off[2][i] : 0.0f;
+        r.u[0] = src.u[0][i]; r.u[1] = src.u[1][i]; r.u[2] = src.u[2][i];
+        r.w = src.w[i];
+        r.id = src.id[i];
+        return r;
+    }
+    __device__ inline void store(const Rec& r, int j) const {
+        dst.cell[j] = r.cell;
+        dst.off[0][j] = r.off[0];
+        dst.off[1][j] = r.off[1];
+        if (dim == 3) dst.off[2][j] = r.off[2];
+        dst.u[0][j] = r.u[0]; dst.u[1][j] = r.u[1]; dst.u[2][j] = r.u[2];
+        dst.w[j] = r.w;
+        dst.id[j] = r.id;
     }
 };
 
 struct MoveFP64 {
     P64 src, dst;
     int dim;
-    __device__ inline void operator()(int i, int j) const {
-        dst.x[0][j] = src.x[0][i];
-        dst.x[1][j] = src.x[1][i];
-        if (dim == 3) dst.x[2][j] = src.x[2][i];
-        dst.u[0][j] = src.u[0][i]; dst.u[1][j] = src.u[1][i]; dst.u[2][j] = src.u[2][i];
-        dst.w[j] = src.w[i];
-        dst.id[j] = src.id[i];
+    struct Rec { double x[3], u[3], w; int id; };
+    __device__ inline Rec load(int i) const {
+        Rec r;
+        r.x[0] = src.x[0][i];
+        r.x[1] = src.x[1][i];
+        r.x[2] = (dim == 3) ? src.x[2][i] : 0.0;
+        r.u[0] = src.u[0][i]; r.u[1] = src.u[1][i]; r.u[2] = src.u[2][i];
+        r.w = src.w[i];
+        r.id = src.id[i];
+        return r;
+    }
+    __device__ inline void store(const Rec& r, int j) const {
+        dst.x[0][j] = r.x[0];
+        dst.x[1][j] = r.x[1];
+        if (dim == 3) dst.x[2][j] = r.x[2];
+        dst.u[0][j] = r.u[0]; dst.u[1][j] = r.u[1]; dst.u[2][j] = r.u[2];
+        dst.w[j] = r.w;
+        dst.id[j] = r.id;
     }
 };
 
@@ -154,6 +179,8 @@ __device__ inline void sort_scatter_body(const Key& key, const Move& mv, int n, 
     for (int r = 0; r < nround; ++r, i += stride) {
         const bool valid = i < n;
         const int k = valid ? key(i) : -1;
+        typename Move::Rec rec{};
+        if (valid && k < ntiles) rec = mv.load(i);
         const unsigned peers = __match_any_sync(0xffffffffu, k);
         const int leader = __ffs(peers) - 1;
         int base = 0;
@@ -161,7 +188,7 @@ __device__ inline void sort_scatter_body(const Key& key, const Move& mv, int n, 
         base = __shfl_sync(0xffffffffu, base, leader);
         if (valid && k < ntiles) {
             const int rank = __popc(peers & ((1u << lane_id()) - 1u));
-            mv(i, start[k] + base + rank);
+            mv.store(rec, start[k] + base + rank);
         }
     }
 }
