@@ -694,7 +694,8 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     for (int rnd = 0; rnd < nround; ++rnd) {
         const int i = beg + rnd * kGpdThreads + threadIdx.x;
         int cell = -1;
-        float pf[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};   // 2D: off0, off1, u0, u1, u2, w
+        // off0, off1, u0, u1, u2, then 2D: w / 3D: off2 (3D weight in pf3w)
+        float pf[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, pf3w = 0.0f;
         if constexpr (DIM == 2) {
             cp_async_wait_all();
             const int* b = sPf + (rnd & 1) * kPrefWords * kGpdThreads + threadIdx.x;
@@ -705,7 +706,13 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
             }
             prefetch(rnd + 1);
         } else {
-            cell = (i < end) ? p.cell[i] : -1;
+            // 3D: all of the particle's loads in flight together
+            if (i < end) {
+                cell = p.cell[i];
+                pf[0] = p.off[0][i]; pf[1] = p.off[1][i]; pf[5] = p.off[2][i];
+                pf[2] = p.u[0][i]; pf[3] = p.u[1][i]; pf[4] = p.u[2][i];
+                pf3w = p.w[i];
+            }
         }
         int cell_out = cell;      // the particle's cell after this round (-1: removed)
         // 3D: the move this particle deposits (if dep), staged below
@@ -739,8 +746,8 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                     f[0] = pf[0]; f[1] = pf[1]; f[2] = 0.0f;
                     ux = pf[2]; uy = pf[3]; uz = pf[4]; w = pf[5];
                 } else {
-                    f[0] = p.off[0][i]; f[1] = p.off[1][i]; f[2] = p.off[2][i];
-                    ux = p.u[0][i]; uy = p.u[1][i]; uz = p.u[2][i]; w = p.w[i];
+                    f[0] = pf[0]; f[1] = pf[1]; f[2] = pf[5];
+                    ux = pf[2]; uy = pf[3]; uz = pf[4]; w = pf3w;
                 }
 
                 // gather at x^{n+1/2} from the shared-memory halo
