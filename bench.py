@@ -39,6 +39,9 @@ WORKLOADS = {
     "thermal3d": ("3D3V periodic thermal plasma 256^3, 8 electrons/cell (134M), v_th=0.05c, TSC, "
                   "FP32 cell+offset positions, int64 fixed-point deposit", 0),
     "thermal2d": ("2D3V periodic thermal plasma 64x64, 16 electrons/cell, v_th=0.01c, CIC", 0),
+    "heating2d": ("2D3V numerical-heating set-up 640x640, dx=lambda/40, e-+ion plasma at 10 n_c, "
+                  "kT=1 keV Maxwell-Juttner, 64+64 particles/cell (52M), CIC, periodic, FP32 push + "
+                  "int64 fixed-point deposit", 0),
     "laser3d": ("3D3V laser-target 512x256x256, dx=lambda/32, a0=20 w0=2lambda 8-cycle laser through "
                 "an absorbing x-min edge, e-+p slab 30 n_c at x in [4,6] lambda, 16+16 particles/cell "
                 "(134M), CIC, re-sorted every 10 steps, FP32 push + int64 fixed-point deposit", 400),
@@ -56,6 +59,8 @@ def make_workload(name, precision, seed_offset=0, ny=None, n3=None):
         wl = W.thermal3d(precision=precision, n=n3 or 256)
     elif name == "thermal2d":
         wl = W.thermal2d(precision=precision)
+    elif name == "heating2d":
+        wl = W.heating2d(res=40, ppc=64, precision=precision)
     elif name == "laser3d":
         wl = W.laser3d(precision=precision, nx=n3 or 512, ny=(n3 or 512) // 2, nz=(n3 or 512) // 2)
     else:

@@ -63,6 +63,9 @@ class SpeciesSpec:
     m: float
     ppc: int
     vth: float                      # per-component momentum spread (u ~ N(0, vth^2))
+    # or, with theta > 0, momenta from the Maxwell-Juttner distribution at
+    # temperature kT = theta m c^2 (vth unused)
+    theta: float = 0.0
     density: float = 1.0            # peak density
     profile: str = "uniform"        # "uniform" | "slab"
     slab: tuple = ()                # (ramp_start, ramp_end, plateau_end) in x, physical units
@@ -121,10 +124,42 @@ def _density(spec: SpeciesSpec, xc: np.ndarray) -> np.ndarray:
     return n
 
 
+def maxwell_juttner(g: np.random.Generator, theta: float, n: int) -> np.ndarray:
+    """Momenta u = gamma v / c (shape (3, n), float64) of n particles drawn
+    from the Maxwell-Juttner distribution at temperature kT = theta m c^2:
+    isotropic, |u| with density proportional to u^2 exp(-(gamma - 1) / theta).
+
+    Exact rejection sampling on the kinetic energy e = gamma - 1, whose density
+    is proportional to sqrt(e (e + 2)) (1 + e) exp(-e / theta).  Because
+    sqrt(e + 2) <= sqrt(2) sqrt(1 + e) and (1 + e)^(3/2) <= (1 + e)^2
+    <= 2 (1 + e^2), that density lies under 2 sqrt(2) (e^(1/2) + e^(5/2))
+    exp(-e / theta), a mixture of two gamma distributions (shapes 3/2 and 7/2,
+    scale theta) that numpy samples directly; a candidate is kept with
+    probability sqrt(e + 2) (1 + e) / (2 sqrt(2) (1 + e^2)) (at least about
+    one half at small theta).  Directions are uniform on the sphere."""
+    wa = math.gamma(1.5) * theta ** 1.5
+    wb = math.gamma(3.5) * theta ** 3.5
+    pa = wa / (wa + wb)
+    out = np.empty(0)
+    while out.shape[0] < n:
+        m = 2 * (n - out.shape[0]) + 64
+        shape = np.where(g.random(m) < pa, 1.5, 3.5)
+        e = theta * g.standard_gamma(shape)
+        keep = g.random(m) * (2.0 * math.sqrt(2.0) * (1.0 + e * e)) <= np.sqrt(e + 2.0) * (1.0 + e)
+        out = np.concatenate([out, e[keep]])
+    e = out[:n]
+    umag = np.sqrt(e * (e + 2.0))
+    cth = 2.0 * g.random(n) - 1.0
+    phi = 2.0 * math.pi * g.random(n)
+    sth = np.sqrt(np.maximum(0.0, 1.0 - cth * cth))
+    return np.stack([umag * sth * np.cos(phi), umag * sth * np.sin(phi), umag * cth])
+
+
 def load_species(wl: Workload, sid: int, previous: list | None = None,
                  cells: tuple | None = None) -> Particles:
     """Exactly ``ppc`` particles per loaded cell, uniform in the cell, with
-    momenta u_i ~ N(0, vth^2) and weight w = n(x_cell) dV / ppc.  Cells of zero
+    momenta u_i ~ N(0, vth^2) (or Maxwell-Juttner at theta) and weight
+    w = n(x_cell) dV / ppc.  Cells of zero
     density get no particles.  ``cells`` restricts loading to a box of cells
     ((lo, hi) per dimension) for sampled runs."""
     spec = wl.species[sid]
@@ -155,8 +190,11 @@ def load_species(wl: Workload, sid: int, previous: list | None = None,
         for d in range(dim):
             cell[d] = np.repeat(cc[d].astype(np.int32), ppc)
         off = _f32_unit(g.random((dim, n), dtype=np.float32))
-    u = g.standard_normal((3, n), dtype=np.float32)
-    u *= np.float32(spec.vth)
+    if spec.theta > 0.0:
+        u = maxwell_juttner(g, spec.theta, n).astype(np.float32)
+    else:
+        u = g.standard_normal((3, n), dtype=np.float32)
+        u *= np.float32(spec.vth)
     w = (np.repeat(dens, ppc) * wl.dV / ppc).astype(np.float32)
     ids = np.arange(n, dtype=np.int32)
     return Particles(spec.q, spec.m, cell, off, u, w, ids)
@@ -226,6 +264,30 @@ def laser3d(nx=512, ny=256, nz=256, ppc=16, order=1, steps=500, precision="fp32"
     return Workload(f"laser3d_{nx}x{ny}x{nz}", 3, (nx, ny, nz), h, cfl_dt(h), order, True, sp, steps,
                     laser=LaserSpec(a0=20.0, w0=2.0 * LAMBDA, tau=8.0 * LAMBDA),
                     precision=precision, seed=SEED_BASE + 1000 * 5 if seed is None else seed)
+
+
+M_E_KEV = 510.999  # electron rest energy, keV
+
+
+def heating2d(res=20, ppc=16, L_lambda=16, precision="fp32", seed=None) -> Workload:
+    """The numerical-heating set-up (Sec. 4.1): a uniform 2D electron-ion
+    plasma at n_e = 10 n_c and kT = 1 keV for both species (Maxwell-Juttner
+    momenta), periodic in both directions, cell-in-cell shapes, dt = 0.95 CFL,
+    evolved for 5000 / omega_pe, dx = lambda / res (20 and 40 in the paper),
+    ppc particles per cell and species (16 and 64).  The box side (L_lambda
+    wavelengths) and the ion mass (protons) are not given in the paper; the
+    ions start at the electrons' positions (a neutral start)."""
+    dx = LAMBDA / res
+    n = int(round(L_lambda * res))
+    h = (dx, dx)
+    dt = cfl_dt(h)
+    omega_pe = math.sqrt(10.0)
+    steps = int(math.ceil(5000.0 / omega_pe / dt))
+    sp = [SpeciesSpec(**ELECTRON, ppc=ppc, vth=0.0, density=10.0, theta=1.0 / M_E_KEV),
+          SpeciesSpec(**PROTON, ppc=ppc, vth=0.0, density=10.0, theta=1.0 / (M_E_KEV * PROTON["m"]),
+                      same_positions_as=0)]
+    return Workload(f"heating2d_dx{res}_ppc{ppc}_{n}x{n}", 2, (n, n), h, dt, 1, False, sp, steps,
+                    precision=precision, seed=SEED_BASE + 1000 * 6 + res + ppc if seed is None else seed)
 
 
 @dataclass

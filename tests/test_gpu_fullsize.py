@@ -61,6 +61,37 @@ def test_energy_history_200_steps(precision):
     assert G.check_status() == 0
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_heating_setup_energy_history(precision):
+    """The numerical-heating set-up (n_e = 10 n_c, 1 keV Maxwell-Juttner
+    electrons and ions, CIC, periodic) on a 32 x 32 box at dx = lambda/20,
+    16 particles per cell and species: 300 steps, total energy within 1 % of
+    the initial energy of the oracle's at every 10th step, and the drift
+    itself reproduced to 1 %."""
+    from paper_2607_13507_b300 import lpic
+    wl = W.heating2d(res=20, ppc=16, L_lambda=1.6)
+    parts = W.load_all(wl)
+    g, sps = oracle_case(wl, parts)
+    G = gpu_case(wl, parts, lpic.FP64 if precision == "fp64" else lpic.FP32_FIXED)
+    hist_g, hist_o = [], []
+    for s in range(301):
+        if s % 10 == 0:
+            torch.cuda.synchronize()
+            d = G.diagnostics()
+            ek, ef, _ = O.energy(g, sps)
+            hist_g.append(d.kinetic + d.field)
+            hist_o.append(ek + ef)
+        if s < 300:
+            O.step(g, sps, s * wl.dt)
+            G.step(s * wl.dt)
+    hist_g, hist_o = np.array(hist_g), np.array(hist_o)
+    e0 = hist_o[0]
+    assert np.max(np.abs(hist_g - hist_o)) < 0.01 * e0
+    dg, do = hist_g - hist_g[0], hist_o - hist_o[0]
+    assert np.max(np.abs(dg - do)) < 0.01 * max(np.max(np.abs(do)), 1e-3 * e0)
+    assert G.check_status() == 0
+
+
 def test_laser2d_full_size_sampled_push_and_exact_continuity():
     from paper_2607_13507_b300 import lpic
     wl = W.laser2d()
