@@ -41,7 +41,9 @@
  * sequential-sub-move and path-integral re-derivations of the Esirkepov
  * weights, Villasenor-Buneman limit, the discrete Yee dispersion relation,
  * Gauss-law constancy, cold Langmuir frequency, Mur reflection, translation
- * invariance).
+ * invariance); the CPML layers by a conducting-cavity mode at the discrete
+ * frequency (lossless layers), wave-packet absorption, decay of oblique
+ * waves and the laser sheet's amplitude and one-sidedness.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -57,6 +59,15 @@ typedef struct {
     int laser;               /* 1: incoming laser at x-min (needs absorb_x) */
     double a0, w0, tau, omega, yc, zc;
     double *E[3], *B[3], *J[3];
+    /* CPML absorbing layers instead of the Mur edge condition (cpml = 1):
+     * pml_cells cells at each x end, grading exponent pml_m, sigma_max,
+     * kappa_max, alpha_max; psi[0..3] = memory variables of the x derivatives
+     * in the E_y, E_z, B_y, B_z updates ([nz][ny][fx], zero outside the
+     * layers); the laser then enters as a current sheet on node plane
+     * laser_plane. */
+    int cpml, pml_cells, laser_plane;
+    double pml_m, pml_sigma_max, pml_kappa_max, pml_alpha_max;
+    double *psi[4];
 } orc_grid;
 
 typedef struct {
@@ -396,11 +407,138 @@ double orc_laser_ey(const orc_grid *g, double x, double y, double z, double t)
     return g->a0 * env * exp(-r2 / (g->w0 * g->w0)) * sin(g->omega * s);
 }
 
+/* ------------------------------------------------ CPML (Sec. 3.2 boundaries)
+ * Convolutional PML on the x ends (Roden & Gedney's recursive convolution of
+ * the stretched-coordinate PML of Berenger): inside a layer of L cells the x
+ * derivative d/dx of a field update becomes (1/kappa) d/dx + psi, with the
+ * memory variable psi <- b psi + a d/dx updated before the field, and
+ * b = exp(-(sigma/kappa + alpha) tau), a = sigma (b - 1) / (sigma kappa +
+ * kappa^2 alpha) for the update's time step tau (each half step here).  The
+ * profiles over the depth d in [0, 1] into the layer (d = 0 at the inner
+ * face): sigma = sigma_max d^m, kappa = 1 + (kappa_max - 1) d^m,
+ * alpha = alpha_max (1 - d).  The outer faces x = 0 and x = nx dx are perfect
+ * conductors (tangential E = 0). */
+static double pml_depth(const orc_grid *g, double xc)   /* xc: position in cells */
+{
+    const double L = g->pml_cells;
+    if (xc < L) return (L - xc) / L;
+    if (xc > g->nx - L) return (xc - (g->nx - L)) / L;
+    return 0.0;
+}
+
+static void pml_coef(const orc_grid *g, double xc, double tau, double *kinv, double *a, double *b)
+{
+    const double d = pml_depth(g, xc);
+    const double dm = pow(d, g->pml_m);
+    const double sigma = g->pml_sigma_max * dm;
+    const double kappa = 1.0 + (g->pml_kappa_max - 1.0) * dm;
+    const double alpha = d > 0.0 ? g->pml_alpha_max * (1.0 - d) : 0.0;
+    *kinv = 1.0 / kappa;
+    *b = exp(-(sigma / kappa + alpha) * tau);
+    *a = sigma > 0.0 ? sigma * (*b - 1.0) / (sigma * kappa + kappa * kappa * alpha) : 0.0;
+}
+
+/* The CPML E half step: E_x as in the interior; E_y, E_z on nodes 1..nx-1
+ * with the modified x derivative; nodes 0 and nx stay zero.  The laser sheet:
+ * a surface current K_y = -2 E_inc(t) on node plane laser_plane radiates
+ * E_y = E_inc into +x (and the same into -x, which the layer absorbs); it
+ * enters the update as the volume current K_y / dx at the half step's centre
+ * time. */
+static void advance_E_cpml(orc_grid *g, double tau, double t_old)
+{
+    const long ny = g->ny, nz = (g->dim == 3) ? g->nz : 1, fx = g->fx, nx = g->nx;
+    const long plane = ny * nz;
+    const int d3 = g->dim == 3;
+    for (int c = 0; c < 3; ++c) {
+        double *newE = (double *)malloc(sizeof(double) * fx * plane);
+        memcpy(newE, g->E[c], sizeof(double) * fx * plane);
+        for (long k = 0; k < nz; ++k)
+            for (long j = 0; j < ny; ++j)
+                for (long i = 0; i < fx; ++i) {
+                    if (half_x_E(c) && i == nx) continue;
+                    if (!half_x_E(c) && (i == 0 || i == nx)) continue;
+                    const long n = node(g, i, j, k);
+                    double cb;
+                    if (c == 0) {
+                        if (!curlB(g, c, i, j, k, &cb)) continue;
+                    } else {
+                        double kinv, a, b;
+                        pml_coef(g, (double)i, tau, &kinv, &a, &b);
+                        if (c == 1) {   /* E_y: -dBz/dx + dBx/dz */
+                            const double dbz = (g->B[2][n] - g->B[2][node(g, i - 1, j, k)]) / g->dx;
+                            g->psi[0][n] = b * g->psi[0][n] + a * dbz;
+                            cb = -(kinv * dbz + g->psi[0][n]);
+                            if (d3) cb += (g->B[0][n] - g->B[0][node(g, i, j, k - 1)]) / g->dz;
+                        } else {        /* E_z: dBy/dx - dBx/dy */
+                            const double dby = (g->B[1][n] - g->B[1][node(g, i - 1, j, k)]) / g->dx;
+                            g->psi[1][n] = b * g->psi[1][n] + a * dby;
+                            cb = kinv * dby + g->psi[1][n]
+                               - (g->B[0][n] - g->B[0][node(g, i, j - 1, k)]) / g->dy;
+                        }
+                    }
+                    double jc = g->J[c][n];
+                    if (c == 1 && g->laser && i == g->laser_plane) {
+                        const double y = (j + 0.5) * g->dy, z = k * g->dz;
+                        jc += -2.0 * orc_laser_ey(g, 0.0, y, z, t_old + 0.5 * tau) / g->dx;
+                    }
+                    newE[n] = g->E[c][n] + tau * (cb - jc);
+                }
+        memcpy(g->E[c], newE, sizeof(double) * fx * plane);
+        free(newE);
+    }
+}
+
+/* The CPML B half step: B_x as in the interior; B_y, B_z at i + 1/2 for
+ * i = 0..nx-1 with the modified x derivative. */
+static void advance_B_cpml(orc_grid *g, double tau)
+{
+    const long ny = g->ny, nz = (g->dim == 3) ? g->nz : 1, fx = g->fx, nx = g->nx;
+    const long plane = ny * nz;
+    const int d3 = g->dim == 3;
+    for (int c = 0; c < 3; ++c) {
+        double *newB = (double *)malloc(sizeof(double) * fx * plane);
+        memcpy(newB, g->B[c], sizeof(double) * fx * plane);
+        for (long k = 0; k < nz; ++k)
+            for (long j = 0; j < ny; ++j)
+                for (long i = 0; i < fx; ++i) {
+                    if (half_x_B(c) && i == nx) continue;
+                    const long n = node(g, i, j, k);
+                    double ce;
+                    if (c == 0) {
+                        if (!curlE(g, c, i, j, k, &ce)) continue;
+                    } else {
+                        double kinv, a, b;
+                        pml_coef(g, i + 0.5, tau, &kinv, &a, &b);
+                        if (c == 1) {   /* B_y: dEx/dz - dEz/dx */
+                            const double dez = (g->E[2][node(g, i + 1, j, k)] - g->E[2][n]) / g->dx;
+                            g->psi[2][n] = b * g->psi[2][n] + a * dez;
+                            ce = -(kinv * dez + g->psi[2][n]);
+                            if (d3) ce += (g->E[0][node(g, i, j, k + 1)] - g->E[0][n]) / g->dz;
+                        } else {        /* B_z: dEy/dx - dEx/dy */
+                            const double dey = (g->E[1][node(g, i + 1, j, k)] - g->E[1][n]) / g->dx;
+                            g->psi[3][n] = b * g->psi[3][n] + a * dey;
+                            ce = kinv * dey + g->psi[3][n]
+                               - (g->E[0][node(g, i, j + 1, k)] - g->E[0][n]) / g->dy;
+                        }
+                    }
+                    newB[n] = g->B[c][n] - tau * ce;
+                }
+        memcpy(g->B[c], newB, sizeof(double) * fx * plane);
+        free(newB);
+    }
+}
+
 /* E += tau (curl B - J) at every E position; absorbing x edges of E_y and
  * E_z then follow the first-order Mur condition for an outgoing wave (with
- * the incoming laser added at x-min).  tau = dt/2, t_old -> t_old + tau. */
+ * the incoming laser added at x-min), or, with CPML, the x derivatives in the
+ * layers are replaced as above, the outer faces stay at zero and the laser is
+ * a current sheet.  tau = dt/2, t_old -> t_old + tau. */
 static void advance_E(orc_grid *g, double tau, double t_old)
 {
+    if (g->absorb_x && g->cpml) {
+        advance_E_cpml(g, tau, t_old);
+        return;
+    }
     const long ny = g->ny, nz = (g->dim == 3) ? g->nz : 1, fx = g->fx, nx = g->nx;
     const long plane = ny * nz;
     double *old = NULL;
@@ -464,9 +602,14 @@ static void advance_E(orc_grid *g, double tau, double t_old)
     }
 }
 
-/* B -= tau curl E at every B position. */
+/* B -= tau curl E at every B position (with CPML: the x derivatives of E_z and
+ * E_y in the B_y and B_z updates replaced inside the layers). */
 static void advance_B(orc_grid *g, double tau)
 {
+    if (g->absorb_x && g->cpml) {
+        advance_B_cpml(g, tau);
+        return;
+    }
     const long ny = g->ny, nz = (g->dim == 3) ? g->nz : 1, fx = g->fx, nx = g->nx;
     const long plane = ny * nz;
     for (int c = 0; c < 3; ++c) {

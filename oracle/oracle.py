@@ -46,7 +46,22 @@ class _CGrid(ctypes.Structure):
                 ("laser", ctypes.c_int), ("a0", ctypes.c_double), ("w0", ctypes.c_double),
                 ("tau", ctypes.c_double), ("omega", ctypes.c_double), ("yc", ctypes.c_double),
                 ("zc", ctypes.c_double),
-                ("E", _dp * 3), ("B", _dp * 3), ("J", _dp * 3)]
+                ("E", _dp * 3), ("B", _dp * 3), ("J", _dp * 3),
+                ("cpml", ctypes.c_int), ("pml_cells", ctypes.c_int), ("laser_plane", ctypes.c_int),
+                ("pml_m", ctypes.c_double), ("pml_sigma_max", ctypes.c_double),
+                ("pml_kappa_max", ctypes.c_double), ("pml_alpha_max", ctypes.c_double),
+                ("psi", _dp * 4)]
+
+
+class Pml:
+    """CPML layers on the x ends (absorbing x only): cells per layer, grading
+    exponent m, sigma_max (None: 0.8 (m + 1) / dx, the usual optimum for
+    c = eps0 = 1), kappa_max, alpha_max.  The laser (if any) is a current sheet
+    on node plane cells + 2."""
+
+    def __init__(self, cells=16, m=3.0, sigma_max=None, kappa_max=1.0, alpha_max=0.05):
+        self.cells, self.m, self.sigma_max = int(cells), float(m), sigma_max
+        self.kappa_max, self.alpha_max = float(kappa_max), float(alpha_max)
 
 
 class _CSpecies(ctypes.Structure):
@@ -100,7 +115,8 @@ class Laser:
 class Grid:
     """Yee grid: E, B, J as float64 arrays of shape (nz, ny, fx)."""
 
-    def __init__(self, dim, n, h, dt, order, absorb_x=False, laser: Laser | None = None):
+    def __init__(self, dim, n, h, dt, order, absorb_x=False, laser: Laser | None = None,
+                 pml: Pml | None = None):
         nx, ny = int(n[0]), int(n[1])
         nz = int(n[2]) if dim == 3 else 1
         self.dim, self.nx, self.ny, self.nz = dim, nx, ny, nz
@@ -113,6 +129,9 @@ class Grid:
         self.B = [np.zeros(shape) for _ in range(3)]
         self.J = [np.zeros(shape) for _ in range(3)]
         self.laser = laser
+        assert pml is None or absorb_x, "CPML layers need absorbing x"
+        self.pml = pml
+        self.psi = [np.zeros(shape) for _ in range(4)]
 
     @property
     def dV(self):
@@ -129,6 +148,14 @@ class Grid:
                 arr = getattr(self, name)[c]
                 assert arr.dtype == np.float64 and arr.flags.c_contiguous
                 getattr(g, name)[c] = _ptr(arr)
+        P = self.pml
+        if P is not None:
+            g.cpml, g.pml_cells, g.laser_plane = 1, P.cells, P.cells + 2
+            g.pml_m = P.m
+            g.pml_sigma_max = 0.8 * (P.m + 1.0) / self.dx if P.sigma_max is None else float(P.sigma_max)
+            g.pml_kappa_max, g.pml_alpha_max = P.kappa_max, P.alpha_max
+        for c in range(4):
+            g.psi[c] = _ptr(self.psi[c])
         return g
 
 
