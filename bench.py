@@ -51,10 +51,10 @@ WORKLOADS = {
 }
 
 
-def make_workload(name, precision, seed_offset=0, ny=None, n3=None):
+def make_workload(name, precision, seed_offset=0, ny=None, n3=None, boundary="mur"):
     from paper_2607_13507_b300 import workloads as W
     if name == "laser2d":
-        wl = W.laser2d(precision=precision, ny=ny or 1024)
+        wl = W.laser2d(precision=precision, ny=ny or 1024, boundary=boundary)
     elif name == "thermal3d":
         wl = W.thermal3d(precision=precision, n=n3 or 256)
     elif name == "thermal2d":
@@ -62,7 +62,8 @@ def make_workload(name, precision, seed_offset=0, ny=None, n3=None):
     elif name == "heating2d":
         wl = W.heating2d(res=40, ppc=64, precision=precision)
     elif name == "laser3d":
-        wl = W.laser3d(precision=precision, nx=n3 or 512, ny=(n3 or 512) // 2, nz=(n3 or 512) // 2)
+        wl = W.laser3d(precision=precision, nx=n3 or 512, ny=(n3 or 512) // 2, nz=(n3 or 512) // 2,
+                       boundary=boundary)
     else:
         raise SystemExit(f"unknown workload {name}")
     wl.seed += seed_offset
@@ -218,7 +219,8 @@ def run_b300(args, rank, world, local_rank):
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
 
-    wl = make_workload(args.workload, args.precision, seed_offset=rank, ny=args.ny, n3=args.n3)
+    wl = make_workload(args.workload, args.precision, seed_offset=rank, ny=args.ny, n3=args.n3,
+                       boundary=args.boundary)
     prec = lpic.FP32_FIXED if args.precision == "fp32" else lpic.FP64
     tuned = tuned_choice(args, wl)
     parts = W.load_all(wl)
@@ -300,7 +302,9 @@ def run_b300(args, rank, world, local_rank):
             "dtype": "f32 (int64 fixed-point current)" if args.precision == "fp32" else "f64",
             "data": "synthetic (seeded Philox initial conditions)",
             "config": {
-                "workload": WORKLOADS[args.workload][0],
+                "workload": WORKLOADS[args.workload][0] + (
+                    "; CPML x layers of 16 cells, laser entering as a current sheet"
+                    if args.boundary == "cpml" else ""),
                 "grid": list(wl.n), "species": len(wl.species),
                 "particles": int(sum(counts0)), "pre_steps": pre,
                 "l2": "inputs larger than L2 (particle state %.1f GB)" % (
@@ -448,7 +452,7 @@ def oracle_sample(args, budget_s, max_steps):
     import numpy as np
     from oracle import oracle as O
     from paper_2607_13507_b300 import workloads as W
-    wl = make_workload(args.workload, "fp64")
+    wl = make_workload(args.workload, "fp64", boundary=args.boundary)
     if wl.dim == 2:
         sample = dict(n=(wl.n[0], min(16, wl.n[1])))
     elif wl.laser is not None:
@@ -462,7 +466,8 @@ def oracle_sample(args, budget_s, max_steps):
         c = wl.laser_center()
         laser = O.Laser(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega, c[0],
                         c[1] if wl.dim == 3 else 0.0)
-    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x, laser=laser)
+    pml = O.Pml() if wl.boundary == "cpml" else None
+    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x, laser=laser, pml=pml)
     h = np.array(wl.h)[:, None]
     sps = [O.Species(p.q, p.m, (p.cell + p.off) * h, p.u, p.w) for p in parts]
     npart = sum(p.n for p in parts)
@@ -518,6 +523,8 @@ def main():
                     help="cells per side of the 3D thermal workload (smaller cases for profiling)")
     ap.add_argument("--ny", type=int, default=None,
                     help="transverse cells of the 2D laser workload (smaller cases for profiling)")
+    ap.add_argument("--boundary", choices=["mur", "cpml"], default="mur",
+                    help="absorbing x of the laser workloads: Mur edges or CPML layers")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

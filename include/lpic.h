@@ -98,7 +98,10 @@ typedef struct {
     int nx, ny, nz;             /* cells per dimension; nz ignored in 2D */
     double dx, dy, dz, dt;      /* cell sizes and time step; dz ignored in 2D.
                                    dt must satisfy the Courant limit of Sec. 3.2 */
-    int absorb_x;               /* 0: periodic x; 1: absorbing x edges */
+    int absorb_x;               /* 0: periodic x; 1: absorbing x edges (first-order Mur,
+                                   laser entering through the x-min edge); 2: CPML layers
+                                   (pml_* below, laser entering as a current sheet on
+                                   node plane pml_cells + 2) */
     int shape_order;            /* 1: cloud-in-cell, 2: quadratic spline (TSC) */
     int precision;              /* LPIC_FP64 or LPIC_FP32_FIXED */
     int tile[3];                /* cells per tile for the FP32 path; 0 = default */
@@ -112,6 +115,17 @@ typedef struct {
                                    particles beyond it take a global-memory path */
     void *E[3], *B[3], *J[3];   /* caller-owned device field arrays (see layout) */
     const lpic_laser_desc *laser; /* NULL: no laser; copied at create (needs absorb_x) */
+    /* CPML (absorb_x = 2; Sec. 3.2 names CPML absorbing boundaries): layers of
+     * pml_cells cells at both x ends in which the x derivatives of the field
+     * updates become (1/kappa) d/dx + psi with the recursive convolution
+     * psi <- b psi + a d/dx, b = exp(-(sigma/kappa + alpha) dt/2),
+     * a = sigma (b - 1) / (sigma kappa + kappa^2 alpha), per half step; over the
+     * depth d in [0, 1] into a layer sigma = pml_sigma_max d^pml_m,
+     * kappa = 1 + (pml_kappa_max - 1) d^pml_m, alpha = pml_alpha_max (1 - d).
+     * The outer faces are perfect conductors.  Requires 1 <= pml_cells and
+     * 2 pml_cells + 8 <= nx; ignored unless absorb_x = 2. */
+    int pml_cells;
+    double pml_m, pml_sigma_max, pml_kappa_max, pml_alpha_max;
 } lpic_grid_desc;
 
 typedef struct {

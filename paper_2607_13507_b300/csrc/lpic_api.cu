@@ -92,6 +92,9 @@ struct lpic_grid {
     unsigned* d_status = nullptr;
     void* d_mur = nullptr;
     double* d_lprof = nullptr;   // transverse laser profile on the x-min plane
+    int cpml = 0;                // CPML layers (absorb_x = 2)
+    void* d_psi = nullptr;       // CPML memory: 4 x plane x (2 L + 2) field-precision values
+    void* d_pcoef = nullptr;     // CPML coefficients: 1/kappa, a, b at nodes and half nodes (6 x fx)
     double* d_acc = nullptr;
     unsigned long long* d_cnt = nullptr;
     bool started = false;
@@ -254,23 +257,56 @@ lpic_status maxwell_impl(lpic_grid* g, int half, double t, cudaStream_t st, cons
     const int plane = g->d.ny * (DIM == 3 ? g->d.nz : 1);
     Ptr3<R> Ep;
     for (int c = 0; c < 3; ++c) Ep.p[c] = a.E[c];
+    const bool mur = g->geo.absorb && !g->cpml;
+    CpmlArgs<R> cp{};
+    Ptr3<const R> Ec, Bc;
+    for (int c = 0; c < 3; ++c) { Ec.p[c] = a.E[c]; Bc.p[c] = a.B[c]; }
+    Ptr3<R> Bp;
+    for (int c = 0; c < 3; ++c) Bp.p[c] = a.B[c];
+    const int nbp = grid_blocks((long long)plane * (2 * g->d.pml_cells + 2), g->nsm);
+    if (g->cpml) {
+        const size_t W = (size_t)plane * (2 * g->d.pml_cells + 2);
+        R* psi = static_cast<R*>(g->d_psi);
+        const R* cf = static_cast<const R*>(g->d_pcoef);
+        const size_t fx = (size_t)g->geo.fx;
+        for (int k = 0; k < 4; ++k) cp.psi[k] = psi + k * W;
+        for (int h = 0; h < 2; ++h) {
+            cp.kinv[h] = cf + (0 + h) * fx;
+            cp.a[h] = cf + (2 + h) * fx;
+            cp.b[h] = cf + (4 + h) * fx;
+        }
+        cp.L = g->d.pml_cells;
+    }
     auto updE = [&]() -> lpic_status {
-        if (g->geo.absorb) {
+        if (mur) {
             k_mur_save<R><<<grid_blocks(8LL * plane, g->nsm), 256, 0, st>>>(g->geo, Ep, static_cast<R*>(g->d_mur));
             LPIC_LAUNCHED("k_mur_save");
         }
         k_update_E<DIM, R, JT><<<nb, 256, 0, st>>>(g->geo, a);
         LPIC_LAUNCHED("k_update_E");
-        if (g->geo.absorb) {
+        if (mur) {
             k_mur_apply<R><<<grid_blocks(2LL * plane, g->nsm), 256, 0, st>>>(
                 g->geo, Ep, static_cast<const R*>(g->d_mur), g->laser, g->d_lprof, t, clock, tau);
             LPIC_LAUNCHED("k_mur_apply");
+        }
+        if (g->cpml) {
+            k_cpml_E<R><<<nbp, 256, 0, st>>>(g->geo, Ep, Bc, cp, (R)tau);
+            LPIC_LAUNCHED("k_cpml_E");
+            if (g->laser.on) {
+                k_laser_sheet<R><<<grid_blocks(plane, g->nsm), 256, 0, st>>>(
+                    g->geo, a.E[1], g->laser, g->d_lprof, g->d.pml_cells + 2, t, clock, tau);
+                LPIC_LAUNCHED("k_laser_sheet");
+            }
         }
         return LPIC_OK;
     };
     auto updB = [&]() -> lpic_status {
         k_update_B<DIM, R, JT><<<nb, 256, 0, st>>>(g->geo, a);
         LPIC_LAUNCHED("k_update_B");
+        if (g->cpml) {
+            k_cpml_B<R><<<nbp, 256, 0, st>>>(g->geo, Ec, Bp, cp, (R)tau);
+            LPIC_LAUNCHED("k_cpml_B");
+        }
         return LPIC_OK;
     };
     lpic_status r;
@@ -418,7 +454,13 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         return fail(LPIC_EINVAL, "dt = %g violates the Courant limit %g", d.dt, 1.0 / std::sqrt(s2));
     if (d.shape_order != 1 && d.shape_order != 2) return fail(LPIC_EINVAL, "shape_order must be 1 or 2");
     if (d.precision != LPIC_FP64 && d.precision != LPIC_FP32_FIXED) return fail(LPIC_EINVAL, "bad precision");
-    if (d.absorb_x != 0 && d.absorb_x != 1) return fail(LPIC_EINVAL, "absorb_x must be 0 or 1");
+    if (d.absorb_x < 0 || d.absorb_x > 2) return fail(LPIC_EINVAL, "absorb_x must be 0, 1 or 2");
+    if (d.absorb_x == 2) {
+        if (d.pml_cells < 1 || 2 * d.pml_cells + 8 > d.nx)
+            return fail(LPIC_EINVAL, "pml_cells must be >= 1 with 2 pml_cells + 8 <= nx");
+        if (!(d.pml_m >= 0) || !(d.pml_sigma_max >= 0) || !(d.pml_kappa_max >= 1) || !(d.pml_alpha_max >= 0))
+            return fail(LPIC_EINVAL, "CPML needs pml_m, pml_sigma_max, pml_alpha_max >= 0 and pml_kappa_max >= 1");
+    }
     if (d.absorb_x && d.nx < 8) return fail(LPIC_EINVAL, "absorbing x needs nx >= 8");
     if (d.laser && !d.absorb_x) return fail(LPIC_EINVAL, "a laser needs absorbing x edges");
     if (d.block_particles != 0 && (d.block_particles < 256 || d.block_particles > (1 << 20)))
@@ -439,7 +481,8 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     }
     g->d.laser = nullptr;
     const int fx = d.absorb_x ? d.nx + 1 : d.nx;
-    g->geo = Geo{d.dim, d.nx, d.ny, nz, fx, d.absorb_x, d.dx, d.dy, g->d.dz, d.dt};
+    g->cpml = d.absorb_x == 2;
+    g->geo = Geo{d.dim, d.nx, d.ny, nz, fx, d.absorb_x ? 1 : 0, d.dx, d.dy, g->d.dz, d.dt};
     g->nfield = (long long)fx * d.ny * nz;
     const int defT[2][3] = {{16, 16, 1}, {8, 8, 8}};
     const int n3[3] = {d.nx, d.ny, nz};
@@ -491,10 +534,45 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         cudaMalloc(&g->d_clock, 64) != cudaSuccess ||
         cudaMalloc(&g->d_acc, 64) != cudaSuccess ||
         cudaMalloc(&g->d_cnt, 64) != cudaSuccess ||
-        (d.absorb_x && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess) ||
+        (d.absorb_x == 1 && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess) ||
+        (g->cpml && cudaMalloc(&g->d_psi, fbytes * 4 * plane * (2 * d.pml_cells + 2)) != cudaSuccess) ||
+        (g->cpml && cudaMalloc(&g->d_pcoef, fbytes * 6 * fx) != cudaSuccess) ||
         (g->laser.on && cudaMalloc(&g->d_lprof, sizeof(double) * plane) != cudaSuccess)) {
         lpic_destroy_grid(g);
         return fail(LPIC_ENOMEM, "scratch allocation failed");
+    }
+    if (g->cpml) {
+        // coefficients per x index for the half step tau = dt/2: nodes (x = i dx)
+        // and half nodes (x = (i + 1/2) dx), depth measured into the layer
+        const double tau = 0.5 * d.dt, L = d.pml_cells;
+        std::vector<double> cf(6 * (size_t)fx);
+        for (int h = 0; h < 2; ++h)
+            for (int i = 0; i < fx; ++i) {
+                const double xc = i + 0.5 * h;
+                double dep = 0.0;
+                if (xc < L) dep = (L - xc) / L;
+                else if (xc > d.nx - L) dep = (xc - (d.nx - L)) / L;
+                const double dm = std::pow(dep, d.pml_m);
+                const double sigma = d.pml_sigma_max * dm;
+                const double kappa = 1.0 + (d.pml_kappa_max - 1.0) * dm;
+                const double alpha = dep > 0.0 ? d.pml_alpha_max * (1.0 - dep) : 0.0;
+                const double b = std::exp(-(sigma / kappa + alpha) * tau);
+                const double a = sigma > 0.0 ? sigma * (b - 1.0) / (sigma * kappa + kappa * kappa * alpha) : 0.0;
+                cf[(0 + h) * fx + i] = 1.0 / kappa;
+                cf[(2 + h) * fx + i] = a;
+                cf[(4 + h) * fx + i] = b;
+            }
+        cudaError_t e = cudaSuccess;
+        if (fbytes == 8) {
+            e = cudaMemcpy(g->d_pcoef, cf.data(), 8 * cf.size(), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> cff(cf.begin(), cf.end());
+            e = cudaMemcpy(g->d_pcoef, cff.data(), 4 * cff.size(), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess || cudaMemset(g->d_psi, 0, fbytes * 4 * plane * (2 * d.pml_cells + 2)) != cudaSuccess) {
+            lpic_destroy_grid(g);
+            return fail(LPIC_ECUDA, "CPML set-up failed");
+        }
     }
     if (g->laser.on) {
         k_laser_profile<<<grid_blocks(plane, g->nsm), 256>>>(g->geo, g->laser, g->d_lprof);
@@ -525,6 +603,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : g->ev) cudaEventDestroy(e);
     cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur); cudaFree(g->d_lprof);
+    cudaFree(g->d_psi); cudaFree(g->d_pcoef);
     cudaFree(g->d_clock);
     delete g;
     return LPIC_OK;

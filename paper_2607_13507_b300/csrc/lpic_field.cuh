@@ -173,6 +173,91 @@ __global__ void k_mur_apply(Geo g, Ptr3<R> E, const R* old, Laser L, const doubl
     }
 }
 
+// ----------------------------------------------------------------- CPML
+// Layers of L cells at both x ends (layer slots 0..L: nodes 0..L; slots
+// L+1..2L+1: nodes nx-L..nx).  After the interior update has applied the
+// plain x derivative, these kernels add the difference to the CPML form
+// (1/kappa) d/dx + psi, updating psi first (psi <- b psi + a d/dx).  Node
+// coefficients serve E_y, E_z (at x = i dx), half-node ones B_y, B_z (at
+// x = (i + 1/2) dx); E_y, E_z stay zero on the outer faces i = 0, nx.
+template <typename R>
+struct CpmlArgs {
+    R* psi[4];                    // E_y, E_z, B_y, B_z memory: [plane][2 L + 2]
+    const R* kinv[2];             // 1 / kappa: [0] nodes, [1] half nodes, fx entries
+    const R* a[2];
+    const R* b[2];
+    int L;
+};
+
+__device__ inline int cpml_node(const Geo& g, int L, int slot) {
+    return slot <= L ? slot : g.nx - L + (slot - (L + 1));
+}
+
+template <typename R>
+__global__ void k_cpml_E(Geo g, Ptr3<R> E, Ptr3<const R> B, CpmlArgs<R> c, R tau) {
+    const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
+    const int W = 2 * c.L + 2;
+    const R rdx = (R)(1.0 / g.dx);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < plane * W; t += gridDim.x * blockDim.x) {
+        const int q = t / W, slot = t - q * W;
+        const int i = cpml_node(g, c.L, slot);
+        if (i <= 0 || i >= g.nx) continue;
+        const long long n = (long long)q * g.fx + i;
+        const R ki = c.kinv[0][i], a = c.a[0][i], b = c.b[0][i];
+        const R dbz = (B.p[2][n] - B.p[2][n - 1]) * rdx;
+        const R p0 = b * c.psi[0][t] + a * dbz;
+        c.psi[0][t] = p0;
+        E.p[1][n] += tau * (((R)1 - ki) * dbz - p0);
+        const R dby = (B.p[1][n] - B.p[1][n - 1]) * rdx;
+        const R p1 = b * c.psi[1][t] + a * dby;
+        c.psi[1][t] = p1;
+        E.p[2][n] += tau * ((ki - (R)1) * dby + p1);
+    }
+}
+
+template <typename R>
+__global__ void k_cpml_B(Geo g, Ptr3<const R> E, Ptr3<R> B, CpmlArgs<R> c, R tau) {
+    const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
+    const int W = 2 * c.L + 2;
+    const R rdx = (R)(1.0 / g.dx);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < plane * W; t += gridDim.x * blockDim.x) {
+        const int q = t / W, slot = t - q * W;
+        const int i = cpml_node(g, c.L, slot);
+        if (i < 0 || i >= g.nx) continue;
+        const long long n = (long long)q * g.fx + i;
+        const R ki = c.kinv[1][i], a = c.a[1][i], b = c.b[1][i];
+        const R dez = (E.p[2][n + 1] - E.p[2][n]) * rdx;
+        const R p2 = b * c.psi[2][t] + a * dez;
+        c.psi[2][t] = p2;
+        B.p[1][n] -= tau * (((R)1 - ki) * dez - p2);
+        const R dey = (E.p[1][n + 1] - E.p[1][n]) * rdx;
+        const R p3 = b * c.psi[3][t] + a * dey;
+        c.psi[3][t] = p3;
+        B.p[2][n] -= tau * ((ki - (R)1) * dey + p3);
+    }
+}
+
+// The laser with CPML: a surface current K_y = -2 E_inc on node plane `is`
+// radiates E_inc into +x (and into -x, where the layer absorbs it); added to
+// E_y there as tau K_y / dx with the laser at the half step's centre time
+// t_old + tau / 2 (t_old = *clock + t_arg under graph replay).
+template <typename R>
+__global__ void k_laser_sheet(Geo g, R* Ey, Laser L, const double* prof, int is, double t_arg,
+                              const double* clock, double tau) {
+    __shared__ double s_tf[2];
+    const int plane = g.ny * (g.dim == 3 ? g.nz : 1);
+    if (threadIdx.x == 0) {
+        const double t_old = clock ? *clock + t_arg : t_arg;
+        laser_time(L, t_old + 0.5 * tau, s_tf[0], s_tf[1]);
+    }
+    __syncthreads();
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < plane; q += gridDim.x * blockDim.x) {
+        const double einc = s_tf[0] * prof[q] * s_tf[1];
+        const long long n = (long long)q * g.fx + is;
+        Ey[n] = (R)((double)Ey[n] + tau * (2.0 * einc / g.dx));
+    }
+}
+
 // Device clock of the captured step: advanced by dt at the end of each replay.
 __global__ void k_clock_add(double* clock, double dt) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *clock += dt;

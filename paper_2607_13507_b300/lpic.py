@@ -51,7 +51,19 @@ class GridDesc(ctypes.Structure):
                 ("tile", ctypes.c_int * 3), ("block_particles", ctypes.c_int),
                 ("sort_interval", ctypes.c_int),
                 ("E", ctypes.c_void_p * 3), ("B", ctypes.c_void_p * 3),
-                ("J", ctypes.c_void_p * 3), ("laser", ctypes.POINTER(LaserDesc))]
+                ("J", ctypes.c_void_p * 3), ("laser", ctypes.POINTER(LaserDesc)),
+                ("pml_cells", ctypes.c_int), ("pml_m", ctypes.c_double),
+                ("pml_sigma_max", ctypes.c_double), ("pml_kappa_max", ctypes.c_double),
+                ("pml_alpha_max", ctypes.c_double)]
+
+
+class PmlSpec:
+    """CPML layers for absorbing x: cells per layer, grading exponent m,
+    sigma_max (None: 0.8 (m + 1) / dx), kappa_max, alpha_max."""
+
+    def __init__(self, cells=16, m=3.0, sigma_max=None, kappa_max=1.0, alpha_max=0.05):
+        self.cells, self.m, self.sigma_max = int(cells), float(m), sigma_max
+        self.kappa_max, self.alpha_max = float(kappa_max), float(alpha_max)
 
 
 class SpeciesDesc(ctypes.Structure):
@@ -249,7 +261,7 @@ class Grid:
     """A grid with caller-owned (torch) field arrays and its species."""
 
     def __init__(self, dim, n, h, dt, order, precision, absorb_x=False, laser=None, tile=None,
-                 device="cuda", block_particles=0, sort_interval=0):
+                 device="cuda", block_particles=0, sort_interval=0, pml: PmlSpec | None = None):
         load()
         self.dim, self.precision, self.order = dim, precision, order
         self.n = tuple(int(v) for v in n) + ((1,) if dim == 2 else ())
@@ -268,12 +280,18 @@ class Grid:
         self._laser = None
         if laser is not None:
             self._laser = LaserDesc(laser.a0, laser.w0, laser.tau, laser.omega, laser.yc, laser.zc)
+        if pml is not None and not absorb_x:
+            raise ValueError("CPML layers need absorbing x")
+        mode = 0 if not absorb_x else (2 if pml is not None else 1)
+        P = pml or PmlSpec(cells=0)
+        smax = 0.8 * (P.m + 1.0) / self.h[0] if P.sigma_max is None else float(P.sigma_max)
         desc = GridDesc(dim, self.n[0], self.n[1], nz, self.h[0], self.h[1], self.h[2], self.dt,
-                        int(absorb_x), order, precision, (ctypes.c_int * 3)(*t), int(block_particles), int(sort_interval),
+                        mode, order, precision, (ctypes.c_int * 3)(*t), int(block_particles), int(sort_interval),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.E]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.B]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.J]),
-                        ctypes.pointer(self._laser) if self._laser is not None else None)
+                        ctypes.pointer(self._laser) if self._laser is not None else None,
+                        P.cells, P.m, smax, P.kappa_max, P.alpha_max)
         h = ctypes.c_void_p()
         _check(load().lpic_create_grid(ctypes.byref(desc), ctypes.byref(h)))
         self.h_ = h
@@ -419,5 +437,6 @@ def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, so
         c = wl.laser_center()
         laser = W.LaserSpec(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega)
         laser.yc, laser.zc = c[0], (c[1] if wl.dim == 3 else 0.0)
+    pml = PmlSpec() if getattr(wl, "boundary", "mur") == "cpml" else None
     return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device,
-                block_particles, sort_interval)
+                block_particles, sort_interval, pml)

@@ -95,6 +95,7 @@ class Workload:
     precision: str = "fp32"         # "fp64" | "fp32"
     seed: int = SEED_BASE
     notes: str = ""
+    boundary: str = "mur"           # absorbing x: "mur" edges or "cpml" layers
 
     @property
     def cells(self) -> int:
@@ -222,7 +223,8 @@ def thermal2d(n=64, ppc=16, vth=0.01, order=1, steps=200, precision="fp64", seed
                     precision=precision, seed=SEED_BASE + 1000 * 1 if seed is None else seed)
 
 
-def laser2d(nx=2048, ny=1024, ppc=32, order=2, steps=1600, precision="fp32", seed=None) -> Workload:
+def laser2d(nx=2048, ny=1024, ppc=32, order=2, steps=1600, precision="fp32", seed=None,
+            boundary="mur") -> Workload:
     """2D3V laser-plasma: dx = lambda/32, a0 = 10 laser (waist 4 lambda, 8-cycle
     sin^2 envelope) entering at x-min through an absorbing edge; electron +
     proton slab at 10 n_c with a 2 lambda linear ramp; absorbing x, periodic y.
@@ -234,9 +236,11 @@ def laser2d(nx=2048, ny=1024, ppc=32, order=2, steps=1600, precision="fp32", see
     sp = [SpeciesSpec(**ELECTRON, ppc=ppc, vth=0.01, density=10.0, profile="slab", slab=(r0, r1, p1)),
           SpeciesSpec(**PROTON, ppc=ppc, vth=0.0, density=10.0, profile="slab", slab=(r0, r1, p1),
                       same_positions_as=0)]
-    return Workload(f"laser2d_{nx}x{ny}", 2, (nx, ny), h, cfl_dt(h), order, True, sp, steps,
+    return Workload(f"laser2d_{nx}x{ny}" + ("_cpml" if boundary == "cpml" else ""), 2, (nx, ny), h,
+                    cfl_dt(h), order, True, sp, steps,
                     laser=LaserSpec(a0=10.0, w0=4.0 * LAMBDA, tau=8.0 * LAMBDA),
-                    precision=precision, seed=SEED_BASE + 1000 * 2 if seed is None else seed)
+                    precision=precision, seed=SEED_BASE + 1000 * 2 if seed is None else seed,
+                    boundary=boundary)
 
 
 def thermal3d(n=256, ppc=8, vth=0.05, order=2, steps=100, precision="fp32", seed=None) -> Workload:
@@ -248,7 +252,8 @@ def thermal3d(n=256, ppc=8, vth=0.05, order=2, steps=100, precision="fp32", seed
                     precision=precision, seed=SEED_BASE + 1000 * 3 if seed is None else seed)
 
 
-def laser3d(nx=512, ny=256, nz=256, ppc=16, order=1, steps=500, precision="fp32", seed=None) -> Workload:
+def laser3d(nx=512, ny=256, nz=256, ppc=16, order=1, steps=500, precision="fp32", seed=None,
+            boundary="mur") -> Workload:
     """3D3V laser-target: dx = lambda/32, a0 = 20 laser (waist 2 lambda, 8-cycle
     envelope) on a 30 n_c slab 2 lambda thick at x in [4, 6] lambda (scaled with
     nx), electrons + protons, absorbing x, periodic y and z."""
@@ -261,9 +266,10 @@ def laser3d(nx=512, ny=256, nz=256, ppc=16, order=1, steps=500, precision="fp32"
     sp = [SpeciesSpec(**ELECTRON, ppc=ppc, vth=0.01, density=30.0, profile="slab", slab=(r0, r1, p1)),
           SpeciesSpec(**PROTON, ppc=ppc, vth=0.0, density=30.0, profile="slab", slab=(r0, r1, p1),
                       same_positions_as=0)]
-    return Workload(f"laser3d_{nx}x{ny}x{nz}", 3, (nx, ny, nz), h, cfl_dt(h), order, True, sp, steps,
+    return Workload(f"laser3d_{nx}x{ny}x{nz}" + ("_cpml" if boundary == "cpml" else ""), 3, (nx, ny, nz), h, cfl_dt(h), order, True, sp, steps,
                     laser=LaserSpec(a0=20.0, w0=2.0 * LAMBDA, tau=8.0 * LAMBDA),
-                    precision=precision, seed=SEED_BASE + 1000 * 5 if seed is None else seed)
+                    precision=precision, seed=SEED_BASE + 1000 * 5 if seed is None else seed,
+                    boundary=boundary)
 
 
 M_E_KEV = 510.999  # electron rest energy, keV

@@ -15,7 +15,8 @@ def oracle_case(wl: W.Workload, parts):
         c = wl.laser_center()
         laser = O.Laser(wl.laser.a0, wl.laser.w0, wl.laser.tau, wl.laser.omega, c[0],
                         c[1] if wl.dim == 3 else 0.0)
-    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x, laser=laser)
+    pml = O.Pml() if getattr(wl, "boundary", "mur") == "cpml" else None
+    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x, laser=laser, pml=pml)
     h = np.array(wl.h)[:, None]
     sps = [O.Species(p.q, p.m, (p.cell + p.off) * h, p.u, p.w) for p in parts]
     return g, sps

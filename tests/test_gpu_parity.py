@@ -77,6 +77,17 @@ def test_fp64_laser3d_absorbing_small():
     _fp64_parity(wl, 60, 1e-10)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp64_laser_cpml_small(dim):
+    """The laser entering as a current sheet, CPML layers on the x ends."""
+    if dim == 2:
+        wl = W.laser2d(nx=128, ny=64, ppc=2, precision="fp64", boundary="cpml")
+        _fp64_parity(wl, 80, 1e-10)
+    else:
+        wl = W.laser3d(nx=128, ny=8, nz=8, ppc=1, precision="fp64", boundary="cpml")
+        _fp64_parity(wl, 60, 1e-10)
+
+
 def _fp32_case(wl, steps, tile=None):
     from paper_2607_13507_b300 import lpic
     parts = W.load_all(wl)
@@ -118,6 +129,18 @@ def test_fp32_laser2d_small_against_oracle():
     accumulates in E and B like a random walk, sqrt(80) * 3e-5 ~ 3e-4;
     bound 1e-3."""
     wl = W.laser2d(nx=128, ny=64, ppc=2, precision="fp32")
+    steps = 80
+    G, g, sps = _fp32_case(wl, steps)
+    for c in range(3):
+        ee = rel_l2(G.E[c].cpu().numpy(), g.E[c])
+        eb = rel_l2(G.B[c].cpu().numpy(), g.B[c])
+        assert ee < 1e-3, ("E", c, ee)
+        assert eb < 1e-3, ("B", c, eb)
+
+
+def test_fp32_laser2d_cpml_small_against_oracle():
+    """As the Mur case, with CPML layers and the laser sheet."""
+    wl = W.laser2d(nx=128, ny=64, ppc=2, precision="fp32", boundary="cpml")
     steps = 80
     G, g, sps = _fp32_case(wl, steps)
     for c in range(3):
