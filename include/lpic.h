@@ -231,7 +231,37 @@ lpic_status lpic_graph_steps(lpic_grid_t grid, int nsteps, cudaStream_t stream);
  * arithmetic as the deposit (rho = rho_int * rho_scale). */
 lpic_status lpic_deposit_charge(lpic_grid_t grid, int species_id, void *rho, cudaStream_t stream);
 
-/* Gauss's law diagnostic (Sec. 3.2; Sec. 4.1 checks charge conservation):
+/* The unfused path (Sec. 2.3 "Callback system" and Sec. 3.3: the paper fuses
+ * position push, field interpolation, momentum push and deposition into one
+ * loop only when no callback sits between them).  Stage 1,
+ * lpic_gather_fields, sorts the species by tile if it was pushed since its
+ * last sort, then writes each particle's six interpolated field components
+ * (E_x, E_y, E_z, B_x, B_y, B_z at x^{n+1/2}, the fused kernel's gather) to
+ * the caller's device array fields[6][capacity] (float), indexed like the
+ * current particle buffer.  Between the stages the caller may read or change
+ * those fields with its own kernels on `stream` (an external field, a
+ * per-particle diagnostic).  Stage 2, lpic_push_deposit_fields, then pushes
+ * and deposits the species exactly as lpic_gather_push_deposit would, with
+ * the fields read from the array; it must follow stage 1 of the same species
+ * with no sort or push in between (else LPIC_EINVAL).  With unchanged fields
+ * the two stages give bit-identical results to the fused call.  FP32 path
+ * only (LPIC_EUNSUPPORTED otherwise).  Asynchronous on `stream`. */
+lpic_status lpic_gather_fields(lpic_grid_t grid, int species_id, float *fields, cudaStream_t stream);
+lpic_status lpic_push_deposit_fields(lpic_grid_t grid, int species_id, const float *fields,
+                                     cudaStream_t stream);
+
+/* Species-resolved fields (Sec. 6.1): one lpic_step of `grid` that also
+ * advances the fields of `aux` with the current of species `species_id`
+ * alone as the source (Maxwell's equations are linear, so aux holds the
+ * field that species radiates).  aux is another grid with the same
+ * geometry, time step, precision and x boundary and no species (its laser,
+ * if any, is its own); the species is deposited first and its current copied
+ * into aux's J, then the other species deposit on top.  Asynchronous on
+ * `stream`. */
+lpic_status lpic_step_resolved(lpic_grid_t grid, double t, int species_id, lpic_grid_t aux,
+                               cudaStream_t stream);
+
+/* Gauss's law diagnostic/* Gauss's law diagnostic (Sec. 3.2; Sec. 4.1 checks charge conservation):
  * the discrete divergence of the current E at the integer nodes,
  * sum_d (E_d(i+1/2) - E_d(i-1/2)) / h_d, in double, written to the caller's
  * device array out[nz][ny][fx] (overwritten; periodic wrap, E_x = 0 below an

@@ -53,6 +53,8 @@ lpic_status fail(lpic_status s, const char* fmt, ...) {
 struct Species {
     double q = 0, m = 1;
     long long cap = 0;
+    long long sort_gen = 0;      // sorts so far (the particle order changes with each)
+    long long gather_gen = -1;   // sort_gen at the last unfused gather stage
     void* buf[2] = {nullptr, nullptr};
     int cur = 0;
     int* d_n = nullptr;          // particles in the current buffer
@@ -189,20 +191,14 @@ void box_divisors(const lpic_grid* g, Tiles& t) {
     t.fJ = make_fastdiv((unsigned)(H0 * H1 * H2));
 }
 
-// tile-kernel instance and its dynamic shared memory
-template <int DIM, int ORDER>
-lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
+// Arguments of the tile kernel for one species.
+GpdArgs gpd_args(lpic_grid* g, Species& s, bool count_next) {
     const P32 p = view32(g, s, s.cur);
     Tiles t{};
     for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; t.m[d] = g->m[d]; t.fT[d] = g->fT[d]; }
-    t.next_count = nullptr;
-    if (count_next) {
-        LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (g->ntiles + 1), st));
-        t.next_count = s.d_count;
-    }
+    t.next_count = count_next ? s.d_count : nullptr;
     t.esc = s.d_esc;
     t.nesc = s.d_nesc;
-    LPIC_CUDA(cudaMemsetAsync(s.d_nesc, 0, sizeof(int), st));
     t.start = s.d_start;
     t.items = s.d_items;
     t.nitems = s.d_nitems;
@@ -211,13 +207,34 @@ lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_n
     box_divisors(g, t);
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
-    GpdArgs A{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
-              p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
-              (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status};
+    return GpdArgs{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
+                   p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
+                   (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status, nullptr, 0};
+}
+
+// tile-kernel instance and its dynamic shared memory
+template <int DIM, int ORDER>
+lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
+    if (count_next) LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (g->ntiles + 1), st));
+    LPIC_CUDA(cudaMemsetAsync(s.d_nesc, 0, sizeof(int), st));
+    const GpdArgs A = gpd_args(g, s, count_next);
     Gpd32<DIM, ORDER>::tile(A, (unsigned)s.item_cap, g->smem32, st);
     LPIC_LAUNCHED("k_gpd32");
     Gpd32<DIM, ORDER>::escape(A, (unsigned)(2 * g->nsm), st);
     LPIC_LAUNCHED("k_gpd32_escape");
+    return LPIC_OK;
+}
+
+// One unfused stage (gather: fields written; else push and deposit with the
+// fields read) on freshly sorted particles, which never leave their tile.
+template <int DIM, int ORDER>
+lpic_status launch_stage(lpic_grid* g, Species& s, cudaStream_t st, bool gather, float* fields) {
+    GpdArgs A = gpd_args(g, s, false);
+    A.fields = fields;
+    A.fcap = s.cap;
+    if (gather) Gpd32Stages<DIM, ORDER>::gather(A, (unsigned)s.item_cap, g->smem32, st);
+    else        Gpd32Stages<DIM, ORDER>::push(A, (unsigned)s.item_cap, g->smem32, st);
+    LPIC_LAUNCHED(gather ? "k_gpd32_gather" : "k_gpd32_fields_in");
     return LPIC_OK;
 }
 
@@ -233,7 +250,8 @@ lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
 
 template <int DIM, int ORDER>
 cudaError_t set_smem_attrs(size_t bytes) {
-    return Gpd32<DIM, ORDER>::set_smem(bytes);
+    const cudaError_t e = Gpd32<DIM, ORDER>::set_smem(bytes);
+    return e != cudaSuccess ? e : Gpd32Stages<DIM, ORDER>::set_smem(bytes);
 }
 
 // clock != nullptr: the laser time is read from the device clock plus t.
@@ -360,6 +378,7 @@ lpic_status sort_one(lpic_grid* g, Species& s, cudaStream_t st, bool use_counts 
     s.sorted = true;
     s.since_sort = 0;
     s.counts_fresh = false;
+    s.sort_gen += 1;
     return LPIC_OK;
 }
 
@@ -760,6 +779,41 @@ lpic_status lpic_gather_push_deposit(lpic_grid_t g, int sid, cudaStream_t st) {
     return gpd_impl(g, sid, st, false);
 }
 
+lpic_status lpic_gather_fields(lpic_grid_t g, int sid, float* fields, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "the unfused stages need the FP32 path");
+    if (!fields) return fail(LPIC_EINVAL, "fields is NULL");
+    Species& s = g->sp[sid];
+    g->started = true;
+    if (!s.sorted || s.since_sort > 0)
+        if (lpic_status r = sort_one(g, s, st, false)) return r;
+    const int D = g->d.dim, O = g->d.shape_order;
+    lpic_status r;
+    if (D == 2) r = (O == 1) ? launch_stage<2, 1>(g, s, st, true, fields) : launch_stage<2, 2>(g, s, st, true, fields);
+    else        r = (O == 1) ? launch_stage<3, 1>(g, s, st, true, fields) : launch_stage<3, 2>(g, s, st, true, fields);
+    if (r == LPIC_OK) s.gather_gen = s.sort_gen;
+    return r;
+}
+
+lpic_status lpic_push_deposit_fields(lpic_grid_t g, int sid, const float* fields, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "the unfused stages need the FP32 path");
+    if (!fields) return fail(LPIC_EINVAL, "fields is NULL");
+    Species& s = g->sp[sid];
+    if (s.gather_gen != s.sort_gen || s.since_sort != 0)
+        return fail(LPIC_EINVAL, "species %d: call lpic_gather_fields first (the particles were re-sorted or "
+                    "pushed since)", sid);
+    const int D = g->d.dim, O = g->d.shape_order;
+    float* f = const_cast<float*>(fields);
+    lpic_status r;
+    if (D == 2) r = (O == 1) ? launch_stage<2, 1>(g, s, st, false, f) : launch_stage<2, 2>(g, s, st, false, f);
+    else        r = (O == 1) ? launch_stage<3, 1>(g, s, st, false, f) : launch_stage<3, 2>(g, s, st, false, f);
+    s.since_sort += 1;
+    s.counts_fresh = false;
+    s.gather_gen = -1;
+    return r;
+}
+
 static lpic_status maxwell_any(lpic_grid_t g, int half, double t, cudaStream_t st, const double* clock) {
     if (g->d.precision == LPIC_FP32_FIXED)
         return g->d.dim == 3 ? maxwell_impl<3, float, long long>(g, half, t, st, clock)
@@ -801,6 +855,46 @@ static lpic_status step_impl(lpic_grid_t g, double t, cudaStream_t st, double* c
 lpic_status lpic_step(lpic_grid_t g, double t, cudaStream_t st) {
     if (lpic_status r = check_grid(g)) return r;
     return step_impl(g, t, st, nullptr);
+}
+
+// A step that also advances `aux` with the current of species sid alone: the
+// species is deposited first, its current copied into aux's J, then the
+// other species deposit on top; aux's Maxwell halves use the grid's
+// fixed-point scale.
+lpic_status lpic_step_resolved(lpic_grid_t g, double t, int sid, lpic_grid_t aux, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (!aux || aux == g) return fail(LPIC_EINVAL, "aux must be another grid");
+    const lpic_grid_desc &a = aux->d, &d = g->d;
+    if (a.dim != d.dim || a.nx != d.nx || a.ny != d.ny || a.nz != d.nz || a.dx != d.dx || a.dy != d.dy ||
+        a.dz != d.dz || a.dt != d.dt || a.precision != d.precision || a.absorb_x != d.absorb_x ||
+        (a.absorb_x == 2 && a.pml_cells != d.pml_cells))
+        return fail(LPIC_EINVAL, "aux must have the grid's geometry, time step, precision and x boundary");
+    if (!aux->sp.empty()) return fail(LPIC_EINVAL, "aux must hold no species");
+    auto aux_half = [&](int half, double th) -> lpic_status {
+        for (int c = 0; c < 3; ++c) aux->jscale[c] = g->jscale[c];
+        return maxwell_any(aux, half, th, st, nullptr);
+    };
+    if (lpic_status r = maxwell_any(g, 0, t, st, nullptr)) return r;
+    if (lpic_status r = aux_half(0, t)) return r;
+    if (lpic_status r = lpic_zero_current(g, st)) return r;
+    const int n = (int)g->sp.size();
+    const size_t jbytes = (size_t)g->nfield * (d.precision == LPIC_FP64 ? sizeof(double) : sizeof(long long));
+    for (int k = 0; k < n; ++k) {
+        const int s = k == 0 ? sid : (k <= sid ? k - 1 : k);
+        Species& sp = g->sp[s];
+        bool count_next = false;
+        if (d.precision == LPIC_FP32_FIXED) {
+            if (!sp.sorted || sp.since_sort >= g->K)
+                if (lpic_status r = sort_one(g, sp, st, sp.sorted && sp.counts_fresh)) return r;
+            count_next = sp.since_sort + 1 >= g->K;
+        }
+        if (lpic_status r = gpd_impl(g, s, st, count_next)) return r;
+        if (k == 0)
+            for (int c = 0; c < 3; ++c)
+                LPIC_CUDA(cudaMemcpyAsync(aux->d.J[c], g->d.J[c], jbytes, cudaMemcpyDeviceToDevice, st));
+    }
+    if (lpic_status r = maxwell_any(g, 1, t + 0.5 * d.dt, st, nullptr)) return r;
+    return aux_half(1, t + 0.5 * d.dt);
 }
 
 lpic_status lpic_set_clock(lpic_grid_t g, double t, cudaStream_t st) {
@@ -853,7 +947,7 @@ lpic_status lpic_graph_steps(lpic_grid_t g, int nsteps, cudaStream_t st) {
         // replay the host-side bookkeeping of the captured step
         if (g->d.precision == LPIC_FP32_FIXED)
             for (auto& s : g->sp) {
-                if (!s.sorted || s.since_sort >= g->K) { s.cur = 1 - s.cur; s.sorted = true; s.since_sort = 0; }
+                if (!s.sorted || s.since_sort >= g->K) { s.cur = 1 - s.cur; s.sorted = true; s.since_sort = 0; s.sort_gen += 1; }
                 s.since_sort += 1;
                 s.counts_fresh = s.since_sort >= g->K;
             }
@@ -1084,6 +1178,7 @@ void ens_sync_grids(lpic_ensemble* e) {
         Species& s = e->grids[sl.first]->sp[sl.second];
         s.cur = e->parity;
         s.sorted = true;
+        s.sort_gen += 1;
         s.since_sort = 1;
         s.counts_fresh = true;
         e->grids[sl.first]->started = true;

@@ -597,10 +597,18 @@ struct GpdArgs {
     CellDecode dec;
     float k, sq, dth0, dth1, dth2;
     unsigned* st;
+    float* fields;       // unfused stages: per-particle E_x..B_z, [6][fcap]
+    long long fcap;
 };
 
+// Forms of the tile kernel: the fused gather/push/deposit, and the two
+// stages of the unfused path (the gather alone, writing each particle's
+// fields; the push and deposit with fields read back).  Between them the
+// caller may change the fields (an external field, a diagnostic).
+enum { kGpdFused = 0, kGpdGather = 1, kGpdFieldsIn = 2 };
+
 // One work item (a tile, or a chunk of a crowded tile) of one species.
-template <int DIM, int ORDER>
+template <int DIM, int ORDER, int MODE = kGpdFused>
 __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float4* smem4) {
     const Geo& g = A.g;
     const Ptr3<const float>& E = A.E;
@@ -638,7 +646,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     int* sRing = sSt + kStageWords * kGpdThreads;
     int* sCnt = sRing + kStageWords * kRing;
 
-    for (int idx = threadIdx.x; idx < 6 * fsz; idx += blockDim.x) {
+    for (int idx = threadIdx.x; MODE != kGpdFieldsIn && idx < 6 * fsz; idx += blockDim.x) {
         const int c = fdiv(idx, t.fF), r = idx - c * fsz;
         const int q = fdiv(r, t.fG0), lx = r - q * G0;
         const int lz = (DIM == 3) ? fdiv(q, t.fG1) : 0, ly = q - lz * G1;
@@ -736,9 +744,14 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 inside &= (lc[d] >= 0 && lc[d] < Te[d]);
             }
             if (!inside) {
-                // beyond the tile's drift margin: queued for the global-memory
-                // path, which also counts its new tile key
-                t.esc[atomicAdd(t.nesc, 1)] = i;
+                if (MODE == kGpdFused) {
+                    // beyond the tile's drift margin: queued for the global-memory
+                    // path, which also counts its new tile key
+                    t.esc[atomicAdd(t.nesc, 1)] = i;
+                } else {
+                    // the unfused stages run on freshly sorted particles only
+                    set_status(st, LPIC_ST_HALO);
+                }
                 cell_out = -1;
             } else {
                 float f[3], ux, uy, uz, w;
@@ -754,7 +767,16 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
                 const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
                 float fld[6];
-                gather32<DIM, ORDER>(LoadShared<DIM>{sF, fsz, G0, G1}, nx_, ny_, nz_, hx_, hy_, hz_, fld);
+                if constexpr (MODE == kGpdFieldsIn) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) fld[c] = A.fields[c * A.fcap + i];
+                } else {
+                    gather32<DIM, ORDER>(LoadShared<DIM>{sF, fsz, G0, G1}, nx_, ny_, nz_, hx_, hy_, hz_, fld);
+                }
+                if constexpr (MODE == kGpdGather) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) A.fields[c * A.fcap + i] = fld[c];
+                } else {
                 boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
                 if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
                     set_status(st, LPIC_ST_NAN);
@@ -811,6 +833,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                         p.u[0][i] = ux; p.u[1][i] = uy; p.u[2][i] = uz;
                     }
                 }
+                }   // not the gather stage
             }
         }
         // histogram of the tile keys for the next sort (all lanes take part)
@@ -905,11 +928,11 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 }
 
 
-template <int DIM, int ORDER>
+template <int DIM, int ORDER, int MODE = kGpdFused>
 __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB) k_gpd32(GpdArgs A) {
     extern __shared__ float4 smem4[];
     if ((int)blockIdx.x >= *A.t.nitems) return;
-    gpd_item<DIM, ORDER>(A, blockIdx.x, smem4);
+    gpd_item<DIM, ORDER, MODE>(A, blockIdx.x, smem4);
 }
 
 // Persistent form for a batch of grids: blocks pull work items from one

@@ -25,4 +25,13 @@ struct Gpd32 {
     static const void* queue_fn();
 };
 
+// The unfused stages (kGpdGather, kGpdFieldsIn), compiled in translation
+// units of their own (lpic_gpd32s_<dim><order>.cu).
+template <int DIM, int ORDER>
+struct Gpd32Stages {
+    static cudaError_t set_smem(size_t bytes);
+    static void gather(const GpdArgs& A, unsigned blocks, size_t smem, cudaStream_t st);
+    static void push(const GpdArgs& A, unsigned blocks, size_t smem, cudaStream_t st);
+};
+
 }  // namespace lpic

@@ -26,6 +26,7 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_species_query", "lpic_sort_particles", "lpic_zero_current",
            "lpic_gather_push_deposit", "lpic_maxwell_half_step", "lpic_step",
            "lpic_deposit_charge", "lpic_div_e", "lpic_positions_at_step", "lpic_diagnostics",
+           "lpic_gather_fields", "lpic_push_deposit_fields", "lpic_step_resolved",
            "lpic_grid_get_info", "lpic_check_status", "lpic_last_error", "lpic_set_clock",
            "lpic_graph_steps", "lpic_sort_tiles_static", "lpic_kernel_timing",
            "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
@@ -120,6 +121,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                            vp, vp, vp, st]
     lib.lpic_deposit_charge.argtypes = [vp, i, vp, st]
     lib.lpic_div_e.argtypes = [vp, vp, st]
+    lib.lpic_gather_fields.argtypes = [vp, i, vp, st]
+    lib.lpic_push_deposit_fields.argtypes = [vp, i, vp, st]
+    lib.lpic_step_resolved.argtypes = [vp, ctypes.c_double, i, vp, st]
     lib.lpic_positions_at_step.argtypes = [vp, i, vp, st]
     lib.lpic_diagnostics.argtypes = [vp, ctypes.POINTER(Diag), st]
     lib.lpic_grid_get_info.argtypes = [vp, ctypes.POINTER(GridInfo)]
@@ -363,6 +367,24 @@ class Grid:
         if rc not in (0, 4):
             _check(rc)
         return bits.value
+
+    def gather_fields(self, sid, out=None, stream=None) -> torch.Tensor:
+        """Unfused stage 1: the species' particles' fields, float32 (6, capacity)."""
+        sp = self.species[sid]
+        if out is None:
+            out = torch.empty((6, sp.cap), dtype=torch.float32, device=self.device)
+        _check(load().lpic_gather_fields(self.h_, sid, out.data_ptr(), _stream(stream)))
+        return out
+
+    def push_deposit_fields(self, sid, fields, stream=None):
+        """Unfused stage 2: push and deposit with the given per-particle fields."""
+        assert fields.dtype == torch.float32 and fields.is_contiguous()
+        assert fields.shape == (6, self.species[sid].cap)
+        _check(load().lpic_push_deposit_fields(self.h_, sid, fields.data_ptr(), _stream(stream)))
+
+    def step_resolved(self, t, sid, aux: "Grid", stream=None):
+        """One step that also advances aux with the current of species sid alone."""
+        _check(load().lpic_step_resolved(self.h_, t, sid, aux.h_, _stream(stream)))
 
     def div_e(self, stream=None) -> torch.Tensor:
         """Discrete divergence of E at the integer nodes (float64)."""
