@@ -249,13 +249,28 @@ def run_b300(args, rank, world, local_rank):
     clock.start()
     time.sleep(0.3)
     launches0 = G.info().launches
-    G.kernel_timing(args.steps * len(G.species))
+    unfused = bool(getattr(args, "unfused", False))
+    bufs = [torch.empty((6, sp.cap), dtype=torch.float32, device=dev) for sp in G.species] if unfused else []
+
+    def one_step(t):
+        if not unfused:
+            G.step(t, stream)
+            return
+        # the unfused path: gather stage, (hooks would go here), push/deposit stage
+        G.maxwell_half(0, t, stream)
+        G.zero_current(stream)
+        for sid in range(len(G.species)):
+            G.gather_fields(sid, out=bufs[sid], stream=stream)
+            G.push_deposit_fields(sid, bufs[sid], stream=stream)
+        G.maxwell_half(1, t + 0.5 * dt, stream)
+
+    G.kernel_timing(args.steps * len(G.species) * (2 if unfused else 1))
     t_start, t_stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     t_start.record(stream)
     with torch.cuda.stream(stream):
         for _ in range(args.steps):
-            G.step(step * dt, stream)
+            one_step(step * dt)
             step += 1
     t_stop.record(stream)
     torch.cuda.synchronize(dev)
@@ -278,6 +293,12 @@ def run_b300(args, rank, world, local_rank):
         algo_bytes_step += algorithmic_bytes(wl, n_mean, loaded[i], args.precision)[0]
     launch_bytes = algo_bytes_step / len(G.species)
     launch_time = gpd_time / max(1, gpd_launches)
+    if unfused:
+        # a "launch" is the pair of stages; the field array adds 24 B written
+        # and 24 B read per particle
+        n_mean_all = sum(0.5 * (a + b) for a, b in zip(counts0, counts1))
+        launch_bytes += 48.0 * n_mean_all / len(G.species)
+        launch_time *= 2.0
 
     if world > 1:
         elapsed, psteps = reduce_over_ranks(elapsed, psteps, dev)
@@ -304,7 +325,8 @@ def run_b300(args, rank, world, local_rank):
             "config": {
                 "workload": WORKLOADS[args.workload][0] + (
                     "; CPML x layers of 16 cells, laser entering as a current sheet"
-                    if args.boundary == "cpml" else ""),
+                    if args.boundary == "cpml" else "") + (
+                    "; unfused path (gather stage, then push/deposit stage)" if unfused else ""),
                 "grid": list(wl.n), "species": len(wl.species),
                 "particles": int(sum(counts0)), "pre_steps": pre,
                 "l2": "inputs larger than L2 (particle state %.1f GB)" % (
@@ -313,13 +335,15 @@ def run_b300(args, rank, world, local_rank):
             },
             "gpd_particle_steps_per_s": psteps / max(gpd_time, 1e-12) if world == 1 else None,
             "roofline": {
-                "bound": "hbm", "kernel": "k_gpd32" if args.precision == "fp32" else "k_gpd64",
+                "bound": "hbm",
+                "kernel": ("k_gpd32 gather + fields-in stages" if unfused else "k_gpd32")
+                if args.precision == "fp32" else "k_gpd64",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{which} hbm_gbs",
-                "bytes_per_particle_step": per_ps,
+                "bytes_per_particle_step": per_ps + (48 if unfused else 0),
                 "algorithmic_bytes_per_launch": launch_bytes,
                 "launch_ms": 1e3 * launch_time,
-                "traffic": ncu_traffic(args.workload),
+                "traffic": None if unfused else ncu_traffic(args.workload),
             },
             "gpu_launches": int(launches),
             "clocks": clocks,
@@ -525,6 +549,8 @@ def main():
                     help="transverse cells of the 2D laser workload (smaller cases for profiling)")
     ap.add_argument("--boundary", choices=["mur", "cpml"], default="mur",
                     help="absorbing x of the laser workloads: Mur edges or CPML layers")
+    ap.add_argument("--unfused", action="store_true",
+                    help="time the unfused path (gather stage + push/deposit stage) instead of the fused kernel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)

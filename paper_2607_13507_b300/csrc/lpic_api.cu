@@ -789,8 +789,11 @@ lpic_status lpic_gather_fields(lpic_grid_t g, int sid, float* fields, cudaStream
         if (lpic_status r = sort_one(g, s, st, false)) return r;
     const int D = g->d.dim, O = g->d.shape_order;
     lpic_status r;
+    const bool timed = g->timing && g->ev_used + 2 <= g->ev.size();
+    if (timed) LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used], st));
     if (D == 2) r = (O == 1) ? launch_stage<2, 1>(g, s, st, true, fields) : launch_stage<2, 2>(g, s, st, true, fields);
     else        r = (O == 1) ? launch_stage<3, 1>(g, s, st, true, fields) : launch_stage<3, 2>(g, s, st, true, fields);
+    if (timed) { LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used + 1], st)); g->ev_used += 2; }
     if (r == LPIC_OK) s.gather_gen = s.sort_gen;
     return r;
 }
@@ -806,8 +809,11 @@ lpic_status lpic_push_deposit_fields(lpic_grid_t g, int sid, const float* fields
     const int D = g->d.dim, O = g->d.shape_order;
     float* f = const_cast<float*>(fields);
     lpic_status r;
+    const bool timed = g->timing && g->ev_used + 2 <= g->ev.size();
+    if (timed) LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used], st));
     if (D == 2) r = (O == 1) ? launch_stage<2, 1>(g, s, st, false, f) : launch_stage<2, 2>(g, s, st, false, f);
     else        r = (O == 1) ? launch_stage<3, 1>(g, s, st, false, f) : launch_stage<3, 2>(g, s, st, false, f);
+    if (timed) { LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used + 1], st)); g->ev_used += 2; }
     s.since_sort += 1;
     s.counts_fresh = false;
     s.gather_gen = -1;
