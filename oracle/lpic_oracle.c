@@ -46,6 +46,7 @@
  * waves and the laser sheet's amplitude and one-sidedness.
  */
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -659,11 +660,15 @@ int orc_push_species(orc_grid *g, orc_species *sp)
         if (!sp->alive[p]) continue;
         double xm[3] = {0, 0, 0}, x1[3] = {0, 0, 0}, xe[3] = {0, 0, 0}, u[3], E[3], B[3];
         for (int c = 0; c < 3; ++c) u[c] = sp->u[c][p];
-        double g0 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        for (int d = 0; d < g->dim; ++d) xm[d] = sp->x[d][p] + 0.5 * dt * u[d] / g0;
+        /* a massless species (photons, m = 0, q = 0) moves at c along u */
+        const int massless = sp->m == 0.0;
+        const double uu0 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double g0 = massless ? sqrt(uu0) : sqrt(1.0 + uu0);
+        for (int d = 0; d < g->dim; ++d) xm[d] = sp->x[d][p] + (g0 > 0 ? 0.5 * dt * u[d] / g0 : 0.0);
         if (orc_gather(g, xm, E, B) != ORC_OK) return ORC_EOUTSIDE;
-        orc_boris(sp->q, sp->m, dt, u, E, B);
-        double g1 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (!massless) orc_boris(sp->q, sp->m, dt, u, E, B);
+        const double uu1 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        double g1 = massless ? (uu1 > 0 ? sqrt(uu1) : 1.0) : sqrt(1.0 + uu1);
         for (int d = 0; d < g->dim; ++d) {
             x1[d] = xm[d] + 0.5 * dt * u[d] / g1;
             xe[d] = xm[d] + dt * u[d] / g1;
@@ -717,7 +722,8 @@ void orc_energy(const orc_grid *g, const orc_species *sp, int nsp, double out[3]
             if (!sp[s].alive[p]) continue;
             double u2 = sp[s].u[0][p] * sp[s].u[0][p] + sp[s].u[1][p] * sp[s].u[1][p]
                       + sp[s].u[2][p] * sp[s].u[2][p];
-            ek += sp[s].w[p] * sp[s].m * (sqrt(1.0 + u2) - 1.0);
+            /* photons (m = 0) carry energy |u| m_e c^2 */
+            ek += sp[s].m == 0.0 ? sp[s].w[p] * sqrt(u2) : sp[s].w[p] * sp[s].m * (sqrt(1.0 + u2) - 1.0);
             qt += sp[s].w[p] * sp[s].q;
         }
     for (int c = 0; c < 3; ++c)
@@ -740,4 +746,169 @@ void orc_div_e(const orc_grid *g, double *out)
                 if (g->dim == 3) v += (g->E[2][n] - g->E[2][node(g, i, j, k - 1)]) / g->dz;
                 out[n] = v;
             }
+}
+
+/* --------------------------------------------- QED: nonlinear Compton (Sec. 3.4)
+ * Photon emission by electrons (and positrons) in the locally-constant-field
+ * approximation, event-based Monte Carlo with an optical depth per particle
+ * (Sec. 3.4 and its references).  Normalised units: eps_ref = hbar omega_ref /
+ * (m c^2) for the unit frequency omega_ref; fields in m c omega_ref / e.
+ *
+ * chi_e = eps_ref gamma sqrt((E + beta x B)^2 - (beta . E)^2).
+ * Emission spectrum per unit time and photon energy fraction xi:
+ *   d2W / dt dxi = alpha / (eps_ref sqrt(3) pi gamma) S(xi, chi),
+ *   S = (1 - xi + 1 / (1 - xi)) K_{2/3}(delta) - int_delta^inf K_{1/3}(s) ds,
+ *   delta = 2 xi / (3 chi (1 - xi)),
+ * with the modified Bessel functions from their integral representation
+ * K_nu(x) = int_0^inf exp(-x cosh t) cosh(nu t) dt (and int_x^inf K_nu =
+ * int_0^inf exp(-x cosh t) cosh(nu t) / cosh t dt), evaluated by the
+ * trapezoid rule (the integrands decay double-exponentially).
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), counter (id, step,
+ * kind, 0), key (seed_lo, seed_hi). */
+
+static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c0 = hi1 ^ c1 ^ k0; c1 = lo1; c2 = hi0 ^ c3 ^ k1; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+void orc_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) { philox4x32_10(ctr, key, out); }
+
+/* uniform in (0, 1) from 32 random bits */
+static double u01(uint32_t x) { return ((double)x + 0.5) * (1.0 / 4294967296.0); }
+
+static double bessel_k_int(double nu, double x, int integrated)
+{
+    if (x <= 0.0) return INFINITY;
+    const double h = 0.01;
+    double tmax = acosh(fmax(1.0, 60.0 / x)) + 1.0;
+    double sum = 0.5 * exp(-x) * (integrated ? 1.0 : 1.0);
+    for (double t = h; t <= tmax; t += h) {
+        const double ch = cosh(t);
+        double v = exp(-x * ch) * cosh(nu * t);
+        if (integrated) v /= ch;
+        sum += v;
+    }
+    return sum * h;
+}
+
+double orc_bessel_k(double nu, double x) { return bessel_k_int(nu, x, 0); }
+double orc_bessel_k_int(double nu, double x) { return bessel_k_int(nu, x, 1); }
+
+double orc_compton_s(double xi, double chi)
+{
+    if (xi <= 0.0 || xi >= 1.0) return 0.0;
+    const double delta = 2.0 * xi / (3.0 * chi * (1.0 - xi));
+    if (delta > 700.0) return 0.0;
+    return (1.0 - xi + 1.0 / (1.0 - xi)) * bessel_k_int(2.0 / 3.0, delta, 0) - bessel_k_int(1.0 / 3.0, delta, 1);
+}
+
+/* cumulative int_0^xi S dxi' on xi = y^3, y in [0, 1] (n intervals); cum[n] = total */
+static void compton_cumulative(double chi, int n, double *cum)
+{
+    cum[0] = 0.0;
+    double prev = 0.0;              /* S(y^3) 3 y^2 -> finite limit at y = 0 */
+    {
+        const double y = 1e-4;
+        prev = orc_compton_s(y * y * y, chi) * 3.0 * y * y;
+    }
+    for (int k = 1; k <= n; ++k) {
+        const double y = (double)k / n;
+        const double f = (k == n) ? 0.0 : orc_compton_s(y * y * y, chi) * 3.0 * y * y;
+        cum[k] = cum[k - 1] + 0.5 * (prev + f) / n;
+        prev = f;
+    }
+}
+
+/* total emission rate per unit time (units of omega_ref) */
+double orc_compton_rate(double chi, double gamma, double eps_ref)
+{
+    const int n = 2000;
+    double *cum = (double *)malloc(sizeof(double) * (n + 1));
+    compton_cumulative(chi, n, cum);
+    const double F = cum[n];
+    free(cum);
+    const double alpha = 1.0 / 137.035999084;
+    return alpha / (eps_ref * sqrt(3.0) * M_PI * gamma) * F;
+}
+
+/* photon energy fraction with cumulative probability r */
+double orc_compton_xi(double chi, double r)
+{
+    const int n = 2000;
+    double *cum = (double *)malloc(sizeof(double) * (n + 1));
+    compton_cumulative(chi, n, cum);
+    const double target = r * cum[n];
+    int k = 0;
+    while (k < n && cum[k + 1] < target) ++k;
+    const double f = (cum[k + 1] > cum[k]) ? (target - cum[k]) / (cum[k + 1] - cum[k]) : 0.0;
+    const double y = (k + f) / n;
+    free(cum);
+    return y * y * y;
+}
+
+double orc_chi_e(const double u[3], const double E[3], const double B[3], double eps_ref)
+{
+    const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double b[3] = {u[0] / gam, u[1] / gam, u[2] / gam};
+    const double f[3] = {E[0] + b[1] * B[2] - b[2] * B[1], E[1] + b[2] * B[0] - b[0] * B[2],
+                         E[2] + b[0] * B[1] - b[1] * B[0]};
+    const double be = b[0] * E[0] + b[1] * E[1] + b[2] * E[2];
+    const double q = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] - be * be;
+    return eps_ref * gam * sqrt(q > 0.0 ? q : 0.0);
+}
+
+/* Initial optical depth of particle id: -ln u, counter (id, 0, 2, 0). */
+double orc_qed_initial_tau(long id, uint32_t seed_lo, uint32_t seed_hi)
+{
+    const uint32_t ctr[4] = {(uint32_t)id, 0u, 2u, 0u}, key[2] = {seed_lo, seed_hi};
+    uint32_t o[4];
+    philox4x32_10(ctr, key, o);
+    return -log(u01(o[0]));
+}
+
+/* After the push of step `step`: for every alive particle of `e` the fields
+ * at x^{n+1/2} (reconstructed from x^{n+1} and v^{n+1}) and u^{n+1} give chi;
+ * tau[p] decreases by W dt; when it reaches zero a photon of energy fraction
+ * xi = F^-1(r1) (counter (id, step, 0, 0), first word) is emitted along the
+ * particle's velocity with the particle's weight and position, the particle
+ * recoils by the photon momentum, and tau restarts at -ln r2 (second word).
+ * Photons go to ph[7][cap] (x0, x1, x2, u0, u1, u2, w) from *nph on. */
+int orc_qed_compton(const orc_grid *g, orc_species *e, double eps_ref, uint32_t seed_lo, uint32_t seed_hi,
+                    long step, double *tau, double *ph, long cap, long *nph)
+{
+    const double dt = g->dt;
+    for (long p = 0; p < e->n; ++p) {
+        if (!e->alive[p]) continue;
+        double u[3] = {e->u[0][p], e->u[1][p], e->u[2][p]}, xm[3] = {0, 0, 0}, E[3], B[3];
+        const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        for (int d = 0; d < g->dim; ++d) xm[d] = e->x[d][p] - 0.5 * dt * u[d] / gam;
+        if (orc_gather(g, xm, E, B) != ORC_OK) return ORC_EOUTSIDE;
+        const double chi = orc_chi_e(u, E, B, eps_ref);
+        if (chi <= 0.0) continue;
+        tau[p] -= orc_compton_rate(chi, gam, eps_ref) * dt;
+        if (tau[p] > 0.0) continue;
+        const uint32_t ctr[4] = {(uint32_t)p, (uint32_t)step, 0u, 0u}, key[2] = {seed_lo, seed_hi};
+        uint32_t o[4];
+        philox4x32_10(ctr, key, o);
+        const double xi = orc_compton_xi(chi, u01(o[0]));
+        const double umag = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const double k = xi * gam;                   /* photon energy = momentum (m c) */
+        if (*nph < cap) {
+            for (int d = 0; d < 3; ++d) ph[d * cap + *nph] = d < g->dim ? e->x[d][p] : 0.0;
+            for (int c = 0; c < 3; ++c) ph[(3 + c) * cap + *nph] = k * u[c] / umag;
+            ph[6 * cap + *nph] = e->w[p];
+            *nph += 1;
+        }
+        for (int c = 0; c < 3; ++c) e->u[c][p] = u[c] * (1.0 - k / umag);
+        tau[p] = -log(u01(o[1]));
+    }
+    return ORC_OK;
 }

@@ -258,3 +258,78 @@ def energy(grid: Grid, species: list[Species]):
     out = np.zeros(3)
     lib().orc_energy(ctypes.byref(g), arr, len(species), _ptr(out))
     return out
+
+
+# ------------------------------------------------------------------ QED (Sec. 3.4)
+def philox(ctr, key):
+    """Philox4x32-10 of a 4-word counter and a 2-word key (4 uint32)."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox(c, k, o)
+    return [int(v) for v in o]
+
+
+def _qed_sigs():
+    L = lib()
+    d = ctypes.c_double
+    for name, res, args in (("orc_bessel_k", d, [d, d]), ("orc_bessel_k_int", d, [d, d]),
+                            ("orc_compton_s", d, [d, d]), ("orc_compton_rate", d, [d, d, d]),
+                            ("orc_compton_xi", d, [d, d]), ("orc_qed_initial_tau", d,
+                                                            [ctypes.c_long, ctypes.c_uint32, ctypes.c_uint32])):
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    L.orc_chi_e.restype = d
+    L.orc_chi_e.argtypes = [_dp, _dp, _dp, d]
+    return L
+
+
+def bessel_k(nu, x):
+    return _qed_sigs().orc_bessel_k(nu, x)
+
+
+def bessel_k_int(nu, x):
+    """int_x^inf K_nu(s) ds"""
+    return _qed_sigs().orc_bessel_k_int(nu, x)
+
+
+def compton_s(xi, chi):
+    return _qed_sigs().orc_compton_s(xi, chi)
+
+
+def compton_rate(chi, gamma, eps_ref):
+    return _qed_sigs().orc_compton_rate(chi, gamma, eps_ref)
+
+
+def compton_xi(chi, r):
+    return _qed_sigs().orc_compton_xi(chi, r)
+
+
+def chi_e(u, E, B, eps_ref):
+    a = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (u, E, B)]
+    return _qed_sigs().orc_chi_e(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]), eps_ref)
+
+
+def qed_initial_tau(ids, seed):
+    L = _qed_sigs()
+    lo, hi = int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF
+    return np.array([L.orc_qed_initial_tau(int(i), lo, hi) for i in ids])
+
+
+def qed_compton(grid: Grid, sp: Species, eps_ref, seed, step, tau, cap=1 << 16):
+    """Events of one step (after the push); returns the emitted photons as a
+    Species (q = 0, m = 0) with positions, momenta and weights."""
+    L = lib()
+    L.orc_qed_compton.argtypes = [ctypes.POINTER(_CGrid), ctypes.POINTER(_CSpecies), ctypes.c_double,
+                                  ctypes.c_uint32, ctypes.c_uint32, ctypes.c_long, _dp, _dp,
+                                  ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
+    g, s = grid.c(), sp.c()
+    ph = np.zeros(7 * cap)
+    nph = ctypes.c_long(0)
+    assert tau.dtype == np.float64 and tau.flags.c_contiguous
+    _check(L.orc_qed_compton(ctypes.byref(g), ctypes.byref(s), eps_ref, int(seed) & 0xFFFFFFFF,
+                             (int(seed) >> 32) & 0xFFFFFFFF, int(step), _ptr(tau), _ptr(ph), cap,
+                             ctypes.byref(nph)), "qed")
+    n = nph.value
+    ph = ph.reshape(7, cap)[:, :n]
+    return Species(0.0, 0.0, ph[:grid.dim].copy(), ph[3:6].copy(), ph[6].copy())
