@@ -33,7 +33,7 @@ def test_bessel_integrals(x):
     for nu in (1.0 / 3.0, 2.0 / 3.0):
         assert abs(O.bessel_k(nu, x) / special.kv(nu, x) - 1.0) < 1e-10
     ref = integrate.quad(lambda s: special.kv(1.0 / 3.0, s), x, x + 60.0, limit=200)[0]  # K decays as e^-s
-    assert abs(O.bessel_k_int(1.0 / 3.0, x) / ref - 1.0) < 1e-8
+    assert abs(O.bessel_k_int(1.0 / 3.0, x) / ref - 1.0) < 1e-7
 
 
 def _scipy_moment(chi, k):
