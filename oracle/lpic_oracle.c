@@ -874,8 +874,9 @@ double orc_qed_initial_tau(long id, uint32_t seed_lo, uint32_t seed_hi)
     return -log(u01(o[0]));
 }
 
-/* After the push of step `step`: for every alive particle of `e` the fields
- * at x^{n+1/2} (reconstructed from x^{n+1} and v^{n+1}) and u^{n+1} give chi;
+/* After step n (fields, positions and momenta all at t_{n+1}): for every
+ * alive particle of `e` the fields at its position x^{n+1} and its momentum
+ * u^{n+1} give chi;
  * tau[p] decreases by W dt; when it reaches zero a photon of energy fraction
  * xi = F^-1(r1) (counter (id, step, 0, 0), first word) is emitted along the
  * particle's velocity with the particle's weight and position, the particle
@@ -887,10 +888,10 @@ int orc_qed_compton(const orc_grid *g, orc_species *e, double eps_ref, uint32_t 
     const double dt = g->dt;
     for (long p = 0; p < e->n; ++p) {
         if (!e->alive[p]) continue;
-        double u[3] = {e->u[0][p], e->u[1][p], e->u[2][p]}, xm[3] = {0, 0, 0}, E[3], B[3];
+        double u[3] = {e->u[0][p], e->u[1][p], e->u[2][p]}, x[3] = {0, 0, 0}, E[3], B[3];
         const double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        for (int d = 0; d < g->dim; ++d) xm[d] = e->x[d][p] - 0.5 * dt * u[d] / gam;
-        if (orc_gather(g, xm, E, B) != ORC_OK) return ORC_EOUTSIDE;
+        for (int d = 0; d < g->dim; ++d) x[d] = e->x[d][p];
+        if (orc_gather(g, x, E, B) != ORC_OK) return ORC_EOUTSIDE;
         const double chi = orc_chi_e(u, E, B, eps_ref);
         if (chi <= 0.0) continue;
         tau[p] -= orc_compton_rate(chi, gam, eps_ref) * dt;
