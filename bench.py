@@ -152,12 +152,18 @@ def reduce_over_ranks(elapsed, psteps, device):
     return float(mx[0]), float(sm[0])
 
 
+# the files that define the fused tile kernel k_gpd32 (its code, not its host launcher)
+GPD32_SOURCES = ("lpic_common.cuh", "lpic_fp32.cuh", "lpic_gpd32.h", "lpic_gpd32_impl.cuh",
+                 "lpic_gpd32_21.cu", "lpic_gpd32_22.cu", "lpic_gpd32_31.cu", "lpic_gpd32_32.cu")
+
+
 def kernel_source_hash():
+    """Hash of the fused kernel's source files: the ncu traffic record is
+    valid only for the kernel it was taken on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2607_13507_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in GPD32_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 

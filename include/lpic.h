@@ -129,7 +129,10 @@ typedef struct {
 } lpic_grid_desc;
 
 typedef struct {
-    double q, m;                /* charge (|e| units, signed) and mass (m_e units) */
+    double q, m;                /* charge (|e| units, signed) and mass (m_e units); m = 0 with
+                                   q = 0 is a massless species (photons; FP32_FIXED path): it
+                                   moves at c along u, sees no field, deposits nothing, and its
+                                   energy in lpic_diagnostics is w |u| */
     long long count;            /* particles in buffers[0] at add time (first count entries) */
     long long capacity;         /* entries per array, multiple of 64, >= count */
     void *buffers[2];           /* two device buffers of lpic_species_bytes() bytes */
@@ -343,6 +346,59 @@ lpic_status lpic_sort_tiles_static(int dim, int nx, int ny, int nz, const int ti
                                    const void *src, void *dst, long long capacity,
                                    const int *count_in, int *count_out, int *tile_start,
                                    cudaStream_t stream);
+
+/* Nonlinear Compton emission (Sec. 3.4: the nonlinear Compton module emits
+ * photons from energetic electrons in strong fields; Sec. 2.1: particle
+ * attributes such as chi and the optical depth tau).  FP32_FIXED path only.
+ * Locally-constant-field approximation in normalised units (momenta in m c,
+ * fields in m c omega / e for the unit frequency omega, time in 1/omega),
+ * eps_ref = hbar omega / (m c^2):
+ *   chi = eps_ref gamma sqrt((E + beta x B)^2 - (beta . E)^2),
+ *   dW/dxi = alpha / (eps_ref sqrt(3) pi gamma) S(xi, chi),
+ *   S = (1 - xi + 1/(1 - xi)) K_{2/3}(delta) - int_delta^inf K_{1/3},
+ *   delta = 2 xi / (3 chi (1 - xi)),  W = int_0^1 dW/dxi.
+ * Event Monte Carlo: each particle has an optical depth tau[id] (a caller-owned
+ * device float array indexed by the particle id).  Per call tau decreases by
+ * W dt with chi from the grid's fields gathered (the grid's shape order) at
+ * x - (dt/2) v, the particle's position at the time of its momentum; when it
+ * reaches 0 a photon with momentum xi gamma u/|u| is created at the
+ * particle's stored position with its weight, the particle's momentum
+ * becomes u (1 - xi gamma / |u|) and tau restarts at -ln r2.  xi solves
+ * P(xi; chi) = r1 with P the normalised cumulative of S.  Random numbers:
+ * Philox4x32-10 with counter (id, step, 0, 0) (r1 from word 0, r2 from word 1)
+ * and key (seed low 32 bits, seed high 32 bits); r = (x + 1/2) 2^-32.
+ * The rate and the spectrum come from tables built at lpic_qed_init over
+ * chi in [1e-4, 1e3] (32 rows a decade, the cumulative of S on 513 nodes
+ * per row); below 1e-4 the classical limit (W and xi proportional to chi),
+ * above 1e3 the rate is extrapolated in log-log and the spectrum is that of
+ * chi = 1e3.  Accuracy against the defining integrals: rate ~1e-4 relative,
+ * xi ~2e-4 relative (FP32 table lookups). */
+
+/* Build the tables (on the host, about a second, once per grid), and set
+ * eps_ref and the seed.  Synchronises `stream`. */
+lpic_status lpic_qed_init(lpic_grid_t grid, double eps_ref, uint64_t seed, cudaStream_t stream);
+
+/* tau[id] = -ln r for id in [0, n_ids), r from counter (id, 0, 2, 0). */
+lpic_status lpic_qed_initial_tau(lpic_grid_t grid, float *tau, long long n_ids, cudaStream_t stream);
+
+/* One emission pass over species `electron_species` (any massive species),
+ * normally right after lpic_step (the grid's fields at call time are used).
+ * Photons are appended to `photon_species` (a species added with m = 0 and
+ * q = 0), which gets new particle ids count, count + 1, ... (count = its
+ * particles at add time) in an unspecified order.  A particle id outside
+ * [0, n_ids), or more photons than the photon species' capacity (the extra
+ * photons are dropped, the momentum loss is still applied), sets
+ * LPIC_ST_OVERFLOW; a gather past an absorbing edge sets LPIC_ST_OUTSIDE and
+ * skips the particle.  step is the counter word (0 <= step < 2^32).
+ * Asynchronous. */
+lpic_status lpic_qed_compton(lpic_grid_t grid, int electron_species, int photon_species, float *tau,
+                             long long n_ids, long long step, cudaStream_t stream);
+
+/* The table lookups for n given (chi, r) pairs (device arrays): h = int_0^1 S
+ * dxi at chi (W = alpha h / (eps_ref sqrt(3) pi gamma)) and xi(chi, r).
+ * Asynchronous. */
+lpic_status lpic_qed_eval(lpic_grid_t grid, const double *chi, const double *r, long long n, double *h,
+                          double *xi, cudaStream_t stream);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char *lpic_last_error(void);

@@ -18,6 +18,7 @@
 #include "lpic_fp32.cuh"
 #include "lpic_fp64.cuh"
 #include "lpic_gpd32.h"
+#include "lpic_qed.cuh"
 #include "lpic_sort.cuh"
 
 using namespace lpic;
@@ -72,6 +73,7 @@ struct Species {
     bool sorted = false;         // sorted at least once
     int since_sort = 1 << 30;    // pushes since the last sort
     bool counts_fresh = false;   // d_count holds the histogram of the current cells
+    bool massless = false;       // m = 0, q = 0: moves at c along u, no fields, no current
 };
 
 }  // namespace
@@ -117,6 +119,12 @@ struct lpic_grid {
     std::vector<cudaEvent_t> ev;               // pairs (start, stop)
     size_t ev_used = 0;
     bool attrs_set = false;
+    // nonlinear Compton emission (lpic_qed_init)
+    bool qed = false;
+    double eps_ref = 0;
+    uint32_t seed[2] = {0, 0};
+    QedTab qtab{};
+    float* d_qtab = nullptr;                   // logh | top | cdf
 };
 
 namespace {
@@ -624,6 +632,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     cudaFree(g->d_status); cudaFree(g->d_acc); cudaFree(g->d_cnt); cudaFree(g->d_mur); cudaFree(g->d_lprof);
     cudaFree(g->d_psi); cudaFree(g->d_pcoef);
     cudaFree(g->d_clock);
+    cudaFree(g->d_qtab);
     delete g;
     return LPIC_OK;
 }
@@ -645,7 +654,11 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
     if (!desc || !sid) return fail(LPIC_EINVAL, "NULL descriptor or output");
     if (g->started) return fail(LPIC_EUNSUPPORTED, "species must be added before the first push");
     const lpic_species_desc& d = *desc;
-    if (!(d.m > 0) || !std::isfinite(d.q)) return fail(LPIC_EINVAL, "mass must be positive, charge finite");
+    const bool massless = d.m == 0.0 && d.q == 0.0;
+    if (!(d.m > 0 || massless) || !std::isfinite(d.m) || !std::isfinite(d.q))
+        return fail(LPIC_EINVAL, "mass must be positive (or zero with zero charge), charge finite");
+    if (massless && g->d.precision != LPIC_FP32_FIXED)
+        return fail(LPIC_EUNSUPPORTED, "massless species need the FP32 path");
     if (d.capacity <= 0 || d.capacity % 64 != 0 || d.capacity >= (1LL << 31))
         return fail(LPIC_EINVAL, "capacity %lld must be a positive multiple of 64 below 2^31", d.capacity);
     if (d.count < 0 || d.count > d.capacity) return fail(LPIC_EINVAL, "count %lld outside [0, capacity]", d.count);
@@ -654,7 +667,7 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
     if (!aligned(d.buffers[0], 256) || !aligned(d.buffers[1], 256))
         return fail(LPIC_EINVAL, "particle buffers must be 256-byte aligned");
     Species s;
-    s.q = d.q; s.m = d.m; s.cap = d.capacity; s.count0 = d.count;
+    s.q = d.q; s.m = d.m; s.cap = d.capacity; s.count0 = d.count; s.massless = massless;
     s.buf[0] = d.buffers[0]; s.buf[1] = d.buffers[1];
     const int nt = (int)g->ntiles;
     s.item_cap = nt + (d.capacity + g->P - 1) / g->P + 1;
@@ -672,8 +685,9 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
         cudaFree(s.d_esc); cudaFree(s.d_nesc);
         return fail(LPIC_ENOMEM, "species scratch allocation failed");
     }
-    const int n = (int)d.count;
-    LPIC_CUDA(cudaMemcpyAsync(s.d_n, &n, sizeof(int), cudaMemcpyHostToDevice, st));
+    // d_n[0]: particles; d_n[1]: id of the next particle created on the device
+    const int n2[2] = {(int)d.count, (int)d.count};
+    LPIC_CUDA(cudaMemcpyAsync(s.d_n, n2, sizeof(n2), cudaMemcpyHostToDevice, st));
     // largest |w|, for the fixed-point bound
     if (g->d.precision == LPIC_FP32_FIXED) {
         const P32 p = view32(g, s, 0);
@@ -706,8 +720,13 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
             const P32 p = view32(g, s, 0);
             const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
                         c = (float)(g->d.dt / g->d.dz);
-            if (g->d.dim == 3) k_advance32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
-            else               k_advance32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+            if (massless) {
+                if (g->d.dim == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+                else               k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+            } else {
+                if (g->d.dim == 3) k_advance32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+                else               k_advance32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+            }
         } else {
             const P64 p = view64(g, s, 0);
             if (g->d.dim == 3) k_advance64<3><<<nb, 256, 0, st>>>(g->geo, p, 0.5);
@@ -754,6 +773,22 @@ static lpic_status gpd_impl(lpic_grid_t g, int sid, cudaStream_t st, bool count_
     g->started = true;
     const int D = g->d.dim, O = g->d.shape_order;
     lpic_status r;
+    if (s.massless) {
+        // ballistic push over [0, n): needs no tile order and no fields
+        const bool timed = g->timing && g->ev_used + 2 <= g->ev.size();
+        if (timed) LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used], st));
+        const P32 p = view32(g, s, s.cur);
+        const int nb = grid_blocks(s.cap, g->nsm, 16);
+        const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
+                    c = (float)(g->d.dt / (D == 3 ? g->d.dz : 1.0));
+        if (D == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c);
+        else        k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c);
+        LPIC_LAUNCHED("k_photon32");
+        if (timed) { LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used + 1], st)); g->ev_used += 2; }
+        s.since_sort += 1;
+        s.counts_fresh = false;
+        return LPIC_OK;
+    }
     if (g->d.precision == LPIC_FP32_FIXED) {
         if (!s.sorted || s.since_sort >= g->K)
             return fail(LPIC_EINVAL, "species %d must be sorted by tile at least every %d pushes", sid, g->K);
@@ -782,6 +817,7 @@ lpic_status lpic_gather_push_deposit(lpic_grid_t g, int sid, cudaStream_t st) {
 lpic_status lpic_gather_fields(lpic_grid_t g, int sid, float* fields, cudaStream_t st) {
     if (lpic_status r = check_species(g, sid)) return r;
     if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "the unfused stages need the FP32 path");
+    if (g->sp[sid].massless) return fail(LPIC_EUNSUPPORTED, "a massless species has no field stages");
     if (!fields) return fail(LPIC_EINVAL, "fields is NULL");
     Species& s = g->sp[sid];
     g->started = true;
@@ -801,6 +837,7 @@ lpic_status lpic_gather_fields(lpic_grid_t g, int sid, float* fields, cudaStream
 lpic_status lpic_push_deposit_fields(lpic_grid_t g, int sid, const float* fields, cudaStream_t st) {
     if (lpic_status r = check_species(g, sid)) return r;
     if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "the unfused stages need the FP32 path");
+    if (g->sp[sid].massless) return fail(LPIC_EUNSUPPORTED, "a massless species has no field stages");
     if (!fields) return fail(LPIC_EINVAL, "fields is NULL");
     Species& s = g->sp[sid];
     if (s.gather_gen != s.sort_gen || s.since_sort != 0)
@@ -955,7 +992,7 @@ lpic_status lpic_graph_steps(lpic_grid_t g, int nsteps, cudaStream_t st) {
             for (auto& s : g->sp) {
                 if (!s.sorted || s.since_sort >= g->K) { s.cur = 1 - s.cur; s.sorted = true; s.since_sort = 0; s.sort_gen += 1; }
                 s.since_sort += 1;
-                s.counts_fresh = s.since_sort >= g->K;
+                s.counts_fresh = s.since_sort >= g->K && !s.massless;
             }
         g->started = true;
     }
@@ -1004,8 +1041,8 @@ lpic_status lpic_positions_at_step(lpic_grid_t g, int sid, double* out, cudaStre
     const int nb = grid_blocks(s.cap, g->nsm, 16);
     if (g->d.precision == LPIC_FP32_FIXED) {
         const P32 p = view32(g, s, s.cur);
-        if (g->d.dim == 3) k_positions32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, out, s.cap);
-        else               k_positions32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, out, s.cap);
+        if (g->d.dim == 3) k_positions32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, out, s.cap, s.massless);
+        else               k_positions32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, out, s.cap, s.massless);
     } else {
         const P64 p = view64(g, s, s.cur);
         if (g->d.dim == 3) k_positions64<3><<<nb, 256, 0, st>>>(g->geo, p, out, s.cap);
@@ -1389,6 +1426,101 @@ lpic_status lpic_ensemble_check_status(lpic_ensemble_t e, cudaStream_t st, unsig
 lpic_status lpic_ensemble_launches(lpic_ensemble_t e, long long* launches) {
     if (!e || !launches) return fail(LPIC_EINVAL, "NULL argument");
     *launches = e->launches;
+    return LPIC_OK;
+}
+
+
+// ------------------------------------------------- nonlinear Compton (Sec. 3.4)
+lpic_status lpic_qed_init(lpic_grid_t g, double eps_ref, uint64_t seed, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "QED events need the FP32 path");
+    if (!(eps_ref > 0) || !std::isfinite(eps_ref)) return fail(LPIC_EINVAL, "eps_ref must be positive");
+    if (!g->d_qtab) {
+        const QedHostTables H = qed_build_tables(1e-4, 1e3, 32, 513);
+        const size_t n = H.logh.size() + H.top.size() + H.cdf.size();
+        float* d = nullptr;
+        if (cudaMalloc(&d, n * sizeof(float)) != cudaSuccess) return fail(LPIC_ENOMEM, "QED table allocation failed");
+        g->d_qtab = d;
+        LPIC_CUDA(cudaMemcpyAsync(d, H.logh.data(), H.logh.size() * 4, cudaMemcpyHostToDevice, st));
+        LPIC_CUDA(cudaMemcpyAsync(d + H.nchi, H.top.data(), H.top.size() * 4, cudaMemcpyHostToDevice, st));
+        LPIC_CUDA(cudaMemcpyAsync(d + 2 * H.nchi, H.cdf.data(), H.cdf.size() * 4, cudaMemcpyHostToDevice, st));
+        LPIC_CUDA(cudaStreamSynchronize(st));
+        QedTab& T = g->qtab;
+        T.logh = d; T.top = d + H.nchi; T.cdf = d + 2 * H.nchi;
+        T.nchi = H.nchi; T.ny = H.ny;
+        T.lchi0 = (float)H.lchi0; T.inv_dl = (float)(1.0 / H.dl); T.chi0 = (float)std::exp(H.lchi0);
+    }
+    const double alpha = 1.0 / 137.035999084;
+    g->qtab.pref = (float)(alpha / (eps_ref * std::sqrt(3.0) * M_PI));
+    g->qtab.eps_ref = (float)eps_ref;
+    g->eps_ref = eps_ref;
+    g->seed[0] = (uint32_t)(seed & 0xffffffffu);
+    g->seed[1] = (uint32_t)(seed >> 32);
+    g->qed = true;
+    return LPIC_OK;
+}
+
+lpic_status lpic_qed_initial_tau(lpic_grid_t g, float* tau, long long n_ids, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
+    if (n_ids < 0 || (n_ids > 0 && !tau)) return fail(LPIC_EINVAL, "tau is NULL or n_ids negative");
+    if (n_ids == 0) return LPIC_OK;
+    k_qed_tau0<<<grid_blocks(n_ids, g->nsm), 256, 0, st>>>(tau, n_ids, g->seed[0], g->seed[1]);
+    LPIC_LAUNCHED("k_qed_tau0");
+    return LPIC_OK;
+}
+
+lpic_status lpic_qed_compton(lpic_grid_t g, int sid_e, int sid_ph, float* tau, long long n_ids, long long step,
+                             cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid_e)) return r;
+    if (lpic_status r = check_species(g, sid_ph)) return r;
+    if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
+    if (sid_e == sid_ph) return fail(LPIC_EINVAL, "the emitting and the photon species must differ");
+    Species& e = g->sp[sid_e];
+    Species& ph = g->sp[sid_ph];
+    if (e.massless) return fail(LPIC_EINVAL, "species %d is massless and cannot emit", sid_e);
+    if (!ph.massless) return fail(LPIC_EINVAL, "species %d must be massless and charge-free", sid_ph);
+    if (n_ids < 0 || (n_ids > 0 && !tau)) return fail(LPIC_EINVAL, "tau is NULL or n_ids negative");
+    if (step < 0 || step > 0xffffffffLL) return fail(LPIC_EINVAL, "step must fit 32 bits");
+    QedArgs A{};
+    A.g = g->geo;
+    A.E = ptr3<const float>(g->d.E);
+    A.B = ptr3<const float>(g->d.B);
+    A.e = view32(g, e, e.cur);
+    A.ph = view32(g, ph, ph.cur);
+    A.ph_n = ph.d_n;
+    A.ph_next_id = ph.d_n + 1;
+    A.ph_cap = ph.cap;
+    A.dec = g->dec;
+    A.T = g->qtab;
+    A.tau = tau;
+    A.n_ids = n_ids;
+    A.dt = (float)g->d.dt;
+    A.dth0 = (float)(g->d.dt / g->d.dx);
+    A.dth1 = (float)(g->d.dt / g->d.dy);
+    A.dth2 = (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0));
+    A.k0 = g->seed[0]; A.k1 = g->seed[1];
+    A.step = (uint32_t)step;
+    A.st = g->d_status;
+    const int nb = grid_blocks(e.cap, g->nsm, 16);
+    const int D = g->d.dim, O = g->d.shape_order;
+    if (D == 2) { if (O == 1) k_qed_compton32<2, 1><<<nb, 256, 0, st>>>(A); else k_qed_compton32<2, 2><<<nb, 256, 0, st>>>(A); }
+    else        { if (O == 1) k_qed_compton32<3, 1><<<nb, 256, 0, st>>>(A); else k_qed_compton32<3, 2><<<nb, 256, 0, st>>>(A); }
+    LPIC_LAUNCHED("k_qed_compton32");
+    k_qed_clamp<<<1, 32, 0, st>>>(ph.d_n, ph.cap);
+    LPIC_LAUNCHED("k_qed_clamp");
+    ph.counts_fresh = false;
+    return LPIC_OK;
+}
+
+lpic_status lpic_qed_eval(lpic_grid_t g, const double* chi, const double* r, long long n, double* h, double* xi,
+                          cudaStream_t st) {
+    if (lpic_status rr = check_grid(g)) return rr;
+    if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
+    if (n < 0 || (n > 0 && (!chi || !r || !h || !xi))) return fail(LPIC_EINVAL, "NULL array or negative n");
+    if (n == 0) return LPIC_OK;
+    k_qed_eval<<<grid_blocks(n, g->nsm), 256, 0, st>>>(g->qtab, chi, r, n, h, xi);
+    LPIC_LAUNCHED("k_qed_eval");
     return LPIC_OK;
 }
 

@@ -29,7 +29,9 @@ __global__ void k_diag_p32(P32 p, double q, double m, double* acc, unsigned long
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (p.cell[i] < 0) continue;
         const double ux = p.u[0][i], uy = p.u[1][i], uz = p.u[2][i], w = p.w[i];
-        ek += w * m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
+        // a massless particle carries energy |u| (m c^2 units of the unit mass)
+        ek += m == 0.0 ? w * sqrt(ux * ux + uy * uy + uz * uz)
+                       : w * m * (sqrt(1.0 + ux * ux + uy * uy + uz * uz) - 1.0);
         qt += q * w;
         ++c;
     }
@@ -93,7 +95,7 @@ __global__ void k_charge64(Geo g, P64 p, double q, double* rho) {
 
 // x^n = x^{n+1/2} - (dt/2) v^n, as physical doubles out[d * cap + i].
 template <int DIM>
-__global__ void k_positions32(Geo g, P32 p, CellDecode dec, double* out, long long cap) {
+__global__ void k_positions32(Geo g, P32 p, CellDecode dec, double* out, long long cap, bool massless) {
     const int n = *p.n;
     const double h[3] = {g.dx, g.dy, g.dz};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < (int)cap; i += gridDim.x * blockDim.x) {
@@ -106,7 +108,9 @@ __global__ void k_positions32(Geo g, P32 p, CellDecode dec, double* out, long lo
         int gc[3];
         dec(cell, gc);
         const double ux = p.u[0][i], uy = p.u[1][i], uz = p.u[2][i];
-        const double gm = sqrt(1.0 + ux * ux + uy * uy + uz * uz);
+        // gamma for a massive particle, |u| for a massless one (v = u / |u|)
+        const double um2 = ux * ux + uy * uy + uz * uz;
+        const double gm = massless ? (um2 > 0.0 ? sqrt(um2) : 1.0) : sqrt(1.0 + um2);
         const double u[3] = {ux, uy, uz};
 #pragma unroll
         for (int d = 0; d < DIM; ++d)

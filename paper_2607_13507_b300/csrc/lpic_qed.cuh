@@ -1,0 +1,336 @@
+// Nonlinear Compton emission (Sec. 3.4) on the FP32 path, and the ballistic
+// push of massless, charge-free species (the emitted photons).
+//
+// Physics (locally-constant-field approximation, normalised units: momenta
+// in m c, fields in m c omega_ref / e, eps_ref = hbar omega_ref / (m c^2)):
+//   chi_e = eps_ref gamma sqrt((E + beta x B)^2 - (beta . E)^2),
+//   dW / dxi = alpha / (eps_ref sqrt(3) pi gamma) S(xi, chi),
+//   S = (1 - xi + 1 / (1 - xi)) K_{2/3}(delta) - int_delta^inf K_{1/3},
+//   delta = 2 xi / (3 chi (1 - xi)),
+// W = int_0^1 dW/dxi.  Each particle carries an optical depth tau (indexed by
+// its id); per step tau decreases by W dt and when it reaches zero a photon of
+// energy fraction xi (drawn from the normalised cumulative of S) is emitted
+// along the particle's momentum, the particle recoils and tau restarts at
+// -ln r.  Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
+// counter (id, step, kind, 0), key (seed_lo, seed_hi).
+//
+// Tables (built on the host at lpic_qed_init, read from global memory, where
+// they stay L2-resident):
+//   logh[i]  = ln h(chi_i), h(chi) = int_0^1 S(xi, chi) dxi, chi_i = chi_0 e^{i dl}
+//   cdf[i][j] = normalised cumulative of S at xi = top_i m_i(y_j), y_j = j/(ny-1),
+//   top_i = min(1, 60 chi_i) (the spectrum is negligible beyond 40 e-folds),
+//   m(y) = y^3 (top < 1) or y^3 (10 - 15 y + 6 y^2) (top = 1, which also
+//   resolves the (1 - xi)^{-1/3} edge of the spectrum at large chi).
+// Below chi_0 the classical limit is used: h and xi are proportional to chi.
+#pragma once
+#include <cmath>
+#include <cstdint>
+#include <vector>
+#include "lpic_fp32.cuh"
+
+namespace lpic {
+
+// ------------------------------------------------------------ Philox4x32-10
+struct U4 { uint32_t x, y, z, w; };
+
+__host__ __device__ inline void mulhilo32(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
+    const uint64_t p = (uint64_t)a * (uint64_t)b;
+    hi = (uint32_t)(p >> 32);
+    lo = (uint32_t)p;
+}
+
+// Ten rounds of the Philox-4x32 bijection (multipliers 0xD2511F53 and
+// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85).
+__host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        uint32_t h0, l0, h1, l1;
+        mulhilo32(0xD2511F53u, c.x, h0, l0);
+        mulhilo32(0xCD9E8D57u, c.z, h1, l1);
+        c = U4{h1 ^ c.y ^ k0, l1, h0 ^ c.w ^ k1, l0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// uniform in (0, 1) from 32 bits: (x + 1/2) 2^-32
+__device__ inline double u01d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+
+// --------------------------------------------------------------- the tables
+struct QedTab {
+    const float* logh;     // [nchi]
+    const float* cdf;      // [nchi][ny]
+    const float* top;      // [nchi]
+    int nchi, ny;
+    float lchi0, inv_dl;   // ln chi_0, 1 / dl
+    float chi0;
+    float pref;            // alpha / (eps_ref sqrt(3) pi): W = pref h(chi) / gamma
+    float eps_ref;
+};
+
+// h(chi): piecewise linear in (ln chi, ln h); linear extrapolation in the
+// log-log plane past the last node (h grows like chi^{2/3} there).
+__device__ inline float qed_h(const QedTab& T, float chi) {
+    if (chi <= T.chi0) return __expf(T.logh[0]) * (chi / T.chi0);
+    const float u = (logf(chi) - T.lchi0) * T.inv_dl;
+    const int i = min((int)u, T.nchi - 2);
+    const float f = u - (float)i;
+    return expf(T.logh[i] + f * (T.logh[i + 1] - T.logh[i]));
+}
+
+__device__ inline float qed_map(float y, float top) {
+    const float y3 = y * y * y;
+    return top < 1.0f ? top * y3 : y3 * (10.0f + y * (-15.0f + 6.0f * y));
+}
+
+// xi of cumulative probability r in table row i: bisection for the interval
+// of the cumulative holding r, then xi^{1/3} linear in the probability (the
+// cumulative grows like xi^{1/3} at small xi).
+__device__ inline float qed_row_xi(const QedTab& T, int i, float r) {
+    const float* P = T.cdf + (long long)i * T.ny;
+    int lo = 0, hi = T.ny - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P[mid] <= r) lo = mid; else hi = mid;
+    }
+    const float pa = P[lo], pb = P[hi];
+    const float f = pb > pa ? fminf((r - pa) / (pb - pa), 1.0f) : 0.0f;
+    const float dy = 1.0f / (float)(T.ny - 1);
+    const float za = cbrtf(qed_map((float)lo * dy, T.top[i]));
+    const float zb = cbrtf(qed_map((float)hi * dy, T.top[i]));
+    const float z = za + f * (zb - za);
+    return z * z * z;
+}
+
+// xi(chi, r): rows interpolated in (ln chi, ln xi) (exact in the classical
+// limit, where xi is proportional to chi); clamped to the last row.
+__device__ inline float qed_xi(const QedTab& T, float chi, float r) {
+    if (chi <= T.chi0) return qed_row_xi(T, 0, r) * (chi / T.chi0);
+    float u = (logf(chi) - T.lchi0) * T.inv_dl;
+    u = fminf(u, (float)(T.nchi - 1));
+    const int i = min((int)u, T.nchi - 2);
+    const float f = u - (float)i;
+    const float a = qed_row_xi(T, i, r), b = qed_row_xi(T, i + 1, r);
+    if (!(a > 0.0f) || !(b > 0.0f)) return a + f * (b - a);
+    return expf(logf(a) + f * (logf(b) - logf(a)));
+}
+
+// --------------------------------------------------------------- the kernels
+// Initial optical depths tau[id] = -ln r, r from counter (id, 0, 2, 0).
+__global__ void k_qed_tau0(float* tau, long long n_ids, uint32_t k0, uint32_t k1) {
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n_ids;
+         id += (long long)gridDim.x * blockDim.x) {
+        const U4 o = philox4x32_10(U4{(uint32_t)id, 0u, 2u, 0u}, k0, k1);
+        tau[id] = (float)(-log(u01d(o.x)));
+    }
+}
+
+// Table lookups for given (chi, r): h(chi) and xi(chi, r).
+__global__ void k_qed_eval(QedTab T, const double* chi, const double* r, long long n, double* h,
+                           double* xi) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float c = (float)chi[i];
+        const float rr = fminf((float)r[i], 0.99999994f);
+        h[i] = c > 0.0f ? (double)qed_h(T, c) : 0.0;
+        xi[i] = c > 0.0f ? (double)qed_xi(T, c, rr) : 0.0;
+    }
+}
+
+struct QedArgs {
+    Geo g;
+    Ptr3<const float> E, B;
+    P32 e;                 // emitting species (current buffer)
+    P32 ph;                // photon species (current buffer); ph.n is appended to
+    int* ph_n;             // == ph.n, writable
+    int* ph_next_id;       // id of the next created photon
+    long long ph_cap;
+    CellDecode dec;
+    QedTab T;
+    float* tau;
+    long long n_ids;
+    float dt, dth0, dth1, dth2;
+    uint32_t k0, k1, step;
+    unsigned* st;
+};
+
+// One pass over the emitting species after its push.  The fields are
+// gathered at x - (dt/2) v, the particle's position at the time of its
+// momentum u (the stored position is half a step ahead of it).
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
+    const P32& p = A.e;
+    const int n = *p.n;
+    const float dth[3] = {A.dth0, A.dth1, A.dth2};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int cell = p.cell[i];
+        if (cell < 0) continue;
+        const int id = p.id[i];
+        if (id < 0 || (long long)id >= A.n_ids) { set_status(A.st, LPIC_ST_OVERFLOW); continue; }
+        float u[3] = {p.u[0][i], p.u[1][i], p.u[2][i]};
+        const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const float gam = sqrtf(1.0f + u2);
+        const float ig = 1.0f / gam;
+        int gc[3];
+        A.dec(cell, gc);
+        if (DIM == 2) gc[2] = 0;
+        float f[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            float fd = p.off[d][i] - 0.5f * dth[d] * u[d] * ig;
+            if (fd < 0.0f) { fd += 1.0f; gc[d] -= 1; if (fd >= 1.0f) fd = 0.99999994f; }
+            else if (fd >= 1.0f) { fd -= 1.0f; gc[d] += 1; }
+            f[d] = fd;
+        }
+        const int lc[3] = {2, 2, DIM == 3 ? 2 : 0};
+        const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
+        const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
+        float fld[6];
+        bool outside = false;
+        const LoadGlobal<DIM> ld{&A.g, {A.E.p[0], A.E.p[1], A.E.p[2], A.B.p[0], A.B.p[1], A.B.p[2]},
+                                 {gc[0], gc[1], gc[2]}, &outside};
+        gather32<DIM, ORDER>(ld, nx_, ny_, nz_, hx_, hy_, hz_, fld);
+        if (outside) { set_status(A.st, LPIC_ST_OUTSIDE); continue; }
+        const float b0 = u[0] * ig, b1 = u[1] * ig, b2 = u[2] * ig;
+        const float F0 = fld[0] + b1 * fld[5] - b2 * fld[4];
+        const float F1 = fld[1] + b2 * fld[3] - b0 * fld[5];
+        const float F2 = fld[2] + b0 * fld[4] - b1 * fld[3];
+        const float be = b0 * fld[0] + b1 * fld[1] + b2 * fld[2];
+        const float q2 = F0 * F0 + F1 * F1 + F2 * F2 - be * be;
+        const float chi = A.T.eps_ref * gam * sqrtf(fmaxf(q2, 0.0f));
+        if (!(chi > 0.0f)) continue;
+        float t = A.tau[id] - A.T.pref * qed_h(A.T, chi) * ig * A.dt;
+        if (t > 0.0f) { A.tau[id] = t; continue; }
+        // emission: xi from the first word, the new depth from the second
+        const U4 o = philox4x32_10(U4{(uint32_t)id, A.step, 0u, 0u}, A.k0, A.k1);
+        const float r1 = fminf((float)u01d(o.x), 0.99999994f);
+        const float xi = qed_xi(A.T, chi, r1);
+        const float umag = sqrtf(u2);
+        const float k = xi * gam;
+        const int j = atomicAdd(A.ph_n, 1);
+        if ((long long)j < A.ph_cap) {
+            const float s = k / umag;
+            A.ph.cell[j] = cell;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) A.ph.off[d][j] = p.off[d][i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A.ph.u[c][j] = s * u[c];
+            A.ph.w[j] = p.w[i];
+            A.ph.id[j] = atomicAdd(A.ph_next_id, 1);
+        } else {
+            set_status(A.st, LPIC_ST_OVERFLOW);
+        }
+        const float keep = 1.0f - k / umag;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p.u[c][i] = u[c] * keep;
+        A.tau[id] = (float)(-log(u01d(o.y)));
+    }
+}
+
+// After the emission pass: a photon count past the capacity is cut back.
+__global__ void k_qed_clamp(int* n, long long cap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0 && (long long)*n > cap) *n = (int)cap;
+}
+
+// Massless particles move at c along u: offsets advance by frac dt u / (|u| h)
+// with carries into the cell (at most one per dimension under the Courant
+// limit); they leave the grid through absorbing x edges.
+template <int DIM>
+__global__ void k_photon32(Geo g, P32 p, CellDecode dec, float frac, float dth0, float dth1, float dth2) {
+    const int n = *p.n;
+    const float dth[3] = {dth0, dth1, dth2};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int cell = p.cell[i];
+        if (cell < 0) continue;
+        int gc[3];
+        dec(cell, gc);
+        const float uu[3] = {p.u[0][i], p.u[1][i], p.u[2][i]};
+        const float um = sqrtf(uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+        const float iu = um > 0.0f ? 1.0f / um : 0.0f;
+        const int nn[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const float fr = p.off[d][i] + frac * uu[d] * iu * dth[d];
+            int carry = (int)floorf(fr);
+            float fn = fr - (float)carry;
+            if (fn >= 1.0f) { fn -= 1.0f; carry += 1; }
+            gc[d] += carry;
+            if (!(d == 0 && g.absorb)) gc[d] = wrapi(gc[d], nn[d]);
+            p.off[d][i] = fn;
+        }
+        if (DIM == 2) gc[2] = 0;
+        p.cell[i] = (gc[0] < 0 || gc[0] >= g.nx) ? -1 : (gc[2] * g.ny + gc[1]) * g.nx + gc[0];
+    }
+}
+
+// ---------------------------------------------------- host: building tables
+// K_nu(x) and int_x^inf K_nu from K_nu(x) = int_0^inf e^{-x cosh t} cosh(nu t) dt
+// (and the same integrand over cosh t for the tail integral).  The integrands
+// are analytic in the strip |Im t| < pi/2 and decay double-exponentially, so
+// the trapezoid rule with step 1/8 is accurate to far below double rounding.
+inline void qed_bessel_pair(double x, double& k23, double& ik13) {
+    const double h = 0.125;
+    const double tmax = std::acosh(std::fmax(1.0, 80.0 / x)) + 1.0;
+    double a = 0.5 * std::exp(-x), b = 0.5 * std::exp(-x);
+    for (int m = 1; m * h <= tmax; ++m) {
+        const double t = m * h, ch = std::cosh(t), e = std::exp(-x * ch);
+        a += e * std::cosh(t * (2.0 / 3.0));
+        b += e * std::cosh(t * (1.0 / 3.0)) / ch;
+    }
+    k23 = a * h;
+    ik13 = b * h;
+}
+
+inline double qed_spectrum(double xi, double chi) {
+    if (!(xi > 0.0) || !(xi < 1.0)) return 0.0;
+    const double delta = 2.0 * xi / (3.0 * chi * (1.0 - xi));
+    if (delta > 700.0) return 0.0;
+    double k23, ik13;
+    qed_bessel_pair(delta, k23, ik13);
+    return (1.0 - xi + 1.0 / (1.0 - xi)) * k23 - ik13;
+}
+
+struct QedHostTables {
+    int nchi = 0, ny = 0;
+    double lchi0 = 0, dl = 0;
+    std::vector<float> logh, cdf, top;
+};
+
+// Rows chi_i = chi_min 10^{i / per_decade} up to chi_max; cumulative by the
+// trapezoid rule over y (the integrand S dxi/dy is finite at y = 0, where its
+// limit is 3 Gamma(2/3) (3 chi)^{2/3} (c top)^{1/3} with xi ~ c top y^3).
+inline QedHostTables qed_build_tables(double chi_min, double chi_max, int per_decade, int ny) {
+    QedHostTables T;
+    T.dl = std::log(10.0) / per_decade;
+    T.lchi0 = std::log(chi_min);
+    T.nchi = (int)std::floor((std::log(chi_max) - T.lchi0) / T.dl + 1e-9) + 1;
+    T.ny = ny;
+    T.logh.resize(T.nchi);
+    T.top.resize(T.nchi);
+    T.cdf.resize((size_t)T.nchi * ny);
+    std::vector<double> g(ny), cum(ny);
+    for (int i = 0; i < T.nchi; ++i) {
+        const double chi = std::exp(T.lchi0 + i * T.dl);
+        const double top = std::fmin(1.0, 60.0 * chi);
+        const bool step = !(top < 1.0);
+        const double c = step ? 10.0 : 1.0;
+        g[0] = 3.0 * std::tgamma(2.0 / 3.0) * std::pow(3.0 * chi, 2.0 / 3.0) * std::cbrt(c * top);
+        for (int j = 1; j < ny; ++j) {
+            const double y = (double)j / (ny - 1);
+            const double m = step ? y * y * y * (10.0 + y * (-15.0 + 6.0 * y)) : y * y * y;
+            const double dm = step ? 30.0 * y * y * (1.0 - y) * (1.0 - y) : 3.0 * y * y;
+            g[j] = (j == ny - 1 && step) ? 0.0 : qed_spectrum(top * m, chi) * top * dm;
+        }
+        cum[0] = 0.0;
+        for (int j = 1; j < ny; ++j) cum[j] = cum[j - 1] + 0.5 * (g[j - 1] + g[j]) / (ny - 1);
+        const double total = cum[ny - 1];
+        T.logh[i] = (float)std::log(total);
+        T.top[i] = (float)top;
+        for (int j = 0; j < ny; ++j) T.cdf[(size_t)i * ny + j] = (float)(cum[j] / total);
+        T.cdf[(size_t)i * ny + ny - 1] = 1.0f;
+    }
+    return T;
+}
+
+}  // namespace lpic

@@ -31,7 +31,8 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_graph_steps", "lpic_sort_tiles_static", "lpic_kernel_timing",
            "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
            "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
-           "lpic_ensemble_launches"]
+           "lpic_ensemble_launches", "lpic_qed_init", "lpic_qed_initial_tau", "lpic_qed_compton",
+           "lpic_qed_eval"]
 
 
 class LpicError(RuntimeError):
@@ -128,6 +129,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_diagnostics.argtypes = [vp, ctypes.POINTER(Diag), st]
     lib.lpic_grid_get_info.argtypes = [vp, ctypes.POINTER(GridInfo)]
     lib.lpic_check_status.argtypes = [vp, st, ctypes.POINTER(ctypes.c_uint)]
+    lib.lpic_qed_init.argtypes = [vp, ctypes.c_double, ctypes.c_uint64, st]
+    lib.lpic_qed_initial_tau.argtypes = [vp, vp, ctypes.c_longlong, st]
+    lib.lpic_qed_compton.argtypes = [vp, i, i, vp, ctypes.c_longlong, ctypes.c_longlong, st]
+    lib.lpic_qed_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
     lib.lpic_last_error.restype = ctypes.c_char_p
     lib.lpic_last_error.argtypes = []
     for name in EXPORTS:
@@ -317,6 +322,46 @@ class Grid:
         sp.upload(p, staggered, stream)
         self.species.append(sp)
         return sp
+
+    def add_empty_species(self, q, m, capacity, stream=None) -> Species:
+        """A species that starts empty (m = 0, q = 0: photons created by qed_compton)."""
+        from .workloads import Particles
+        e = np.zeros((self.dim, 0), np.int32)
+        p = Particles(q=q, m=m, cell=e, off=e.astype(np.float32), u=np.zeros((3, 0), np.float32),
+                      w=np.zeros(0, np.float32), id=np.zeros(0, np.int32))
+        sp = Species(self, q, m, _cap(capacity))
+        sp.upload(p, True, stream)
+        self.species.append(sp)
+        return sp
+
+    # -- nonlinear Compton emission
+    def qed_init(self, eps_ref, seed, stream=None):
+        """Build the emission tables; eps_ref = hbar omega / (m c^2) of the unit frequency."""
+        _check(load().lpic_qed_init(self.h_, float(eps_ref), int(seed) & (2**64 - 1), _stream(stream)))
+
+    def qed_initial_tau(self, n_ids, stream=None) -> torch.Tensor:
+        """Optical depths -ln r for ids 0..n_ids-1 (float32 device tensor)."""
+        tau = torch.empty(max(int(n_ids), 1), dtype=torch.float32, device=self.device)
+        _check(load().lpic_qed_initial_tau(self.h_, tau.data_ptr(), int(n_ids), _stream(stream)))
+        return tau[: int(n_ids)]
+
+    def qed_compton(self, electrons, photons, tau, step, stream=None):
+        """One emission pass of `electrons` into `photons` (Species objects)."""
+        assert tau.dtype == torch.float32 and tau.is_cuda and tau.is_contiguous()
+        _check(load().lpic_qed_compton(self.h_, electrons.id, photons.id, tau.data_ptr(), tau.numel(),
+                                       int(step), _stream(stream)))
+
+    def qed_eval(self, chi, r, stream=None):
+        """Device table lookups: (h(chi), xi(chi, r)) as float64 numpy arrays."""
+        c = torch.as_tensor(np.asarray(chi, np.float64), device=self.device).contiguous()
+        rr = torch.as_tensor(np.asarray(r, np.float64), device=self.device).contiguous()
+        assert c.shape == rr.shape
+        h = torch.empty_like(c)
+        xi = torch.empty_like(c)
+        _check(load().lpic_qed_eval(self.h_, c.data_ptr(), rr.data_ptr(), c.numel(), h.data_ptr(),
+                                    xi.data_ptr(), _stream(stream)))
+        torch.cuda.synchronize(self.device)
+        return h.cpu().numpy(), xi.cpu().numpy()
 
     def info(self) -> GridInfo:
         out = GridInfo()
