@@ -45,10 +45,21 @@ WORKLOADS = {
     "laser3d": ("3D3V laser-target 512x256x256, dx=lambda/32, a0=20 w0=2lambda 8-cycle laser through "
                 "an absorbing x-min edge, e-+p slab 30 n_c at x in [4,6] lambda, 16+16 particles/cell "
                 "(134M), CIC, re-sorted every 10 steps, FP32 push + int64 fixed-point deposit", 400),
+    "qed2d": ("2D3V synchrotron cooling of a pair plasma 1024x1024, dx=lambda/32 (0.8 um), e- and e+ "
+              "at kT=3000 m c^2 (Maxwell-Juttner), 16+16 particles/cell (33.5M), uniform B_z=4, "
+              "nonlinear Compton emission every step (chi ~ 0.1, photons pushed at c), TSC, periodic, "
+              "FP32 push + int64 fixed-point deposit", 0),
     "ensemble": ("96 independent 2D3V periodic plasmas in one ensemble (batched kernels, persistent "
                  "work-queue particle kernel, one CUDA graph per step): sides 128-768, 4-64 "
                  "particles/cell, v_th 0.005-0.1c, CIC, FP32 + fixed point", 0),
 }
+
+
+def metric_name(workload):
+    if workload == "qed2d":
+        return ("particle-steps/s (gather+push+deposit, whole step incl. sort, Maxwell and the "
+                "nonlinear Compton emission passes; photons counted)")
+    return "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)"
 
 
 def make_workload(name, precision, seed_offset=0, ny=None, n3=None, boundary="mur"):
@@ -61,6 +72,8 @@ def make_workload(name, precision, seed_offset=0, ny=None, n3=None, boundary="mu
         wl = W.thermal2d(precision=precision)
     elif name == "heating2d":
         wl = W.heating2d(res=40, ppc=64, precision=precision)
+    elif name == "qed2d":
+        wl = W.qed2d(precision=precision, n=ny or 1024)
     elif name == "laser3d":
         wl = W.laser3d(precision=precision, nx=n3 or 512, ny=(n3 or 512) // 2, nz=(n3 or 512) // 2,
                        boundary=boundary)
@@ -214,6 +227,34 @@ def tuned_choice(args, wl):
         ch.update(sort_interval=args.sort_interval, source="command line")
     return ch
 
+def qed_summary(qed, wl, counts0, counts1, G, peak, which):
+    """The emission pass (k_qed_compton32 over each emitting species, plus a
+    one-thread count clamp) timed with CUDA events on the launching stream.
+    Algorithmic bytes per emitter per step: cell, offsets, u, id and tau read,
+    tau written (8 + 4 dim + 12 B); per photon created: the emitter's weight
+    read, its momentum written and the photon written (48 + 4 dim B); the
+    fields of the grid read once (24 B per cell)."""
+    ms = sum(a.elapsed_time(b) for a, b in qed["events"])
+    n_steps = len(qed["events"])
+    emit_ids = [i for i, sp in enumerate(G.species) if sp.m > 0]
+    ph = G.species.index(qed["photons"])
+    n_emit = sum(0.5 * (counts0[i] + counts1[i]) for i in emit_ids)
+    created = (counts1[ph] - counts0[ph]) / max(1, n_steps)
+    d = wl.dim
+    per_emitter = 8 + 4 * d + 12
+    per_photon = 48 + 4 * d
+    bytes_step = n_emit * per_emitter + created * per_photon + 24 * wl.cells
+    t = ms / 1e3 / max(1, n_steps)
+    achieved = bytes_step / t / 1e9
+    return {"kernel": "k_qed_compton32", "ms_per_step": 1e3 * t,
+            "emitters": int(n_emit), "photons_created_per_step": created,
+            "photons_alive": int(counts1[ph]),
+            "emission_passes_per_step": len(emit_ids),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"{which} hbm_gbs",
+                         "algorithmic_bytes_per_step": bytes_step, "traffic": None}}
+
+
 def run_b300(args, rank, world, local_rank):
     import torch
     from paper_2607_13507_b300 import build, lpic
@@ -235,14 +276,38 @@ def run_b300(args, rank, world, local_rank):
     for p in parts:
         G.add_species(p, stream=stream)
     loaded = [p.n // wl.species[i].ppc for i, p in enumerate(parts)]
+    qed = None
+    if wl.qed_eps_ref > 0:
+        # photons appended by the emission passes; depths indexed by the
+        # (species-unique) particle ids
+        n_ids = sum(p.n for p in parts)
+        phot = G.add_empty_species(0.0, 0.0, n_ids // 2, stream=stream)
+        G.B[2].fill_(wl.b0)
+        G.qed_init(wl.qed_eps_ref, wl.seed, stream)
+        qed = dict(emitters=[sp for sp in G.species if sp.m > 0], photons=phot,
+                   tau=G.qed_initial_tau(n_ids, stream), events=[])
     del parts
     dt = G.dt
     pre = WORKLOADS[args.workload][1] if args.pre_steps is None else args.pre_steps
 
+    def advance(k, timed=False):
+        """One step of the path (and the emission passes of a QED workload)."""
+        G.step(k * dt, stream)
+        if qed is None:
+            return
+        if timed:
+            ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+            ev[0].record(stream)
+        for sp in qed["emitters"]:
+            G.qed_compton(sp, qed["photons"], qed["tau"], k, stream)
+        if timed:
+            ev[1].record(stream)
+            qed["events"].append(ev)
+
     step = 0
     with torch.cuda.stream(stream):
         for _ in range(pre + args.warmup):
-            G.step(step * dt, stream)
+            advance(step)
             step += 1
     stream.synchronize()
     if G.check_status(stream) != 0:
@@ -256,11 +321,13 @@ def run_b300(args, rank, world, local_rank):
     time.sleep(0.3)
     launches0 = G.info().launches
     unfused = bool(getattr(args, "unfused", False))
+    if unfused and qed is not None:
+        raise SystemExit("--unfused does not apply to the QED workload")
     bufs = [torch.empty((6, sp.cap), dtype=torch.float32, device=dev) for sp in G.species] if unfused else []
 
     def one_step(t):
         if not unfused:
-            G.step(t, stream)
+            advance(step, timed=True)
             return
         # the unfused path: gather stage, (hooks would go here), push/deposit stage
         G.maxwell_half(0, t, stream)
@@ -294,10 +361,11 @@ def run_b300(args, rank, world, local_rank):
     G.kernel_timing(0)
     gpd_time = gpd_ms / 1e3
     algo_bytes_step = 0
-    for i, sp in enumerate(G.species):
+    massive = [i for i, sp in enumerate(G.species) if sp.m > 0]      # photons skip the fused kernel
+    for i in massive:
         n_mean = 0.5 * (counts0[i] + counts1[i])
         algo_bytes_step += algorithmic_bytes(wl, n_mean, loaded[i], args.precision)[0]
-    launch_bytes = algo_bytes_step / len(G.species)
+    launch_bytes = algo_bytes_step / len(massive)
     launch_time = gpd_time / max(1, gpd_launches)
     if unfused:
         # a "launch" is the pair of stages; the field array adds 24 B written
@@ -316,7 +384,7 @@ def run_b300(args, rank, world, local_rank):
         achieved = launch_bytes / launch_time / 1e9
         per_ps = algorithmic_bytes(wl, 1, 0, args.precision)[1]
         result = {
-            "metric": "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)",
+            "metric": metric_name(args.workload),
             "value": psteps / elapsed,
             "unit": "particle-steps/s",
             "n_gpus": world,
@@ -354,9 +422,12 @@ def run_b300(args, rank, world, local_rank):
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
+        if qed is not None:
+            result["qed"] = qed_summary(qed, wl, counts0, counts1, G, peak, which)
     if result is not None:
         result["config"]["tuning"] = tuned
-    state = dict(G=G, stream=stream, dev=dev, step=step, counts=counts1, wl=wl)
+    state = dict(G=G, stream=stream, dev=dev, step=step, counts=counts1, wl=wl, advance=advance,
+                 extra=[qed["tau"]] if qed is not None else [])
     return result, state
 
 
@@ -414,7 +485,7 @@ def run_ensemble(args, rank, world, local_rank):
     step_bytes = counts * per_ps + loaded * algorithmic_bytes(wl0, 0, 1, "fp32")[2]
     achieved = step_bytes / (elapsed / args.steps) / 1e9
     return {
-        "metric": "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)",
+        "metric": metric_name(args.workload),
         "value": psteps / elapsed, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (int64 fixed-point current)",
@@ -442,7 +513,7 @@ def run_e2e(args, st):
               for sp in G.species]
     for h, sp, c in zip(host_p, G.species, cur):
         h.copy_(sp.buffers[c])
-    fields = G.E + G.B + G.J
+    fields = G.E + G.B + G.J + st["extra"]
     host_f = [torch.empty(f.shape, dtype=f.dtype, pin_memory=True) for f in fields]
     for h, f in zip(host_f, fields):
         h.copy_(f)
@@ -458,7 +529,7 @@ def run_e2e(args, st):
                 sp.buffers[c].copy_(h, non_blocking=True)
             for h, f in zip(host_f, fields):
                 f.copy_(h, non_blocking=True)
-            G.step(step * dt, stream)
+            st["advance"](step)
             step += 1
             for i, sp in enumerate(G.species):
                 cur[i], n = sp.query(stream)
@@ -483,7 +554,11 @@ def oracle_sample(args, budget_s, max_steps):
     from oracle import oracle as O
     from paper_2607_13507_b300 import workloads as W
     wl = make_workload(args.workload, "fp64", boundary=args.boundary)
-    if wl.dim == 2:
+    if wl.qed_eps_ref > 0:
+        # the oracle's emission rate integrates the spectrum afresh for every
+        # particle (about 0.07 s each): a 4 x 4-cell box
+        sample = dict(n=(4, 4))
+    elif wl.dim == 2:
         sample = dict(n=(wl.n[0], min(16, wl.n[1])))
     elif wl.laser is not None:
         sample = dict(n=(wl.n[0], 8, 8))
@@ -501,15 +576,29 @@ def oracle_sample(args, budget_s, max_steps):
     h = np.array(wl.h)[:, None]
     sps = [O.Species(p.q, p.m, (p.cell + p.off) * h, p.u, p.w) for p in parts]
     npart = sum(p.n for p in parts)
+    tau = None
+    if wl.qed_eps_ref > 0:
+        g.B[2][...] = wl.b0
+        ids = np.concatenate([p.id for p in parts])
+        tau = [O.qed_initial_tau(p.id, wl.seed) for p in parts]
+        assert len(set(ids.tolist())) == len(ids)
+    nemit = len(sps)
     t0 = time.perf_counter()
     steps = 0
+    psteps = 0
     while steps < max_steps and (time.perf_counter() - t0) < budget_s:
+        psteps += sum(int(sp.alive.sum()) for sp in sps)
         O.step(g, sps, steps * wl.dt)
+        if tau is not None:
+            for k in range(nemit):
+                ph = O.qed_compton(g, sps[k], wl.qed_eps_ref, wl.seed, steps, tau[k])
+                if ph.x.shape[1]:
+                    sps.append(ph)
         steps += 1
     el = time.perf_counter() - t0
     desc = (f"{'x'.join(str(v) for v in wl.n)} cells of the workload (same dx, profile, ppc), "
             f"{npart} particles, {steps} steps, FP64 oracle, 1 thread")
-    return npart * steps / el, desc, steps, el
+    return psteps / el, desc, steps, el
 
 
 def run_reference(args, rank, world):
@@ -518,7 +607,7 @@ def run_reference(args, rank, world):
     val, desc, steps, el = oracle_sample(args, budget_s=max(10.0, 0.5 * (args.steps + args.warmup)),
                                          max_steps=args.steps + args.warmup)
     return {
-        "metric": "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)",
+        "metric": metric_name(args.workload),
         "value": val, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
         "warmup": 0, "ms_per_step": 1e3 * el / max(steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -774,9 +774,8 @@ static lpic_status gpd_impl(lpic_grid_t g, int sid, cudaStream_t st, bool count_
     const int D = g->d.dim, O = g->d.shape_order;
     lpic_status r;
     if (s.massless) {
-        // ballistic push over [0, n): needs no tile order and no fields
-        const bool timed = g->timing && g->ev_used + 2 <= g->ev.size();
-        if (timed) LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used], st));
+        // ballistic push over [0, n): needs no tile order and no fields (not
+        // a launch of the fused kernel, so not timed with it)
         const P32 p = view32(g, s, s.cur);
         const int nb = grid_blocks(s.cap, g->nsm, 16);
         const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
@@ -784,7 +783,6 @@ static lpic_status gpd_impl(lpic_grid_t g, int sid, cudaStream_t st, bool count_
         if (D == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c);
         else        k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c);
         LPIC_LAUNCHED("k_photon32");
-        if (timed) { LPIC_CUDA(cudaEventRecord(g->ev[g->ev_used + 1], st)); g->ev_used += 2; }
         s.since_sort += 1;
         s.counts_fresh = false;
         return LPIC_OK;

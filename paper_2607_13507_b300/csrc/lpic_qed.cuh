@@ -155,6 +155,62 @@ struct QedArgs {
     unsigned* st;
 };
 
+// E and B at a particle in cell gc with offsets f, read from global memory
+// (the grid's shape functions, staggering as in the particle push).  The
+// stencil covers nodes gc - 1 .. gc + ORDER of each dimension: their wrapped
+// indices are formed once, and every read is unconditional so that the 6
+// (ORDER + 1)^DIM loads issue together.  Returns false (nothing read) when
+// the stencil crosses an absorbing x edge.
+template <int DIM, int ORDER>
+__device__ __forceinline__ bool qed_gather(const QedArgs& A, const int (&gc)[3], const float (&f)[3],
+                                           float (&fld)[6]) {
+    constexpr int K = ORDER + 2;
+    const Geo& g = A.g;
+    int ix[K];
+    long long ry[K], rz[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        int i = gc[0] - 1 + k;
+        if (g.absorb) { if (i < 0 || i >= g.fx) return false; }
+        else          { i = wrapn(i, g.nx); }
+        ix[k] = i;
+        ry[k] = (long long)wrapn(gc[1] - 1 + k, g.ny) * g.fx;
+        rz[k] = DIM == 3 ? (long long)wrapn(gc[2] - 1 + k, g.nz) * g.ny * g.fx : 0;
+    }
+    const NodeW<ORDER> nx_(1, f[0]), ny_(1, f[1]), nz_(1, f[2]);
+    const HalfW<ORDER> hx_(1, f[0]), hy_(1, f[1]), hz_(1, f[2]);
+    const float* F[6] = {A.E.p[0], A.E.p[1], A.E.p[2], A.B.p[0], A.B.p[1], A.B.p[2]};
+#pragma unroll
+    for (int comp = 0; comp < 6; ++comp) {
+        // E_x (h,n,n), E_y (n,h,n), E_z (n,n,h), B_x (n,h,h), B_y (h,n,h), B_z (h,h,n)
+        const bool hx = (comp == 0 || comp == 4 || comp == 5);
+        const bool hy = (comp == 1 || comp == 3 || comp == 5);
+        const bool hz = (comp == 2 || comp == 3 || comp == 4);
+        const int bx = hx ? hx_.base : nx_.base, by = hy ? hy_.base : ny_.base;
+        const int bz = hz ? hz_.base : nz_.base;
+        float acc = 0.0f;
+#pragma unroll
+        for (int c = 0; c < (DIM == 3 ? ORDER + 1 : 1); ++c) {
+            const long long oz = DIM == 3 ? (bz ? rz[c + 1] : rz[c]) : 0;
+            float accb = 0.0f;
+#pragma unroll
+            for (int b = 0; b <= ORDER; ++b) {
+                const long long oy = oz + (by ? ry[b + 1] : ry[b]);
+                float r = 0.0f;
+#pragma unroll
+                for (int a = 0; a <= ORDER; ++a) {
+                    const float v = __ldg(F[comp] + oy + (bx ? ix[a + 1] : ix[a]));
+                    r = __fmaf_rn(v, hx ? hx_.w[a] : nx_.w[a], r);
+                }
+                accb = __fmaf_rn(r, hy ? hy_.w[b] : ny_.w[b], accb);
+            }
+            acc = DIM == 3 ? __fmaf_rn(accb, hz ? hz_.w[c] : nz_.w[c], acc) : accb;
+        }
+        fld[comp] = acc;
+    }
+    return true;
+}
+
 // One pass over the emitting species after its push.  The fields are
 // gathered at x - (dt/2) v, the particle's position at the time of its
 // momentum u (the stored position is half a step ahead of it).
@@ -183,15 +239,8 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
             else if (fd >= 1.0f) { fd -= 1.0f; gc[d] += 1; }
             f[d] = fd;
         }
-        const int lc[3] = {2, 2, DIM == 3 ? 2 : 0};
-        const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
-        const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
         float fld[6];
-        bool outside = false;
-        const LoadGlobal<DIM> ld{&A.g, {A.E.p[0], A.E.p[1], A.E.p[2], A.B.p[0], A.B.p[1], A.B.p[2]},
-                                 {gc[0], gc[1], gc[2]}, &outside};
-        gather32<DIM, ORDER>(ld, nx_, ny_, nz_, hx_, hy_, hz_, fld);
-        if (outside) { set_status(A.st, LPIC_ST_OUTSIDE); continue; }
+        if (!qed_gather<DIM, ORDER>(A, gc, f, fld)) { set_status(A.st, LPIC_ST_OUTSIDE); continue; }
         const float b0 = u[0] * ig, b1 = u[1] * ig, b2 = u[2] * ig;
         const float F0 = fld[0] + b1 * fld[5] - b2 * fld[4];
         const float F1 = fld[1] + b2 * fld[3] - b0 * fld[5];

@@ -96,6 +96,8 @@ class Workload:
     seed: int = SEED_BASE
     notes: str = ""
     boundary: str = "mur"           # absorbing x: "mur" edges or "cpml" layers
+    b0: float = 0.0                 # uniform initial B_z (normalised units)
+    qed_eps_ref: float = 0.0        # > 0: nonlinear Compton emission, hbar omega / (m c^2)
 
     @property
     def cells(self) -> int:
@@ -137,11 +139,25 @@ def maxwell_juttner(g: np.random.Generator, theta: float, n: int) -> np.ndarray:
     exp(-e / theta), a mixture of two gamma distributions (shapes 3/2 and 7/2,
     scale theta) that numpy samples directly; a candidate is kept with
     probability sqrt(e + 2) (1 + e) / (2 sqrt(2) (1 + e^2)) (at least about
-    one half at small theta).  Directions are uniform on the sphere."""
+    one half at small theta).  That acceptance falls like 1 / sqrt(e) at large
+    energies, so for theta >= 1 the envelope is (1 + e)^2 exp(-e / theta)
+    instead (sqrt(e (e + 2)) <= 1 + e): a mixture of gamma distributions of
+    shapes 1, 2, 3 with weights theta, 2 theta^2, 2 theta^3, and acceptance
+    sqrt(e (e + 2)) / (1 + e), close to one where e >> 1.  Directions are
+    uniform on the sphere."""
+    out = np.empty(0)
+    if theta >= 1.0:
+        wts = np.array([theta, 2.0 * theta ** 2, 2.0 * theta ** 3])
+        cum = np.cumsum(wts / wts.sum())
+        while out.shape[0] < n:
+            m = (n - out.shape[0]) * 5 // 4 + 64
+            shape = 1.0 + np.searchsorted(cum, g.random(m), side="right").clip(0, 2)
+            e = theta * g.standard_gamma(shape)
+            keep = g.random(m) * (1.0 + e) <= np.sqrt(e * (e + 2.0))
+            out = np.concatenate([out, e[keep]])
     wa = math.gamma(1.5) * theta ** 1.5
     wb = math.gamma(3.5) * theta ** 3.5
     pa = wa / (wa + wb)
-    out = np.empty(0)
     while out.shape[0] < n:
         m = 2 * (n - out.shape[0]) + 64
         shape = np.where(g.random(m) < pa, 1.5, 3.5)
@@ -205,6 +221,12 @@ def load_all(wl: Workload, cells: tuple | None = None) -> list:
     out = []
     for s in range(len(wl.species)):
         out.append(load_species(wl, s, out, cells))
+    if wl.qed_eps_ref > 0:
+        # the emission draws are keyed by particle id: ids unique across species
+        base = 0
+        for p in out:
+            p.id = (p.id + base).astype(np.int32)
+            base += p.n
     return out
 
 
@@ -294,6 +316,28 @@ def heating2d(res=20, ppc=16, L_lambda=16, precision="fp32", seed=None) -> Workl
                       same_positions_as=0)]
     return Workload(f"heating2d_dx{res}_ppc{ppc}_{n}x{n}", 2, (n, n), h, dt, 1, False, sp, steps,
                     precision=precision, seed=SEED_BASE + 1000 * 6 + res + ppc if seed is None else seed)
+
+
+def qed2d(n=1024, ppc=16, theta=3000.0, b0=4.0, lambda_um=0.8, order=2, precision="fp32",
+          seed=None) -> Workload:
+    """Synchrotron cooling of a hot pair plasma through nonlinear Compton
+    emission (Sec. 3.4): electrons and positrons at kT = theta m c^2
+    (Maxwell-Juttner momenta, mean gamma ~ 3 theta) and density 1 n_c each,
+    in a uniform B_z = b0 (units m c omega / e), periodic n x n box of
+    lambda / 32 cells, dt = 0.95 CFL; eps_ref = hbar omega / (m c^2) of a
+    lambda_um laser.  With the defaults chi ~ eps_ref gamma b0 ~ 0.1 and
+    about 0.5% of the leptons emit a photon per step.  The paper gives no
+    QED benchmark configuration: this set-up is synthetic.  Positron ids
+    follow the electrons' (ids are unique across the emitting species)."""
+    dx = LAMBDA / 32
+    h = (dx, dx)
+    dt = cfl_dt(h)
+    sp = [SpeciesSpec(**ELECTRON, ppc=ppc, vth=0.0, density=1.0, theta=theta),
+          SpeciesSpec(q=1.0, m=1.0, ppc=ppc, vth=0.0, density=1.0, theta=theta, same_positions_as=0)]
+    eps = 1.23984198 / lambda_um / (M_E_KEV * 1e3)
+    return Workload(f"qed2d_{n}x{n}_ppc{ppc}", 2, (n, n), h, dt, order, False, sp, 100,
+                    precision=precision, b0=b0, qed_eps_ref=eps,
+                    seed=SEED_BASE + 1000 * 7 + n + ppc if seed is None else seed)
 
 
 @dataclass

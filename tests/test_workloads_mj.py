@@ -23,7 +23,7 @@ def _sample(theta, seed=11):
     return W.maxwell_juttner(W.generator(seed), theta, N)
 
 
-@pytest.mark.parametrize("theta", [1e-6, 1.0 / 511.0, 0.05, 1.0, 5.0])
+@pytest.mark.parametrize("theta", [1e-6, 1.0 / 511.0, 0.05, 1.0, 5.0, 3000.0])
 def test_mean_gamma_and_pressure(theta):
     u = _sample(theta)
     gam = np.sqrt(1.0 + (u ** 2).sum(0))
@@ -44,8 +44,8 @@ def test_isotropy(theta):
         assert abs(v[c] / v.mean() - 1.0) < 0.02
 
 
-def test_energy_distribution_ks():
-    theta = 0.5
+@pytest.mark.parametrize("theta", [0.5, 2.0])      # both envelopes of the sampler
+def test_energy_distribution_ks(theta):
     u = _sample(theta, seed=13)
     e = np.sort(np.sqrt(1.0 + (u ** 2).sum(0)) - 1.0)
     dens = lambda x: math.sqrt(x * (x + 2.0)) * (1.0 + x) * math.exp(-x / theta)
