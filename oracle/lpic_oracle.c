@@ -913,3 +913,127 @@ int orc_qed_compton(const orc_grid *g, orc_species *e, double eps_ref, uint32_t 
     }
     return ORC_OK;
 }
+
+/* --------------------------------------- QED: Breit-Wheeler pairs (Sec. 3.4)
+ * Pair creation by photons in the locally-constant-field approximation, by
+ * the same event Monte Carlo.  Photon of momentum k (m c units, energy k m c^2)
+ * along khat:
+ *   chi_g = eps_ref k sqrt((E + khat x B)^2 - (khat . E)^2),
+ *   dW / deta = alpha / (eps_ref sqrt(3) pi k) F(eta, chi_g),
+ *   F = (eta / (1 - eta) + (1 - eta) / eta) K_{2/3}(z) + int_z^inf K_{1/3},
+ *   z = 2 / (3 chi_g eta (1 - eta)),
+ * eta = the electron's share of the photon energy (the spectrum is symmetric
+ * in eta <-> 1 - eta).  The pair takes the photon's momentum: u_- = eta k,
+ * u_+ = (1 - eta) k (vectors along khat); photons with k <= 2 (below the
+ * pair threshold) never convert.  Counter (id, step, 1, 0) word 0 draws eta;
+ * a photon's initial depth uses counter (id, 0, 3, 0). */
+
+double orc_bw_f(double eta, double chi)
+{
+    if (eta <= 0.0 || eta >= 1.0) return 0.0;
+    const double z = 2.0 / (3.0 * chi * eta * (1.0 - eta));
+    if (z > 700.0) return 0.0;
+    return (eta / (1.0 - eta) + (1.0 - eta) / eta) * bessel_k_int(2.0 / 3.0, z, 0) + bessel_k_int(1.0 / 3.0, z, 1);
+}
+
+/* cumulative int_0^eta F on the uniform grid eta_k = k / n */
+static void bw_cumulative(double chi, int n, double *cum)
+{
+    cum[0] = 0.0;
+    double prev = 0.0;
+    for (int k = 1; k <= n; ++k) {
+        const double f = orc_bw_f((double)k / n, chi);
+        cum[k] = cum[k - 1] + 0.5 * (prev + f) / n;
+        prev = f;
+    }
+}
+
+double orc_bw_rate(double chi, double k, double eps_ref)
+{
+    if (chi <= 0.0 || k <= 2.0) return 0.0;
+    const int n = 4000;
+    double *cum = (double *)malloc(sizeof(double) * (n + 1));
+    bw_cumulative(chi, n, cum);
+    const double F = cum[n];
+    free(cum);
+    const double alpha = 1.0 / 137.035999084;
+    return alpha / (eps_ref * sqrt(3.0) * M_PI * k) * F;
+}
+
+/* electron energy share with cumulative probability r */
+double orc_bw_eta(double chi, double r)
+{
+    const int n = 4000;
+    double *cum = (double *)malloc(sizeof(double) * (n + 1));
+    bw_cumulative(chi, n, cum);
+    const double target = r * cum[n];
+    int k = 0;
+    while (k < n && cum[k + 1] < target) ++k;
+    const double f = (cum[k + 1] > cum[k]) ? (target - cum[k]) / (cum[k + 1] - cum[k]) : 0.0;
+    free(cum);
+    return (k + f) / n;
+}
+
+double orc_chi_g(const double k[3], const double E[3], const double B[3], double eps_ref)
+{
+    const double km = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+    if (km <= 0.0) return 0.0;
+    const double n[3] = {k[0] / km, k[1] / km, k[2] / km};
+    const double f[3] = {E[0] + n[1] * B[2] - n[2] * B[1], E[1] + n[2] * B[0] - n[0] * B[2],
+                         E[2] + n[0] * B[1] - n[1] * B[0]};
+    const double ne = n[0] * E[0] + n[1] * E[1] + n[2] * E[2];
+    const double q = f[0] * f[0] + f[1] * f[1] + f[2] * f[2] - ne * ne;
+    return eps_ref * km * sqrt(q > 0.0 ? q : 0.0);
+}
+
+double orc_qed_initial_tau_kind(long id, uint32_t kind, uint32_t seed_lo, uint32_t seed_hi)
+{
+    const uint32_t ctr[4] = {(uint32_t)id, 0u, kind, 0u}, key[2] = {seed_lo, seed_hi};
+    uint32_t o[4];
+    philox4x32_10(ctr, key, o);
+    return -log(u01(o[0]));
+}
+
+/* After step n: for every alive photon of `ph` (index = id) the fields at its
+ * position and its momentum give chi_g; tau[p] decreases by W dt and at zero
+ * the photon is removed and an electron (eta) and a positron (1 - eta) are
+ * written to pe[7][cap] and pp[7][cap] (x0, x1, x2, u0, u1, u2, w) from *npair
+ * on (the same count for both). */
+int orc_qed_bw(const orc_grid *g, orc_species *ph, double eps_ref, uint32_t seed_lo, uint32_t seed_hi,
+               long step, double *tau, double *pe, double *pp, long cap, long *npair)
+{
+    const double dt = g->dt;
+    for (long p = 0; p < ph->n; ++p) {
+        if (!ph->alive[p]) continue;
+        const double k[3] = {ph->u[0][p], ph->u[1][p], ph->u[2][p]};
+        const double km = sqrt(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        if (km <= 2.0) continue;
+        double x[3] = {0, 0, 0}, E[3], B[3];
+        for (int d = 0; d < g->dim; ++d) x[d] = ph->x[d][p];
+        if (orc_gather(g, x, E, B) != ORC_OK) return ORC_EOUTSIDE;
+        const double chi = orc_chi_g(k, E, B, eps_ref);
+        if (chi <= 0.0) continue;
+        tau[p] -= orc_bw_rate(chi, km, eps_ref) * dt;
+        if (tau[p] > 0.0) continue;
+        const uint32_t ctr[4] = {(uint32_t)p, (uint32_t)step, 1u, 0u}, key[2] = {seed_lo, seed_hi};
+        uint32_t o[4];
+        philox4x32_10(ctr, key, o);
+        const double eta = orc_bw_eta(chi, u01(o[0]));
+        if (*npair < cap) {
+            for (int d = 0; d < 3; ++d) {
+                const double xd = d < g->dim ? ph->x[d][p] : 0.0;
+                pe[d * cap + *npair] = xd;
+                pp[d * cap + *npair] = xd;
+            }
+            for (int c = 0; c < 3; ++c) {
+                pe[(3 + c) * cap + *npair] = eta * k[c];
+                pp[(3 + c) * cap + *npair] = (1.0 - eta) * k[c];
+            }
+            pe[6 * cap + *npair] = ph->w[p];
+            pp[6 * cap + *npair] = ph->w[p];
+            *npair += 1;
+        }
+        ph->alive[p] = 0;
+    }
+    return ORC_OK;
+}

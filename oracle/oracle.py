@@ -281,6 +281,13 @@ def _qed_sigs():
         f.restype, f.argtypes = res, args
     L.orc_chi_e.restype = d
     L.orc_chi_e.argtypes = [_dp, _dp, _dp, d]
+    for name, res, args in (("orc_bw_f", d, [d, d]), ("orc_bw_rate", d, [d, d, d]), ("orc_bw_eta", d, [d, d]),
+                            ("orc_qed_initial_tau_kind", d,
+                             [ctypes.c_long, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32])):
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    L.orc_chi_g.restype = d
+    L.orc_chi_g.argtypes = [_dp, _dp, _dp, d]
     return L
 
 
@@ -333,3 +340,50 @@ def qed_compton(grid: Grid, sp: Species, eps_ref, seed, step, tau, cap=1 << 16):
     n = nph.value
     ph = ph.reshape(7, cap)[:, :n]
     return Species(0.0, 0.0, ph[:grid.dim].copy(), ph[3:6].copy(), ph[6].copy())
+
+
+# Breit-Wheeler pair creation (Sec. 3.4)
+def bw_f(eta, chi):
+    return _qed_sigs().orc_bw_f(eta, chi)
+
+
+def bw_rate(chi, k, eps_ref):
+    return _qed_sigs().orc_bw_rate(chi, k, eps_ref)
+
+
+def bw_eta(chi, r):
+    return _qed_sigs().orc_bw_eta(chi, r)
+
+
+def chi_g(k, E, B, eps_ref):
+    a = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) for v in (k, E, B)]
+    return _qed_sigs().orc_chi_g(_ptr(a[0]), _ptr(a[1]), _ptr(a[2]), eps_ref)
+
+
+def qed_initial_tau_kind(ids, kind, seed):
+    """-ln r with r from counter (id, 0, kind, 0): kind 2 for leptons, 3 for photons."""
+    L = _qed_sigs()
+    lo, hi = int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF
+    return np.array([L.orc_qed_initial_tau_kind(int(i), int(kind), lo, hi) for i in ids])
+
+
+def qed_bw(grid: Grid, ph: Species, eps_ref, seed, step, tau, cap=1 << 16):
+    """Pair events of one step; removes converted photons from `ph` and
+    returns (electrons, positrons) as Species (q = -1 / +1, m = 1)."""
+    L = lib()
+    L.orc_qed_bw.argtypes = [ctypes.POINTER(_CGrid), ctypes.POINTER(_CSpecies), ctypes.c_double,
+                             ctypes.c_uint32, ctypes.c_uint32, ctypes.c_long, _dp, _dp, _dp,
+                             ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
+    g, s = grid.c(), ph.c()
+    pe, pp = np.zeros(7 * cap), np.zeros(7 * cap)
+    npair = ctypes.c_long(0)
+    assert tau.dtype == np.float64 and tau.flags.c_contiguous
+    _check(L.orc_qed_bw(ctypes.byref(g), ctypes.byref(s), eps_ref, int(seed) & 0xFFFFFFFF,
+                        (int(seed) >> 32) & 0xFFFFFFFF, int(step), _ptr(tau), _ptr(pe), _ptr(pp), cap,
+                        ctypes.byref(npair)), "qed bw")
+    n = npair.value
+    out = []
+    for arr, q in ((pe, -1.0), (pp, 1.0)):
+        a = arr.reshape(7, cap)[:, :n]
+        out.append(Species(q, 1.0, a[:grid.dim].copy(), a[3:6].copy(), a[6].copy()))
+    return out[0], out[1]
