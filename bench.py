@@ -47,7 +47,8 @@ WORKLOADS = {
                 "(134M), CIC, re-sorted every 10 steps, FP32 push + int64 fixed-point deposit", 400),
     "qed2d": ("2D3V synchrotron cooling of a pair plasma 1024x1024, dx=lambda/32 (0.8 um), e- and e+ "
               "at kT=3000 m c^2 (Maxwell-Juttner), 16+16 particles/cell (33.5M), uniform B_z=4, "
-              "nonlinear Compton emission every step (chi ~ 0.1, photons pushed at c), TSC, periodic, "
+              "nonlinear Compton emission and Breit-Wheeler pair creation passes every step (chi ~ 0.1, "
+              "photons pushed at c), TSC, periodic, "
               "FP32 push + int64 fixed-point deposit", 0),
     "ensemble": ("96 independent 2D3V periodic plasmas in one ensemble (batched kernels, persistent "
                  "work-queue particle kernel, one CUDA graph per step): sides 128-768, 4-64 "
@@ -58,7 +59,7 @@ WORKLOADS = {
 def metric_name(workload):
     if workload == "qed2d":
         return ("particle-steps/s (gather+push+deposit, whole step incl. sort, Maxwell and the "
-                "nonlinear Compton emission passes; photons counted)")
+                "nonlinear Compton and Breit-Wheeler passes; photons counted)")
     return "particle-steps/s (gather+push+deposit, whole step incl. sort and Maxwell)"
 
 
@@ -228,12 +229,15 @@ def tuned_choice(args, wl):
     return ch
 
 def qed_summary(qed, wl, counts0, counts1, G, peak, which):
-    """The emission pass (k_qed_compton32 over each emitting species, plus a
-    one-thread count clamp) timed with CUDA events on the launching stream.
+    """The QED passes (k_qed_compton32 over each emitting species, then
+    k_qed_bw32 over the photons, each followed by a one-thread count clamp)
+    timed with CUDA events on the launching stream.
     Algorithmic bytes per emitter per step: cell, offsets, u, id and tau read,
     tau written (8 + 4 dim + 12 B); per photon created: the emitter's weight
     read, its momentum written and the photon written (48 + 4 dim B); the
-    fields of the grid read once (24 B per cell)."""
+    fields of the grid read once (24 B per cell).  The pair pass reads each
+    photon's cell and momentum (16 B) and, above the pair threshold, its
+    offsets, id and depth (not counted)."""
     ms = sum(a.elapsed_time(b) for a, b in qed["events"])
     n_steps = len(qed["events"])
     emit_ids = [i for i, sp in enumerate(G.species) if sp.m > 0]
@@ -243,10 +247,11 @@ def qed_summary(qed, wl, counts0, counts1, G, peak, which):
     d = wl.dim
     per_emitter = 8 + 4 * d + 12
     per_photon = 48 + 4 * d
-    bytes_step = n_emit * per_emitter + created * per_photon + 24 * wl.cells
+    n_ph = 0.5 * (counts0[ph] + counts1[ph])
+    bytes_step = n_emit * per_emitter + created * per_photon + 24 * wl.cells + 16 * n_ph
     t = ms / 1e3 / max(1, n_steps)
     achieved = bytes_step / t / 1e9
-    return {"kernel": "k_qed_compton32", "ms_per_step": 1e3 * t,
+    return {"kernel": "k_qed_compton32 + k_qed_bw32", "ms_per_step": 1e3 * t,
             "emitters": int(n_emit), "photons_created_per_step": created,
             "photons_alive": int(counts1[ph]),
             "emission_passes_per_step": len(emit_ids),
@@ -284,8 +289,10 @@ def run_b300(args, rank, world, local_rank):
         phot = G.add_empty_species(0.0, 0.0, n_ids // 2, stream=stream)
         G.B[2].fill_(wl.b0)
         G.qed_init(wl.qed_eps_ref, wl.seed, stream)
-        qed = dict(emitters=[sp for sp in G.species if sp.m > 0], photons=phot,
-                   tau=G.qed_initial_tau(n_ids, stream), events=[])
+        emitters = [sp for sp in G.species if sp.m > 0]
+        qed = dict(emitters=emitters, photons=phot, tau=G.qed_initial_tau(n_ids, stream),
+                   ph_tau=torch.zeros(phot.cap, dtype=torch.float32, device=dev), events=[],
+                   pairs=(emitters[0], emitters[1]) if len(emitters) == 2 else None)
     del parts
     dt = G.dt
     pre = WORKLOADS[args.workload][1] if args.pre_steps is None else args.pre_steps
@@ -299,7 +306,9 @@ def run_b300(args, rank, world, local_rank):
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ev[0].record(stream)
         for sp in qed["emitters"]:
-            G.qed_compton(sp, qed["photons"], qed["tau"], k, stream)
+            G.qed_compton(sp, qed["photons"], qed["tau"], k, stream, photon_tau=qed["ph_tau"])
+        if qed["pairs"] is not None:
+            G.qed_breit_wheeler(qed["photons"], *qed["pairs"], qed["ph_tau"], k, stream)
         if timed:
             ev[1].record(stream)
             qed["events"].append(ev)
@@ -427,7 +436,7 @@ def run_b300(args, rank, world, local_rank):
     if result is not None:
         result["config"]["tuning"] = tuned
     state = dict(G=G, stream=stream, dev=dev, step=step, counts=counts1, wl=wl, advance=advance,
-                 extra=[qed["tau"]] if qed is not None else [])
+                 extra=[qed["tau"], qed["ph_tau"]] if qed is not None else [])
     return result, state
 
 
@@ -582,6 +591,7 @@ def oracle_sample(args, budget_s, max_steps):
         ids = np.concatenate([p.id for p in parts])
         tau = [O.qed_initial_tau(p.id, wl.seed) for p in parts]
         assert len(set(ids.tolist())) == len(ids)
+    phots = []
     nemit = len(sps)
     t0 = time.perf_counter()
     steps = 0
@@ -594,6 +604,10 @@ def oracle_sample(args, budget_s, max_steps):
                 ph = O.qed_compton(g, sps[k], wl.qed_eps_ref, wl.seed, steps, tau[k])
                 if ph.x.shape[1]:
                     sps.append(ph)
+                    phots.append((ph, O.qed_initial_tau_kind(np.arange(ph.x.shape[1]), 3, wl.seed)))
+            for ph, pt in list(phots):                   # pair creation by the photons
+                e_, p_ = O.qed_bw(g, ph, wl.qed_eps_ref, wl.seed, steps, pt)
+                sps += [s for s in (e_, p_) if s.x.shape[1]]
         steps += 1
     el = time.perf_counter() - t0
     desc = (f"{'x'.join(str(v) for v in wl.n)} cells of the workload (same dx, profile, ppc), "

@@ -138,6 +138,9 @@ typedef struct {
     void *buffers[2];           /* two device buffers of lpic_species_bytes() bytes */
     int staggered;              /* 0: buffers hold x^0, add_species advances them by dt/2;
                                    1: they already hold x^{1/2} */
+    double max_weight;          /* bound on |w| of particles created in this species later
+                                   (Breit-Wheeler pairs); the fixed-point shift covers
+                                   max(this, the largest |w| in the buffer); 0 = none */
 } lpic_species_desc;
 
 typedef struct {
@@ -378,10 +381,16 @@ lpic_status lpic_sort_tiles_static(int dim, int nx, int ny, int nz, const int ti
  * eps_ref and the seed.  Synchronises `stream`. */
 lpic_status lpic_qed_init(lpic_grid_t grid, double eps_ref, uint64_t seed, cudaStream_t stream);
 
-/* tau[id] = -ln r for id in [0, n_ids), r from counter (id, 0, 2, 0). */
-lpic_status lpic_qed_initial_tau(lpic_grid_t grid, float *tau, long long n_ids, cudaStream_t stream);
+/* tau[id] = -ln r for id in [0, n_ids), r from counter (id, 0, 2, 0) for the
+ * depths of emitting particles (photons = 0) or (id, 0, 3, 0) for the
+ * pair-creation depths of photons (photons = 1). */
+lpic_status lpic_qed_initial_tau(lpic_grid_t grid, float *tau, long long n_ids, int photons,
+                                 cudaStream_t stream);
 
 /* One emission pass over species `electron_species` (any massive species),
+ * optionally setting each new photon's pair-creation depth
+ * photon_tau[photon id] (counter (id, 0, 3, 0); photon_tau may be NULL with
+ * photon_n_ids = 0; an id outside [0, photon_n_ids) sets LPIC_ST_OVERFLOW),
  * normally right after lpic_step (the grid's fields at call time are used).
  * Photons are appended to `photon_species` (a species added with m = 0 and
  * q = 0), which gets new particle ids count, count + 1, ... (count = its
@@ -392,7 +401,38 @@ lpic_status lpic_qed_initial_tau(lpic_grid_t grid, float *tau, long long n_ids, 
  * skips the particle.  step is the counter word (0 <= step < 2^32).
  * Asynchronous. */
 lpic_status lpic_qed_compton(lpic_grid_t grid, int electron_species, int photon_species, float *tau,
-                             long long n_ids, long long step, cudaStream_t stream);
+                             long long n_ids, float *photon_tau, long long photon_n_ids, long long step,
+                             cudaStream_t stream);
+
+/* Breit-Wheeler pair creation (Sec. 3.4: pairs from energetic photons, the
+ * energy split by the pair spectrum, the pair inserted into the electron and
+ * positron species).  Same approximation and Monte Carlo as above, for a
+ * photon of momentum k (energy k m c^2) along khat:
+ *   chi_g = eps_ref k sqrt((E + khat x B)^2 - (khat . E)^2),
+ *   dW/deta = alpha / (eps_ref sqrt(3) pi k) F(eta, chi_g),
+ *   F = (eta/(1 - eta) + (1 - eta)/eta) K_{2/3}(z) + int_z^inf K_{1/3},
+ *   z = 2 / (3 chi_g eta (1 - eta)),
+ * eta the electron's share; r from counter (id, step, 1, 0) word 0; the
+ * electron gets momentum eta k, the positron (1 - eta) k, both the photon's
+ * stored position and weight; the photon is removed.  Photons with |k| <= 2
+ * (below the pair threshold) never convert.  Tables over chi_g in
+ * [1e-2, 1e3] (the rate is 0 below, where it is under 1e-110 of its scale,
+ * and flushes to 0 in float below chi_g ~ 0.03); rate ~1e-4, eta ~1e-4.
+ * One pass over `photon_species` with depths tau[photon id] (n_ids entries).
+ * New particles get ids count, count + 1, ... of their species; a pair that
+ * exceeds a capacity or whose weight exceeds a receiving species' bound
+ * (max_weight at add time) is dropped and sets LPIC_ST_OVERFLOW (its photon
+ * is still removed).  The two pair species need a sort before their next
+ * push (lpic_step does it).  Asynchronous. */
+lpic_status lpic_qed_breit_wheeler(lpic_grid_t grid, int photon_species, int electron_species,
+                                   int positron_species, float *tau, long long n_ids, long long step,
+                                   cudaStream_t stream);
+
+/* The pair tables' lookups for n (chi_g, r) pairs (device arrays): H =
+ * int_0^1 F deta at chi_g (W = alpha H / (eps_ref sqrt(3) pi k)) and eta(chi_g, r).
+ * Asynchronous. */
+lpic_status lpic_qed_pair_eval(lpic_grid_t grid, const double *chi, const double *r, long long n, double *h,
+                               double *eta, cudaStream_t stream);
 
 /* The table lookups for n given (chi, r) pairs (device arrays): h = int_0^1 S
  * dxi at chi (W = alpha h / (eps_ref sqrt(3) pi gamma)) and xi(chi, r).

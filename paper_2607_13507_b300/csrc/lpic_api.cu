@@ -125,6 +125,8 @@ struct lpic_grid {
     uint32_t seed[2] = {0, 0};
     QedTab qtab{};
     float* d_qtab = nullptr;                   // logh | top | cdf
+    BwTab btab{};
+    float* d_btab = nullptr;                   // g | cdf (Breit-Wheeler)
 };
 
 namespace {
@@ -633,6 +635,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     cudaFree(g->d_psi); cudaFree(g->d_pcoef);
     cudaFree(g->d_clock);
     cudaFree(g->d_qtab);
+    cudaFree(g->d_btab);
     delete g;
     return LPIC_OK;
 }
@@ -668,6 +671,7 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
         return fail(LPIC_EINVAL, "particle buffers must be 256-byte aligned");
     Species s;
     s.q = d.q; s.m = d.m; s.cap = d.capacity; s.count0 = d.count; s.massless = massless;
+    if (!(d.max_weight >= 0) || !std::isfinite(d.max_weight)) return fail(LPIC_EINVAL, "max_weight must be finite, >= 0");
     s.buf[0] = d.buffers[0]; s.buf[1] = d.buffers[1];
     const int nt = (int)g->ntiles;
     s.item_cap = nt + (d.capacity + g->P - 1) / g->P + 1;
@@ -713,6 +717,7 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
         s.wmax = wm;
     }
     if (!std::isfinite(s.wmax)) return fail(LPIC_EINVAL, "non-finite particle weight");
+    s.wmax = std::max(s.wmax, d.max_weight);   // particles created later (pairs) stay under the bound
     // x^0 -> x^{1/2}
     if (!d.staggered) {
         const int nb = grid_blocks(s.cap, g->nsm);
@@ -1448,9 +1453,25 @@ lpic_status lpic_qed_init(lpic_grid_t g, double eps_ref, uint64_t seed, cudaStre
         T.nchi = H.nchi; T.ny = H.ny;
         T.lchi0 = (float)H.lchi0; T.inv_dl = (float)(1.0 / H.dl); T.chi0 = (float)std::exp(H.lchi0);
     }
+    if (!g->d_btab) {
+        const BwHostTables H = bw_build_tables(1e-2, 1e3, 32, 513);
+        const size_t n = H.g.size() + H.cdf.size();
+        float* d = nullptr;
+        if (cudaMalloc(&d, n * sizeof(float)) != cudaSuccess) return fail(LPIC_ENOMEM, "QED table allocation failed");
+        g->d_btab = d;
+        LPIC_CUDA(cudaMemcpyAsync(d, H.g.data(), H.g.size() * 4, cudaMemcpyHostToDevice, st));
+        LPIC_CUDA(cudaMemcpyAsync(d + H.nchi, H.cdf.data(), H.cdf.size() * 4, cudaMemcpyHostToDevice, st));
+        LPIC_CUDA(cudaStreamSynchronize(st));
+        BwTab& T = g->btab;
+        T.g = d; T.cdf = d + H.nchi;
+        T.nchi = H.nchi; T.ny = H.ny;
+        T.lchi0 = (float)H.lchi0; T.inv_dl = (float)(1.0 / H.dl); T.chi0 = (float)std::exp(H.lchi0);
+    }
     const double alpha = 1.0 / 137.035999084;
     g->qtab.pref = (float)(alpha / (eps_ref * std::sqrt(3.0) * M_PI));
     g->qtab.eps_ref = (float)eps_ref;
+    g->btab.pref = g->qtab.pref;
+    g->btab.eps_ref = (float)eps_ref;
     g->eps_ref = eps_ref;
     g->seed[0] = (uint32_t)(seed & 0xffffffffu);
     g->seed[1] = (uint32_t)(seed >> 32);
@@ -1458,18 +1479,18 @@ lpic_status lpic_qed_init(lpic_grid_t g, double eps_ref, uint64_t seed, cudaStre
     return LPIC_OK;
 }
 
-lpic_status lpic_qed_initial_tau(lpic_grid_t g, float* tau, long long n_ids, cudaStream_t st) {
+lpic_status lpic_qed_initial_tau(lpic_grid_t g, float* tau, long long n_ids, int photons, cudaStream_t st) {
     if (lpic_status r = check_grid(g)) return r;
     if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
     if (n_ids < 0 || (n_ids > 0 && !tau)) return fail(LPIC_EINVAL, "tau is NULL or n_ids negative");
     if (n_ids == 0) return LPIC_OK;
-    k_qed_tau0<<<grid_blocks(n_ids, g->nsm), 256, 0, st>>>(tau, n_ids, g->seed[0], g->seed[1]);
+    k_qed_tau0<<<grid_blocks(n_ids, g->nsm), 256, 0, st>>>(tau, n_ids, photons ? 3u : 2u, g->seed[0], g->seed[1]);
     LPIC_LAUNCHED("k_qed_tau0");
     return LPIC_OK;
 }
 
-lpic_status lpic_qed_compton(lpic_grid_t g, int sid_e, int sid_ph, float* tau, long long n_ids, long long step,
-                             cudaStream_t st) {
+lpic_status lpic_qed_compton(lpic_grid_t g, int sid_e, int sid_ph, float* tau, long long n_ids, float* ph_tau,
+                             long long ph_n_ids, long long step, cudaStream_t st) {
     if (lpic_status r = check_species(g, sid_e)) return r;
     if (lpic_status r = check_species(g, sid_ph)) return r;
     if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
@@ -1480,6 +1501,7 @@ lpic_status lpic_qed_compton(lpic_grid_t g, int sid_e, int sid_ph, float* tau, l
     if (!ph.massless) return fail(LPIC_EINVAL, "species %d must be massless and charge-free", sid_ph);
     if (n_ids < 0 || (n_ids > 0 && !tau)) return fail(LPIC_EINVAL, "tau is NULL or n_ids negative");
     if (step < 0 || step > 0xffffffffLL) return fail(LPIC_EINVAL, "step must fit 32 bits");
+    if (ph_n_ids < 0 || (ph_n_ids > 0 && !ph_tau)) return fail(LPIC_EINVAL, "photon_tau is NULL or its length negative");
     QedArgs A{};
     A.g = g->geo;
     A.E = ptr3<const float>(g->d.E);
@@ -1493,6 +1515,8 @@ lpic_status lpic_qed_compton(lpic_grid_t g, int sid_e, int sid_ph, float* tau, l
     A.T = g->qtab;
     A.tau = tau;
     A.n_ids = n_ids;
+    A.ph_tau = ph_n_ids > 0 ? ph_tau : nullptr;
+    A.ph_n_ids = ph_n_ids;
     A.dt = (float)g->d.dt;
     A.dth0 = (float)(g->d.dt / g->d.dx);
     A.dth1 = (float)(g->d.dt / g->d.dy);
@@ -1519,6 +1543,74 @@ lpic_status lpic_qed_eval(lpic_grid_t g, const double* chi, const double* r, lon
     if (n == 0) return LPIC_OK;
     k_qed_eval<<<grid_blocks(n, g->nsm), 256, 0, st>>>(g->qtab, chi, r, n, h, xi);
     LPIC_LAUNCHED("k_qed_eval");
+    return LPIC_OK;
+}
+
+
+lpic_status lpic_qed_breit_wheeler(lpic_grid_t g, int sid_ph, int sid_el, int sid_po, float* tau, long long n_ids,
+                                   long long step, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid_ph)) return r;
+    if (lpic_status r = check_species(g, sid_el)) return r;
+    if (lpic_status r = check_species(g, sid_po)) return r;
+    if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
+    Species& ph = g->sp[sid_ph];
+    Species& el = g->sp[sid_el];
+    Species& po = g->sp[sid_po];
+    if (!ph.massless) return fail(LPIC_EINVAL, "species %d must be massless and charge-free", sid_ph);
+    if (el.massless || po.massless) return fail(LPIC_EINVAL, "the pair species must be massive");
+    if (n_ids < 0 || (n_ids > 0 && !tau)) return fail(LPIC_EINVAL, "tau is NULL or n_ids negative");
+    if (step < 0 || step > 0xffffffffLL) return fail(LPIC_EINVAL, "step must fit 32 bits");
+    BwArgs A{};
+    QedArgs& Q = A.q;
+    Q.g = g->geo;
+    Q.E = ptr3<const float>(g->d.E);
+    Q.B = ptr3<const float>(g->d.B);
+    Q.e = view32(g, ph, ph.cur);
+    Q.dec = g->dec;
+    Q.tau = tau;
+    Q.n_ids = n_ids;
+    Q.dt = (float)g->d.dt;
+    Q.dth0 = (float)(g->d.dt / g->d.dx);
+    Q.dth1 = (float)(g->d.dt / g->d.dy);
+    Q.dth2 = (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0));
+    Q.k0 = g->seed[0]; Q.k1 = g->seed[1];
+    Q.step = (uint32_t)step;
+    Q.st = g->d_status;
+    A.T = g->btab;
+    A.el = view32(g, el, el.cur);
+    A.po = view32(g, po, po.cur);
+    A.el_n = el.d_n; A.po_n = po.d_n;
+    A.el_next_id = el.d_n + 1; A.po_next_id = po.d_n + 1;
+    A.el_cap = el.cap; A.po_cap = po.cap;
+    A.el_wmax = (float)el.wmax; A.po_wmax = (float)po.wmax;
+    const int nb = grid_blocks(ph.cap, g->nsm, 16);
+    const int D = g->d.dim, O = g->d.shape_order;
+    if (D == 2) { if (O == 1) k_qed_bw32<2, 1><<<nb, 256, 0, st>>>(A); else k_qed_bw32<2, 2><<<nb, 256, 0, st>>>(A); }
+    else        { if (O == 1) k_qed_bw32<3, 1><<<nb, 256, 0, st>>>(A); else k_qed_bw32<3, 2><<<nb, 256, 0, st>>>(A); }
+    LPIC_LAUNCHED("k_qed_bw32");
+    k_qed_clamp<<<1, 32, 0, st>>>(el.d_n, el.cap);
+    LPIC_LAUNCHED("k_qed_clamp");
+    if (&po != &el) {
+        k_qed_clamp<<<1, 32, 0, st>>>(po.d_n, po.cap);
+        LPIC_LAUNCHED("k_qed_clamp");
+    }
+    // the new particles sit after the tiles' ranges: sort before the next push
+    for (Species* s : {&el, &po}) {
+        s->since_sort = std::max(s->since_sort, g->K);
+        s->counts_fresh = false;
+    }
+    ph.counts_fresh = false;
+    return LPIC_OK;
+}
+
+lpic_status lpic_qed_pair_eval(lpic_grid_t g, const double* chi, const double* r, long long n, double* h,
+                               double* eta, cudaStream_t st) {
+    if (lpic_status rr = check_grid(g)) return rr;
+    if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
+    if (n < 0 || (n > 0 && (!chi || !r || !h || !eta))) return fail(LPIC_EINVAL, "NULL array or negative n");
+    if (n == 0) return LPIC_OK;
+    k_bw_eval<<<grid_blocks(n, g->nsm), 256, 0, st>>>(g->btab, chi, r, n, h, eta);
+    LPIC_LAUNCHED("k_bw_eval");
     return LPIC_OK;
 }
 

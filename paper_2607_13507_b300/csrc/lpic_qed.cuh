@@ -117,11 +117,12 @@ __device__ inline float qed_xi(const QedTab& T, float chi, float r) {
 }
 
 // --------------------------------------------------------------- the kernels
-// Initial optical depths tau[id] = -ln r, r from counter (id, 0, 2, 0).
-__global__ void k_qed_tau0(float* tau, long long n_ids, uint32_t k0, uint32_t k1) {
+// Initial optical depths tau[id] = -ln r, r from counter (id, 0, kind, 0):
+// kind 2 for emitting particles, 3 for photons (pair creation).
+__global__ void k_qed_tau0(float* tau, long long n_ids, uint32_t kind, uint32_t k0, uint32_t k1) {
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n_ids;
          id += (long long)gridDim.x * blockDim.x) {
-        const U4 o = philox4x32_10(U4{(uint32_t)id, 0u, 2u, 0u}, k0, k1);
+        const U4 o = philox4x32_10(U4{(uint32_t)id, 0u, kind, 0u}, k0, k1);
         tau[id] = (float)(-log(u01d(o.x)));
     }
 }
@@ -150,6 +151,8 @@ struct QedArgs {
     QedTab T;
     float* tau;
     long long n_ids;
+    float* ph_tau;         // optional: pair-creation depths of new photons, by photon id
+    long long ph_n_ids;
     float dt, dth0, dth1, dth2;
     uint32_t k0, k1, step;
     unsigned* st;
@@ -266,7 +269,17 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) A.ph.u[c][j] = s * u[c];
             A.ph.w[j] = p.w[i];
-            A.ph.id[j] = atomicAdd(A.ph_next_id, 1);
+            const int pid = atomicAdd(A.ph_next_id, 1);
+            A.ph.id[j] = pid;
+            if (A.ph_tau) {
+                // the new photon's depth for pair creation: counter (id, 0, 3, 0)
+                if (pid >= 0 && (long long)pid < A.ph_n_ids) {
+                    const U4 q = philox4x32_10(U4{(uint32_t)pid, 0u, 3u, 0u}, A.k0, A.k1);
+                    A.ph_tau[pid] = (float)(-log(u01d(q.x)));
+                } else {
+                    set_status(A.st, LPIC_ST_OVERFLOW);
+                }
+            }
         } else {
             set_status(A.st, LPIC_ST_OVERFLOW);
         }
@@ -310,6 +323,155 @@ __global__ void k_photon32(Geo g, P32 p, CellDecode dec, float frac, float dth0,
         }
         if (DIM == 2) gc[2] = 0;
         p.cell[i] = (gc[0] < 0 || gc[0] >= g.nx) ? -1 : (gc[2] * g.ny + gc[1]) * g.nx + gc[0];
+    }
+}
+
+// ------------------------------------------------- Breit-Wheeler (Sec. 3.4)
+// Pair creation by a photon of momentum k along khat:
+//   chi_g = eps_ref k sqrt((E + khat x B)^2 - (khat . E)^2),
+//   dW/deta = alpha / (eps_ref sqrt(3) pi k) F(eta, chi_g),
+//   F = (eta/(1 - eta) + (1 - eta)/eta) K_{2/3}(z) + int_z^inf K_{1/3},
+//   z = 2 / (3 chi_g eta (1 - eta)),
+// eta the electron's energy share (F is symmetric in eta <-> 1 - eta).
+// Tables: g_i = ln H(chi_i) + 8 / (3 chi_i), H = int_0^1 F deta (smooth in
+// ln chi: the exp(-8 / (3 chi)) of the small-chi limit is taken out), and the
+// normalised cumulative of F over eta in [0, 1/2] at eta = y^{3/2} / 2, y
+// uniform (the cumulative grows like eta^{2/3} near 0 at large chi).  Below
+// chi_0 = 0.01 the rate is below 1e-110 of its scale and is taken as 0.
+struct BwTab {
+    const float* g;        // [nchi]
+    const float* cdf;      // [nchi][ny]
+    int nchi, ny;
+    float lchi0, inv_dl, chi0;
+    float pref;            // alpha / (eps_ref sqrt(3) pi): W = pref H(chi) / k
+    float eps_ref;
+};
+
+__device__ inline float bw_h(const BwTab& T, float chi) {
+    if (!(chi >= T.chi0)) return 0.0f;
+    const float u = (logf(chi) - T.lchi0) * T.inv_dl;
+    const int i = min((int)u, T.nchi - 2);
+    const float f = u - (float)i;
+    return expf(T.g[i] + f * (T.g[i + 1] - T.g[i]) - 8.0f / (3.0f * chi));
+}
+
+// share in [0, 1/2] of half-cumulative probability s in row i
+__device__ inline float bw_row_eta(const BwTab& T, int i, float s) {
+    const float* P = T.cdf + (long long)i * T.ny;
+    int lo = 0, hi = T.ny - 1;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P[mid] <= s) lo = mid; else hi = mid;
+    }
+    const float pa = P[lo], pb = P[hi];
+    const float f = pb > pa ? fminf((s - pa) / (pb - pa), 1.0f) : 0.0f;
+    const float y = ((float)lo + f) / (float)(T.ny - 1);
+    return 0.5f * y * sqrtf(y);
+}
+
+// eta(chi, r): the half of the symmetric spectrum from r < 1/2 or not, the
+// share within it from the half-cumulative, rows blended linearly in ln chi.
+__device__ inline float bw_eta(const BwTab& T, float chi, float r) {
+    float u = (logf(fmaxf(chi, T.chi0)) - T.lchi0) * T.inv_dl;
+    u = fminf(fmaxf(u, 0.0f), (float)(T.nchi - 1));
+    const int i = min((int)u, T.nchi - 2);
+    const float f = u - (float)i;
+    const bool low = r < 0.5f;
+    const float s = low ? 2.0f * r : 2.0f * (1.0f - r);
+    const float a = bw_row_eta(T, i, s), b = bw_row_eta(T, i + 1, s);
+    const float e = a + f * (b - a);
+    return low ? e : 1.0f - e;
+}
+
+__global__ void k_bw_eval(BwTab T, const double* chi, const double* r, long long n, double* h, double* eta) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float c = (float)chi[i];
+        const float rr = fminf((float)r[i], 0.99999994f);
+        h[i] = (double)bw_h(T, c);
+        eta[i] = (double)bw_eta(T, c, rr);
+    }
+}
+
+struct BwArgs {
+    QedArgs q;             // geometry, fields, photon species as q.e, keys, step, status
+    BwTab T;
+    P32 el, po;            // receiving species (current buffers)
+    int *el_n, *po_n, *el_next_id, *po_next_id;
+    long long el_cap, po_cap;
+    float el_wmax, po_wmax;  // weight bounds of the receiving species (fixed-point current)
+};
+
+// One pass over a photon species: photons at or below the pair threshold
+// (|k| <= 2) never convert; a converted photon is removed (cell -1) and an
+// electron (eta k) and a positron ((1 - eta) k) appear at its stored position
+// with its weight.
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(256) k_qed_bw32(BwArgs A) {
+    const QedArgs& Q = A.q;
+    const P32& p = Q.e;
+    const int n = *p.n;
+    const float dth[3] = {Q.dth0, Q.dth1, Q.dth2};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int cell = p.cell[i];
+        if (cell < 0) continue;
+        const float k[3] = {p.u[0][i], p.u[1][i], p.u[2][i]};
+        const float km = sqrtf(k[0] * k[0] + k[1] * k[1] + k[2] * k[2]);
+        if (!(km > 2.0f)) continue;
+        const int id = p.id[i];
+        if (id < 0 || (long long)id >= Q.n_ids) { set_status(Q.st, LPIC_ST_OVERFLOW); continue; }
+        const float ik = 1.0f / km;
+        const float nn[3] = {k[0] * ik, k[1] * ik, k[2] * ik};
+        int gc[3];
+        Q.dec(cell, gc);
+        if (DIM == 2) gc[2] = 0;
+        float f[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            float fd = p.off[d][i] - 0.5f * dth[d] * nn[d];
+            if (fd < 0.0f) { fd += 1.0f; gc[d] -= 1; if (fd >= 1.0f) fd = 0.99999994f; }
+            else if (fd >= 1.0f) { fd -= 1.0f; gc[d] += 1; }
+            f[d] = fd;
+        }
+        float fld[6];
+        if (!qed_gather<DIM, ORDER>(Q, gc, f, fld)) { set_status(Q.st, LPIC_ST_OUTSIDE); continue; }
+        const float F0 = fld[0] + nn[1] * fld[5] - nn[2] * fld[4];
+        const float F1 = fld[1] + nn[2] * fld[3] - nn[0] * fld[5];
+        const float F2 = fld[2] + nn[0] * fld[4] - nn[1] * fld[3];
+        const float ne = nn[0] * fld[0] + nn[1] * fld[1] + nn[2] * fld[2];
+        const float q2 = F0 * F0 + F1 * F1 + F2 * F2 - ne * ne;
+        const float chi = A.T.eps_ref * km * sqrtf(fmaxf(q2, 0.0f));
+        if (!(chi > 0.0f)) continue;
+        const float t = Q.tau[id] - A.T.pref * bw_h(A.T, chi) * ik * Q.dt;
+        Q.tau[id] = t;
+        if (t > 0.0f) continue;
+        const U4 o = philox4x32_10(U4{(uint32_t)id, Q.step, 1u, 0u}, Q.k0, Q.k1);
+        const float r = fminf((float)u01d(o.x), 0.99999994f);
+        const float eta = bw_eta(A.T, chi, r);
+        const float w = p.w[i];
+        p.cell[i] = -1;
+        const int je = atomicAdd(A.el_n, 1), jp = atomicAdd(A.po_n, 1);
+        // a pair that does not fit (capacity, or a weight above the receiving
+        // species' fixed-point bound) is dropped; a slot already taken is
+        // written as a removed particle, which the next sort discards
+        const bool fits = (long long)je < A.el_cap && (long long)jp < A.po_cap && w <= A.el_wmax &&
+                          w <= A.po_wmax;
+        if (!fits) {
+            set_status(Q.st, LPIC_ST_OVERFLOW);
+            if ((long long)je < A.el_cap) A.el.cell[je] = -1;
+            if ((long long)jp < A.po_cap) A.po.cell[jp] = -1;
+            continue;
+        }
+        A.el.cell[je] = cell;
+        A.po.cell[jp] = cell;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) { A.el.off[d][je] = p.off[d][i]; A.po.off[d][jp] = p.off[d][i]; }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) { A.el.u[c][je] = eta * k[c]; A.po.u[c][jp] = k[c] - eta * k[c]; }
+        A.el.w[je] = w;
+        A.po.w[jp] = w;
+        A.el.id[je] = atomicAdd(A.el_next_id, 1);
+        A.po.id[jp] = atomicAdd(A.po_next_id, 1);
     }
 }
 
@@ -377,6 +539,51 @@ inline QedHostTables qed_build_tables(double chi_min, double chi_max, int per_de
         T.logh[i] = (float)std::log(total);
         T.top[i] = (float)top;
         for (int j = 0; j < ny; ++j) T.cdf[(size_t)i * ny + j] = (float)(cum[j] / total);
+        T.cdf[(size_t)i * ny + ny - 1] = 1.0f;
+    }
+    return T;
+}
+
+
+inline double bw_spectrum(double eta, double chi) {
+    if (!(eta > 0.0) || !(eta < 1.0)) return 0.0;
+    const double z = 2.0 / (3.0 * chi * eta * (1.0 - eta));
+    if (z > 700.0) return 0.0;
+    double k23, ik13;
+    qed_bessel_pair(z, k23, ik13);
+    return (eta / (1.0 - eta) + (1.0 - eta) / eta) * k23 + ik13;
+}
+
+struct BwHostTables {
+    int nchi = 0, ny = 0;
+    double lchi0 = 0, dl = 0;
+    std::vector<float> g, cdf;
+};
+
+// Rows chi_i = chi_min 10^{i / per_decade}; the half-cumulative over
+// eta = y^{3/2} / 2 by the trapezoid rule in y (the integrand vanishes at
+// y = 0, where z grows without bound); H = twice the half integral.
+inline BwHostTables bw_build_tables(double chi_min, double chi_max, int per_decade, int ny) {
+    BwHostTables T;
+    T.dl = std::log(10.0) / per_decade;
+    T.lchi0 = std::log(chi_min);
+    T.nchi = (int)std::floor((std::log(chi_max) - T.lchi0) / T.dl + 1e-9) + 1;
+    T.ny = ny;
+    T.g.resize(T.nchi);
+    T.cdf.resize((size_t)T.nchi * ny);
+    std::vector<double> v(ny), cum(ny);
+    for (int i = 0; i < T.nchi; ++i) {
+        const double chi = std::exp(T.lchi0 + i * T.dl);
+        v[0] = 0.0;
+        for (int j = 1; j < ny; ++j) {
+            const double y = (double)j / (ny - 1);
+            v[j] = bw_spectrum(0.5 * y * std::sqrt(y), chi) * 0.75 * std::sqrt(y);
+        }
+        cum[0] = 0.0;
+        for (int j = 1; j < ny; ++j) cum[j] = cum[j - 1] + 0.5 * (v[j - 1] + v[j]) / (ny - 1);
+        const double half = cum[ny - 1];
+        T.g[i] = (float)(std::log(2.0 * half) + 8.0 / (3.0 * chi));
+        for (int j = 0; j < ny; ++j) T.cdf[(size_t)i * ny + j] = (float)(cum[j] / half);
         T.cdf[(size_t)i * ny + ny - 1] = 1.0f;
     }
     return T;

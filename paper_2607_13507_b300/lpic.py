@@ -32,7 +32,7 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
            "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
            "lpic_ensemble_launches", "lpic_qed_init", "lpic_qed_initial_tau", "lpic_qed_compton",
-           "lpic_qed_eval"]
+           "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval"]
 
 
 class LpicError(RuntimeError):
@@ -71,7 +71,7 @@ class PmlSpec:
 class SpeciesDesc(ctypes.Structure):
     _fields_ = [("q", ctypes.c_double), ("m", ctypes.c_double), ("count", ctypes.c_longlong),
                 ("capacity", ctypes.c_longlong), ("buffers", ctypes.c_void_p * 2),
-                ("staggered", ctypes.c_int)]
+                ("staggered", ctypes.c_int), ("max_weight", ctypes.c_double)]
 
 
 class GridInfo(ctypes.Structure):
@@ -130,9 +130,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_grid_get_info.argtypes = [vp, ctypes.POINTER(GridInfo)]
     lib.lpic_check_status.argtypes = [vp, st, ctypes.POINTER(ctypes.c_uint)]
     lib.lpic_qed_init.argtypes = [vp, ctypes.c_double, ctypes.c_uint64, st]
-    lib.lpic_qed_initial_tau.argtypes = [vp, vp, ctypes.c_longlong, st]
-    lib.lpic_qed_compton.argtypes = [vp, i, i, vp, ctypes.c_longlong, ctypes.c_longlong, st]
+    lib.lpic_qed_initial_tau.argtypes = [vp, vp, ctypes.c_longlong, i, st]
+    lib.lpic_qed_compton.argtypes = [vp, i, i, vp, ctypes.c_longlong, vp, ctypes.c_longlong,
+                                     ctypes.c_longlong, st]
     lib.lpic_qed_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
+    lib.lpic_qed_breit_wheeler.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, ctypes.c_longlong, st]
+    lib.lpic_qed_pair_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
     lib.lpic_last_error.restype = ctypes.c_char_p
     lib.lpic_last_error.argtypes = []
     for name in EXPORTS:
@@ -196,7 +199,7 @@ class Species:
                     u=[seg(g.dim + c, torch.float64) for c in range(3)],
                     w=seg(g.dim + 3, torch.float64), id=seg(g.dim + 4, torch.int32, 4 * cap))
 
-    def upload(self, p, staggered=False, stream=None):
+    def upload(self, p, staggered=False, stream=None, max_weight=0.0):
         """Copy a workloads.Particles initial state into buffer 0 and register
         the species with the grid."""
         g = self.grid
@@ -224,7 +227,7 @@ class Species:
             v["w"][:n] = torch.from_numpy(p.w.astype(np.float64)).to(dev)
         v["id"][:n] = torch.from_numpy(p.id).to(dev)
         desc = SpeciesDesc(self.q, self.m, n, self.cap, (ctypes.c_void_p * 2)(self.ptr(0), self.ptr(1)),
-                           int(staggered))
+                           int(staggered), float(max_weight))
         sid = ctypes.c_int(-1)
         _check(load().lpic_add_species(g.h_, ctypes.byref(desc), _stream(stream), ctypes.byref(sid)))
         self.id = sid.value
@@ -317,20 +320,20 @@ class Grid:
         except Exception:
             pass
 
-    def add_species(self, p, capacity=None, staggered=False, stream=None) -> Species:
+    def add_species(self, p, capacity=None, staggered=False, stream=None, max_weight=0.0) -> Species:
         sp = Species(self, p.q, p.m, capacity or _cap(p.n))
-        sp.upload(p, staggered, stream)
+        sp.upload(p, staggered, stream, max_weight)
         self.species.append(sp)
         return sp
 
-    def add_empty_species(self, q, m, capacity, stream=None) -> Species:
+    def add_empty_species(self, q, m, capacity, stream=None, max_weight=0.0) -> Species:
         """A species that starts empty (m = 0, q = 0: photons created by qed_compton)."""
         from .workloads import Particles
         e = np.zeros((self.dim, 0), np.int32)
         p = Particles(q=q, m=m, cell=e, off=e.astype(np.float32), u=np.zeros((3, 0), np.float32),
                       w=np.zeros(0, np.float32), id=np.zeros(0, np.int32))
         sp = Species(self, q, m, _cap(capacity))
-        sp.upload(p, True, stream)
+        sp.upload(p, True, stream, max_weight)
         self.species.append(sp)
         return sp
 
@@ -339,17 +342,39 @@ class Grid:
         """Build the emission tables; eps_ref = hbar omega / (m c^2) of the unit frequency."""
         _check(load().lpic_qed_init(self.h_, float(eps_ref), int(seed) & (2**64 - 1), _stream(stream)))
 
-    def qed_initial_tau(self, n_ids, stream=None) -> torch.Tensor:
-        """Optical depths -ln r for ids 0..n_ids-1 (float32 device tensor)."""
+    def qed_initial_tau(self, n_ids, stream=None, photons=False) -> torch.Tensor:
+        """Optical depths -ln r for ids 0..n_ids-1 (float32 device tensor);
+        photons=True: the pair-creation depths of photons."""
         tau = torch.empty(max(int(n_ids), 1), dtype=torch.float32, device=self.device)
-        _check(load().lpic_qed_initial_tau(self.h_, tau.data_ptr(), int(n_ids), _stream(stream)))
+        _check(load().lpic_qed_initial_tau(self.h_, tau.data_ptr(), int(n_ids), int(bool(photons)),
+                                           _stream(stream)))
         return tau[: int(n_ids)]
 
-    def qed_compton(self, electrons, photons, tau, step, stream=None):
-        """One emission pass of `electrons` into `photons` (Species objects)."""
+    def qed_compton(self, electrons, photons, tau, step, stream=None, photon_tau=None):
+        """One emission pass of `electrons` into `photons` (Species objects);
+        photon_tau (optional) receives the new photons' pair-creation depths."""
         assert tau.dtype == torch.float32 and tau.is_cuda and tau.is_contiguous()
+        pt, pn = (None, 0) if photon_tau is None else (photon_tau.data_ptr(), photon_tau.numel())
+        if photon_tau is not None:
+            assert photon_tau.dtype == torch.float32 and photon_tau.is_cuda and photon_tau.is_contiguous()
         _check(load().lpic_qed_compton(self.h_, electrons.id, photons.id, tau.data_ptr(), tau.numel(),
-                                       int(step), _stream(stream)))
+                                       pt, pn, int(step), _stream(stream)))
+
+    def qed_breit_wheeler(self, photons, electrons, positrons, tau, step, stream=None):
+        """One pair-creation pass of `photons` into `electrons` and `positrons`."""
+        assert tau.dtype == torch.float32 and tau.is_cuda and tau.is_contiguous()
+        _check(load().lpic_qed_breit_wheeler(self.h_, photons.id, electrons.id, positrons.id, tau.data_ptr(),
+                                             tau.numel(), int(step), _stream(stream)))
+
+    def qed_pair_eval(self, chi, r, stream=None):
+        """Device pair-table lookups: (H(chi), eta(chi, r)) as float64 numpy arrays."""
+        c = torch.as_tensor(np.asarray(chi, np.float64), device=self.device).contiguous()
+        rr = torch.as_tensor(np.asarray(r, np.float64), device=self.device).contiguous()
+        h, eta = torch.empty_like(c), torch.empty_like(c)
+        _check(load().lpic_qed_pair_eval(self.h_, c.data_ptr(), rr.data_ptr(), c.numel(), h.data_ptr(),
+                                         eta.data_ptr(), _stream(stream)))
+        torch.cuda.synchronize(self.device)
+        return h.cpu().numpy(), eta.cpu().numpy()
 
     def qed_eval(self, chi, r, stream=None):
         """Device table lookups: (h(chi), xi(chi, r)) as float64 numpy arrays."""

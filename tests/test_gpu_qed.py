@@ -287,3 +287,164 @@ def test_photons_stream_at_c_among_plasma_steps(order):
     ek, ef, qt = O.energy(g, sps)
     assert abs(d.kinetic - ek) < 1e-5 * ek
     assert d.particles == sum(p.n for p in parts)
+
+
+# ------------------------------------------------------- Breit-Wheeler pairs
+def test_pair_tables_match_oracle():
+    _, G = _grid()
+    chis = np.array([0.05, 0.1, 0.3, 1.0, 3.0, 10.0, 100.0, 500.0])
+    rs = np.array([0.01, 0.2, 0.45, 0.55, 0.8, 0.99])
+    C, R = np.meshgrid(chis, rs, indexing="ij")
+    h, eta = G.qed_pair_eval(C.ravel(), R.ravel())
+    h = h.reshape(C.shape)[:, 0]
+    eta = eta.reshape(C.shape)
+    for a, chi in enumerate(chis):
+        # the oracle's rate at k = 10, eps_ref = 1 is alpha H / (10 sqrt(3) pi)
+        h_o = O.bw_rate(chi, 10.0, 1.0) * 10.0 * np.sqrt(3.0) * np.pi / ALPHA
+        assert abs(h[a] / h_o - 1) < 3e-4, (chi, h[a], h_o)
+        for b, r in enumerate(rs):
+            assert abs(eta[a, b] - O.bw_eta(chi, r)) < 2e-4, (chi, r)
+    # below the table the rate is zero
+    h0, _ = G.qed_pair_eval([0.005], [0.5])
+    assert h0[0] == 0.0
+
+
+def test_photon_depths_initial_and_at_emission():
+    _, G = _grid()
+    n = 3000
+    tau = G.qed_initial_tau(n, photons=True).cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(tau, O.qed_initial_tau_kind(np.arange(n), 3, SEED), rtol=1e-6)
+    # photons created by emission get their depth from their new id
+    wl, G = _grid()
+    m = 512
+    e = G.add_species(_beam(wl, m, seed=21))
+    ph = G.add_empty_species(0.0, 0.0, 4 * m)
+    g = O.Grid(2, wl.n, wl.h, wl.dt, 1)
+    _set_fields(G, g, wl, E0=800.0, B0=800.0)
+    ptau = torch.full((4 * m,), -7.0, dtype=torch.float32, device=G.device)
+    G.qed_compton(e, ph, torch.zeros(m, dtype=torch.float32, device=G.device), 0, photon_tau=ptau)
+    assert G.check_status() == 0
+    ids = ph.state()["id"]
+    assert len(ids) > m // 2
+    got = ptau.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got[ids], O.qed_initial_tau_kind(ids, 3, SEED), rtol=1e-6)
+    rest = np.setdiff1d(np.arange(4 * m), ids)
+    assert np.all(got[rest] == -7.0)
+
+
+def _photons(wl, n, seed, kmin, kmax, below=10):
+    g = W.generator(seed)
+    cell = np.stack([g.integers(0, wl.n[d], n) for d in range(2)]).astype(np.int32)
+    off = g.random((2, n)).astype(np.float32)
+    d = g.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    mag = np.exp(g.uniform(np.log(kmin), np.log(kmax), n))
+    mag[:below] = 1.5                                          # below the pair threshold
+    return W.Particles(q=0.0, m=0.0, cell=cell, off=off, u=(d * mag).astype(np.float32),
+                       w=np.ones(n, np.float32), id=np.arange(n, dtype=np.int32))
+
+
+def _by_position(st, mask, key):
+    return np.array([key[(int(c), float(a), float(b))]
+                     for c, a, b in zip(st["cell"][mask], st["off"][0][mask], st["off"][1][mask])], dtype=np.int64)
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_pair_passes_match_oracle(order):
+    eps = 2e-5
+    wl, G = _grid(order=order, eps_ref=eps)
+    n = 120
+    # k in [10, 500] keeps chi_gamma = eps k |E_perp| below the tables' upper
+    # end (1e3), past which the rate is an extrapolation
+    p = _photons(wl, n, seed=31 + order, kmin=10.0, kmax=500.0)
+    el = G.add_empty_species(-1.0, 1.0, 2 * n, max_weight=1.0)
+    po = G.add_empty_species(1.0, 1.0, 2 * n, max_weight=1.0)
+    ph = G.add_species(p)
+    g = O.Grid(2, wl.n, wl.h, wl.dt, order)
+    h = np.array(wl.h)[:, None]
+    so = O.Species(0.0, 0.0, (p.cell + p.off) * h, p.u.astype(np.float64), p.w.astype(np.float64))
+    _set_fields(G, g, wl, E0=2e4, B0=2e4)              # chi_gamma up to ~400
+    tau_g = G.qed_initial_tau(n, photons=True)
+    tau_o = O.qed_initial_tau_kind(np.arange(n), 3, SEED)
+    kvec = p.u.astype(np.float64)
+    kmag = np.linalg.norm(kvec, axis=0)
+    ok = np.ones(n, bool)
+    conv_total = 0
+    for step in range(2):
+        t0_o = tau_o.copy()
+        st0 = ph.state()
+        alive_before = np.ones(n, bool)
+        alive_before[st0["id"][st0["cell"] < 0]] = False
+        e_before = set(el.state()["id"].tolist())
+        p_before = set(po.state()["id"].tolist())
+        el_o, po_o = O.qed_bw(g, so, eps, SEED, step, tau_o)
+        G.qed_breit_wheeler(ph, el, po, tau_g, step)
+        assert G.check_status() == 0
+        st1 = ph.state()
+        conv_g = np.zeros(n, bool)
+        conv_g[st1["id"][st1["cell"] < 0]] = True
+        conv_g &= alive_before
+        conv_o = alive_before & (so.alive == 0)
+        assert not conv_g[:10].any() and not conv_o[:10].any()    # below threshold
+        t1_g = tau_g.cpu().numpy().astype(np.float64)
+        # decisions: equal except at a margin within the rate tolerance
+        mis = ok & (conv_g != conv_o)
+        for i in np.nonzero(mis)[0]:
+            rest = t1_g[i] if conv_o[i] else tau_o[i]
+            assert rest < 1e-3 * max(t0_o[i], 1.0) + 1e-4, (i, rest)
+        assert mis.sum() <= 2
+        none = ok & alive_before & ~conv_g & ~conv_o
+        dec_o = t0_o[none] - tau_o[none]
+        assert np.all(np.abs(t1_g[none] - tau_o[none]) <= 5e-4 * dec_o + 2e-6 * t0_o[none] + 1e-5)
+        both = ok & conv_g & conv_o
+        conv_total += int(both.sum())
+        # the pairs, matched to their photon through the stored position
+        key = {(int(c), float(a), float(b)): int(i)
+               for c, a, b, i in zip(st0["cell"], st0["off"][0], st0["off"][1], st0["id"])}
+        se, sq = el.state(), po.state()
+        new_e = np.array([i not in e_before for i in se["id"]], dtype=bool)
+        new_p = np.array([i not in p_before for i in sq["id"]], dtype=bool)
+        assert new_e.sum() == new_p.sum() == conv_g.sum()
+        own_e, own_p = _by_position(se, new_e, key), _by_position(sq, new_p, key)
+        assert set(own_e.tolist()) == set(own_p.tolist()) == set(np.nonzero(conv_g)[0].tolist())
+        ue, up = np.zeros((3, n)), np.zeros((3, n))
+        ue[:, own_e] = se["u"][:, new_e]
+        up[:, own_p] = sq["u"][:, new_p]
+        np.testing.assert_allclose((ue + up)[:, conv_g], kvec[:, conv_g], rtol=1e-6,
+                                   atol=1e-6 * kmag.max())
+        idx_o = np.nonzero(conv_o)[0]
+        assert el_o.n == po_o.n == len(idx_o)
+        ueo = np.zeros((3, n))
+        ueo[:, idx_o] = el_o.u
+        assert np.all(np.abs(ue[:, both] - ueo[:, both]) <= 2e-4 * kmag[both] + 1e-6 * kmag[both])
+        assert np.all(se["w"][new_e] == 1.0) and np.all(sq["w"][new_p] == 1.0)
+        assert len(set(se["id"].tolist())) == len(se["id"])
+        ok &= ~mis          # particles that disagreed diverge: leave them out from now on
+    assert conv_total >= 10
+    # the new particles take part in the next full step (sorted first)
+    G.step(0.0)
+    assert G.check_status() == 0
+    d = G.diagnostics()
+    assert d.particles == ph.query()[1] + el.query()[1] + po.query()[1]
+
+
+def test_pair_capacity_and_weight_bound_overflow():
+    from paper_2607_13507_b300 import lpic
+    for cap, wmax in ((64, 1.0), (1024, 0.5)):
+        wl, G = _grid(eps_ref=2e-5)
+        n = 512
+        el = G.add_empty_species(-1.0, 1.0, cap, max_weight=wmax)
+        po = G.add_empty_species(1.0, 1.0, cap, max_weight=wmax)
+        ph = G.add_species(_photons(wl, n, seed=41, kmin=1e3, kmax=1e4, below=0))
+        g = O.Grid(2, wl.n, wl.h, wl.dt, 1)
+        _set_fields(G, g, wl, E0=2e4, B0=2e4)
+        tau = torch.full((n,), -1.0, dtype=torch.float32, device=G.device)    # every photon converts
+        G.qed_breit_wheeler(ph, el, po, tau, 0)
+        assert G.check_status() & lpic.ST_OVERFLOW
+        assert el.query()[1] <= cap and po.query()[1] <= cap
+        G.sort()
+        kept = el.query()[1]
+        # the two slots of a pair come from separate counters, so a pair can
+        # be dropped while one of its slots fits: at most cap pairs survive
+        assert po.query()[1] == kept
+        assert kept == 0 if wmax < 1.0 else 0 < kept <= cap
