@@ -448,3 +448,122 @@ def test_pair_capacity_and_weight_bound_overflow():
         # be dropped while one of its slots fits: at most cap pairs survive
         assert po.query()[1] == kept
         assert kept == 0 if wmax < 1.0 else 0 < kept <= cap
+
+
+# ------------------------------------------------------------------ 3D passes
+def _key3(st, mask=None):
+    m = np.ones(len(st["cell"]), bool) if mask is None else mask
+    return [(int(c), float(a), float(b), float(d)) for c, a, b, d in
+            zip(st["cell"][m], st["off"][0][m], st["off"][1][m], st["off"][2][m])]
+
+
+def _grid3(order, eps_ref):
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal3d(n=8, ppc=1, order=order, precision="fp32")
+    wl.species = []
+    G = lpic.grid_for(wl, lpic.FP32_FIXED)
+    G.qed_init(eps_ref, SEED)
+    g = O.Grid(3, wl.n, wl.h, wl.dt, order)
+    nz, ny, fx = G.field_shape
+    x = np.arange(fx)[None, None, :] * wl.h[0]
+    y = np.arange(ny)[None, :, None] * wl.h[1]
+    z = np.arange(nz)[:, None, None] * wl.h[2]
+    L = [wl.n[d] * wl.h[d] for d in range(3)]
+    kx, ky, kz = (2 * np.pi / l for l in L)
+    F0 = 2e4
+    vals = [0.1 * F0 * np.sin(ky * y + kz * z), F0 * (1 + 0.3 * np.sin(kx * x)) * (1 + 0.1 * np.cos(kz * z)),
+            0.2 * F0 * np.cos(kx * x + ky * y), 0.05 * F0 * np.cos(ky * y), 0.1 * F0 * np.sin(kx * x + kz * z),
+            F0 * (1 + 0.2 * np.cos(ky * y)) * (1 + 0.1 * np.sin(kz * z))]
+    for c in range(6):
+        v32 = (vals[c] * np.ones((nz, ny, fx))).astype(np.float32)
+        (G.E + G.B)[c].copy_(torch.from_numpy(v32).to(G.device))
+        (g.E + g.B)[c][...] = v32.astype(np.float64)
+    return wl, G, g
+
+
+def _parts3(wl, n, seed, mmin, mmax, q, m):
+    gen = W.generator(seed)
+    cell = np.stack([gen.integers(0, wl.n[d], n) for d in range(3)]).astype(np.int32)
+    off = gen.random((3, n)).astype(np.float32)
+    d = gen.normal(size=(3, n))
+    d /= np.linalg.norm(d, axis=0)
+    mag = np.exp(gen.uniform(np.log(mmin), np.log(mmax), n))
+    return W.Particles(q=q, m=m, cell=cell, off=off, u=(d * mag).astype(np.float32),
+                       w=np.ones(n, np.float32), id=np.arange(n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_3d_emission_and_pair_passes_match_oracle(order):
+    """One emission pass over leptons and one pair pass over photons on a 3D
+    grid whose fields vary along x, y and z."""
+    n = 96
+    # emission: eps_ref chosen for chi ~ 0.1 .. 10 with gamma in [5, 200]
+    wl, G, g = _grid3(order, eps_ref=2e-6)
+    p = _parts3(wl, n, 51 + order, 5.0, 200.0, -1.0, 1.0)
+    e = G.add_species(p)
+    ph = G.add_empty_species(0.0, 0.0, 2 * n)
+    h = np.array(wl.h)[:, None]
+    so = O.Species(-1.0, 1.0, (p.cell + p.off) * h, p.u.astype(np.float64), p.w.astype(np.float64))
+    tau_g = torch.full((n,), 0.05, dtype=torch.float32, device=G.device)
+    tau_o = np.full(n, 0.05)
+    st0 = e.state()
+    ph_o = O.qed_compton(g, so, 2e-6, SEED, 3, tau_o)
+    G.qed_compton(e, ph, tau_g, 3)
+    assert G.check_status() == 0
+    stp = ph.state()
+    key = dict(zip(_key3(st0), st0["id"].tolist()))
+    own_g = np.array([key[k] for k in _key3(stp)], dtype=np.int64)
+    em_g = np.zeros(n, bool)
+    em_g[own_g] = True
+    em_o = np.zeros(n, bool)
+    kv_o = np.zeros((3, n))
+    for j in range(ph_o.x.shape[1]):
+        hit = np.nonzero(np.all(so.x == ph_o.x[:, j:j + 1], axis=0))[0]
+        assert len(hit) == 1
+        em_o[hit[0]] = True
+        kv_o[:, hit[0]] = ph_o.u[:, j]
+    t1 = tau_g.cpu().numpy().astype(np.float64)
+    mis = em_g != em_o
+    for i in np.nonzero(mis)[0]:
+        assert (t1[i] if em_o[i] else tau_o[i]) < 1e-4
+    assert mis.sum() <= 2 and (em_g & em_o).sum() >= 10
+    both = em_g & em_o
+    kv_g = np.zeros((3, n))
+    kv_g[:, own_g] = stp["u"].astype(np.float64)
+    k_o = np.linalg.norm(kv_o, axis=0)
+    assert np.all(np.abs(np.linalg.norm(kv_g, axis=0)[both] - k_o[both]) <= 1e-3 * k_o[both])
+    none = ~em_g & ~em_o
+    assert np.all(np.abs(t1[none] - tau_o[none]) <= 5e-4 * (0.05 - tau_o[none]) + 1e-6)
+
+    # pair creation: photons with k in [10, 500] (chi_gamma below the tables' end)
+    wl, G, g = _grid3(order, eps_ref=2e-5)
+    p = _parts3(wl, n, 61 + order, 10.0, 500.0, 0.0, 0.0)
+    el = G.add_empty_species(-1.0, 1.0, 2 * n, max_weight=1.0)
+    po = G.add_empty_species(1.0, 1.0, 2 * n, max_weight=1.0)
+    phs = G.add_species(p)
+    so = O.Species(0.0, 0.0, (p.cell + p.off) * h, p.u.astype(np.float64), p.w.astype(np.float64))
+    tau_g = G.qed_initial_tau(n, photons=True)
+    tau_o = O.qed_initial_tau_kind(np.arange(n), 3, SEED)
+    st0 = phs.state()
+    el_o, po_o = O.qed_bw(g, so, 2e-5, SEED, 5, tau_o)
+    G.qed_breit_wheeler(phs, el, po, tau_g, 5)
+    assert G.check_status() == 0
+    st1 = phs.state()
+    conv_g = np.zeros(n, bool)
+    conv_g[st1["id"][st1["cell"] < 0]] = True
+    conv_o = so.alive == 0
+    t1 = tau_g.cpu().numpy().astype(np.float64)
+    mis = conv_g != conv_o
+    for i in np.nonzero(mis)[0]:
+        assert (t1[i] if conv_o[i] else tau_o[i]) < 1e-3
+    assert mis.sum() <= 2 and (conv_g & conv_o).sum() >= 10
+    key = dict(zip(_key3(st0), st0["id"].tolist()))
+    se = el.state()
+    own = np.array([key[k] for k in _key3(se)], dtype=np.int64)
+    ue = np.zeros((3, n))
+    ue[:, own] = se["u"].astype(np.float64)
+    ueo = np.zeros((3, n))
+    ueo[:, np.nonzero(conv_o)[0]] = el_o.u
+    both = conv_g & conv_o
+    kmag = np.linalg.norm(p.u.astype(np.float64), axis=0)
+    assert np.all(np.abs(ue[:, both] - ueo[:, both]) <= 2e-4 * kmag[both] + 1e-6 * kmag[both])
