@@ -112,8 +112,9 @@ struct lpic_grid {
     CellDecode dec{};
     FastDiv fT[3]{};
     double* d_clock = nullptr;                 // device time for graph replays
-    std::map<unsigned, cudaGraphExec_t> graphs;  // captured steps keyed by buffer parity
-    std::map<unsigned, long long> graph_launches;
+    // captured steps keyed by every species' buffer parity and sort state
+    std::map<unsigned long long, cudaGraphExec_t> graphs;
+    std::map<unsigned long long, long long> graph_launches;
     // optional timing of the fused particle kernel (benchmarks)
     bool timing = false;
     std::vector<cudaEvent_t> ev;               // pairs (start, stop)
@@ -956,12 +957,18 @@ lpic_status lpic_graph_steps(lpic_grid_t g, int nsteps, cudaStream_t st) {
     if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread)
         return fail(LPIC_EINVAL, "graph capture needs a created (non-default) stream");
     for (int k = 0; k < nsteps; ++k) {
-        unsigned key = 0;
-        for (size_t s = 0; s < g->sp.size(); ++s) key |= (unsigned)g->sp[s].cur << s;
-        if (g->d.precision == LPIC_FP32_FIXED && !g->sp.empty()) {
-            const Species& s0 = g->sp[0];
-            const int phase = (!s0.sorted || s0.since_sort >= g->K) ? 0 : s0.since_sort;
-            key |= (unsigned)phase << 16 | (unsigned)(s0.sorted && s0.counts_fresh) << 24 | (unsigned)s0.sorted << 25;
+        // FNV-1a over each species' buffer parity and sort state: species can
+        // be out of step with one another (a pair-creation pass marks its pair
+        // species for a sort), and the captured step must match all of them
+        unsigned long long key = 1469598103934665603ULL;
+        auto mix = [&key](unsigned long long v) { key ^= v; key *= 1099511628211ULL; };
+        for (const Species& s : g->sp) {
+            mix((unsigned long long)s.cur);
+            if (g->d.precision == LPIC_FP32_FIXED) {
+                const int phase = (!s.sorted || s.since_sort >= g->K) ? 0 : s.since_sort;
+                mix((unsigned long long)phase << 2 | (unsigned long long)(s.sorted && s.counts_fresh) << 1 |
+                    (unsigned long long)s.sorted);
+            }
         }
         auto it = g->graphs.find(key);
         if (it == g->graphs.end()) {
