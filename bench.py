@@ -11,6 +11,10 @@ HBM copy bandwidth as the roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
+--workload selects the set-up (laser2d by default; thermal3d, laser3d,
+thermal2d, heating2d, ensemble, and qed2d, whose steps also run the nonlinear
+Compton and Breit-Wheeler passes, reported in a "qed" object).
+
 Under torchrun each rank runs an independent replica of the workload (the
 problems do not exchange data; "scaling": "weak").  --impl reference times
 the FP64 CPU oracle on a bounded sample of the same workload on the host.
