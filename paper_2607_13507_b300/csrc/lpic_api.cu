@@ -727,8 +727,8 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
             const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
                         c = (float)(g->d.dt / g->d.dz);
             if (massless) {
-                if (g->d.dim == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
-                else               k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
+                if (g->d.dim == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c, 0);
+                else               k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c, 0);
             } else {
                 if (g->d.dim == 3) k_advance32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
                 else               k_advance32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 0.5f, a, b, c);
@@ -786,8 +786,9 @@ static lpic_status gpd_impl(lpic_grid_t g, int sid, cudaStream_t st, bool count_
         const int nb = grid_blocks(s.cap, g->nsm, 16);
         const float a = (float)(g->d.dt / g->d.dx), b = (float)(g->d.dt / g->d.dy),
                     c = (float)(g->d.dt / (D == 3 ? g->d.dz : 1.0));
-        if (D == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c);
-        else        k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c);
+        const int edge = g->d.absorb_x ? 2 : 0;
+        if (D == 3) k_photon32<3><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c, edge);
+        else        k_photon32<2><<<nb, 256, 0, st>>>(g->geo, p, g->dec, 1.0f, a, b, c, edge);
         LPIC_LAUNCHED("k_photon32");
         s.since_sort += 1;
         s.counts_fresh = false;

@@ -297,9 +297,12 @@ __global__ void k_qed_clamp(int* n, long long cap) {
 
 // Massless particles move at c along u: offsets advance by frac dt u / (|u| h)
 // with carries into the cell (at most one per dimension under the Courant
-// limit); they leave the grid through absorbing x edges.
+// limit).  With absorbing x edges a particle is removed once its cell is
+// within `edge` cells of an edge (2 in a step, as for charged particles,
+// whose deposit stencils must stay on the grid; 0 at the initial half push).
 template <int DIM>
-__global__ void k_photon32(Geo g, P32 p, CellDecode dec, float frac, float dth0, float dth1, float dth2) {
+__global__ void k_photon32(Geo g, P32 p, CellDecode dec, float frac, float dth0, float dth1, float dth2,
+                           int edge) {
     const int n = *p.n;
     const float dth[3] = {dth0, dth1, dth2};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -322,7 +325,7 @@ __global__ void k_photon32(Geo g, P32 p, CellDecode dec, float frac, float dth0,
             p.off[d][i] = fn;
         }
         if (DIM == 2) gc[2] = 0;
-        p.cell[i] = (gc[0] < 0 || gc[0] >= g.nx) ? -1 : (gc[2] * g.ny + gc[1]) * g.nx + gc[0];
+        p.cell[i] = (gc[0] < edge || gc[0] >= g.nx - edge) ? -1 : (gc[2] * g.ny + gc[1]) * g.nx + gc[0];
     }
 }
 

@@ -249,13 +249,16 @@ def test_massless_species_rejected_on_fp64_and_as_emitter():
         G2.qed_compton(ph, ph2, tau, 0)
 
 
-@pytest.mark.parametrize("order", [1, 2])
-def test_photons_stream_at_c_among_plasma_steps(order):
+@pytest.mark.parametrize("order,absorb", [(1, False), (2, False), (2, True)])
+def test_photons_stream_at_c_among_plasma_steps(order, absorb):
     """A plasma with a photon species in it, 5 full steps on both sides:
     the photons move on straight lines at c, deposit nothing and see no
     field, so the fields match the oracle's at the plasma's tolerance."""
     from paper_2607_13507_b300 import lpic
     wl = W.thermal2d(n=32, ppc=4, vth=0.05, order=order, precision="fp32")
+    # absorbing x: particles (photons too) are removed when they come within
+    # two cells of an x edge, on both sides alike
+    wl.absorb_x = absorb
     parts = W.load_all(wl)
     gen = W.generator(77)
     m = 500
@@ -267,6 +270,15 @@ def test_photons_stream_at_c_among_plasma_steps(order):
                        u=(d * np.exp(gen.uniform(0, 5, m))).astype(np.float32),
                        w=np.ones(m, np.float32), id=np.arange(m, dtype=np.int32))
     parts = parts + [phot]
+    if absorb:
+        # the plasma starts six cells clear of the x edges (the oracle's
+        # deposit stencils must stay on the grid), the photons three
+        def inner(q, lo):
+            k = (q.cell[0] >= lo) & (q.cell[0] < wl.n[0] - lo)
+            return W.Particles(q=q.q, m=q.m, cell=q.cell[:, k], off=q.off[:, k], u=q.u[:, k], w=q.w[k],
+                               id=np.arange(int(k.sum()), dtype=np.int32))
+        parts = [inner(q, 3 if q.m == 0 else 6) for q in parts]
+        phot = parts[-1]
     g, sps = oracle_case(wl, parts)
     G = gpu_case(wl, parts, lpic.FP32_FIXED)
     steps = 5
@@ -277,16 +289,19 @@ def test_photons_stream_at_c_among_plasma_steps(order):
     for c in range(3):
         assert rel_l2(Jg[c].cpu().numpy(), g.J[c]) < 1e-4, ("J", c)
         assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < 1e-4 * steps, ("E", c)
+    G.sort()            # compact the particles removed in the last step
     for k, sg in enumerate(G.species):
         xg, xo, ug, uo = match_particles(G, sg, sps[k], wl)
         for dd in range(wl.dim):
             assert np.max(np.abs(xg[dd] - xo[dd])) / wl.h[dd] < 1e-5 * steps, (k, dd)
         assert rel_l2(ug, uo) < 1e-5 * steps
-    assert np.array_equal(ug, phot.u.astype(np.float64))     # photons: no force
+    assert np.array_equal(ug, uo)                              # photons: no force
     d = G.diagnostics()
     ek, ef, qt = O.energy(g, sps)
     assert abs(d.kinetic - ek) < 1e-5 * ek
-    assert d.particles == sum(p.n for p in parts)
+    assert d.particles == sum(int(s.alive.sum()) for s in sps)
+    if absorb:
+        assert sps[-1].alive.sum() < phot.n                    # some photons left through the edges
 
 
 # ------------------------------------------------------- Breit-Wheeler pairs
