@@ -283,7 +283,9 @@ def run_b300(args, rank, world, local_rank):
     G = lpic.grid_for(wl, prec, device=dev, tile=tuned["tile"], block_particles=tuned["block_particles"],
                       sort_interval=tuned["sort_interval"])
     for p in parts:
-        G.add_species(p, stream=stream)
+        # a QED set-up keeps room for the pairs created into the lepton species
+        cap = (p.n * 9 // 8 + 63) // 64 * 64 if wl.qed_eps_ref > 0 else None
+        G.add_species(p, capacity=cap, stream=stream)
     loaded = [p.n // wl.species[i].ppc for i, p in enumerate(parts)]
     qed = None
     if wl.qed_eps_ref > 0:
@@ -294,7 +296,13 @@ def run_b300(args, rank, world, local_rank):
         G.B[2].fill_(wl.b0)
         G.qed_init(wl.qed_eps_ref, wl.seed, stream)
         emitters = [sp for sp in G.species if sp.m > 0]
-        qed = dict(emitters=emitters, photons=phot, tau=G.qed_initial_tau(n_ids, stream),
+        # ids of the particles created later: a range of their own per species
+        # (the depths and the random draws are keyed by id)
+        n_tau = n_ids
+        for sp in emitters:
+            sp.set_next_id(n_tau, stream)
+            n_tau += sp.cap
+        qed = dict(emitters=emitters, photons=phot, tau=G.qed_initial_tau(n_tau, stream),
                    ph_tau=torch.zeros(phot.cap, dtype=torch.float32, device=dev), events=[],
                    pairs=(emitters[0], emitters[1]) if len(emitters) == 2 else None)
     del parts

@@ -404,6 +404,14 @@ lpic_status lpic_qed_compton(lpic_grid_t grid, int electron_species, int photon_
                              long long n_ids, float *photon_tau, long long photon_n_ids, long long step,
                              cudaStream_t stream);
 
+/* Id given to the next particle that species `species_id` gains on the
+ * device (emitted photons, Breit-Wheeler pairs); by default its count at add
+ * time.  Ids key the optical depths and the random draws, so species that
+ * share a depth array need disjoint ranges: set each species' next id past
+ * every id in use.  Ids are int32: next_id plus the particles created later
+ * must stay below 2^31.  Asynchronous. */
+lpic_status lpic_species_set_next_id(lpic_grid_t grid, int species_id, long long next_id, cudaStream_t stream);
+
 /* Breit-Wheeler pair creation (Sec. 3.4: pairs from energetic photons, the
  * energy split by the pair spectrum, the pair inserted into the electron and
  * positron species).  Same approximation and Monte Carlo as above, for a

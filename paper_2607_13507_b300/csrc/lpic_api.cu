@@ -1622,4 +1622,13 @@ lpic_status lpic_qed_pair_eval(lpic_grid_t g, const double* chi, const double* r
     return LPIC_OK;
 }
 
+
+lpic_status lpic_species_set_next_id(lpic_grid_t g, int sid, long long next_id, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (next_id < 0 || next_id >= (1LL << 31)) return fail(LPIC_EINVAL, "next_id %lld outside [0, 2^31)", next_id);
+    k_set_int<<<1, 32, 0, st>>>(g->sp[sid].d_n + 1, (int)next_id);
+    LPIC_LAUNCHED("k_set_int");
+    return LPIC_OK;
+}
+
 }  // extern "C"

@@ -290,6 +290,11 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
     }
 }
 
+// One int written on the device (stream-ordered, no host buffer to keep alive).
+__global__ void k_set_int(int* p, int v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
 // After the emission pass: a photon count past the capacity is cut back.
 __global__ void k_qed_clamp(int* n, long long cap) {
     if (threadIdx.x == 0 && blockIdx.x == 0 && (long long)*n > cap) *n = (int)cap;

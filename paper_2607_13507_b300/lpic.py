@@ -32,7 +32,7 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
            "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
            "lpic_ensemble_launches", "lpic_qed_init", "lpic_qed_initial_tau", "lpic_qed_compton",
-           "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval"]
+           "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval", "lpic_species_set_next_id"]
 
 
 class LpicError(RuntimeError):
@@ -136,6 +136,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_qed_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
     lib.lpic_qed_breit_wheeler.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, ctypes.c_longlong, st]
     lib.lpic_qed_pair_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
+    lib.lpic_species_set_next_id.argtypes = [vp, i, ctypes.c_longlong, st]
     lib.lpic_last_error.restype = ctypes.c_char_p
     lib.lpic_last_error.argtypes = []
     for name in EXPORTS:
@@ -258,6 +259,10 @@ class Species:
         _check(load().lpic_positions_at_step(self.grid.h_, self.id, out.data_ptr(), _stream(stream)))
         o = out.view(3, self.cap)[: self.grid.dim, :cnt].cpu().numpy()
         return o
+
+    def set_next_id(self, next_id, stream=None):
+        """Id of the next particle this species gains on the device (photons, pairs)."""
+        _check(load().lpic_species_set_next_id(self.grid.h_, self.id, int(next_id), _stream(stream)))
 
     def charge(self, stream=None) -> torch.Tensor:
         """Charge density of the stored positions: float64 (FP64 path) or the

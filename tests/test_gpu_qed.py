@@ -631,3 +631,25 @@ def test_graph_replay_after_pair_pass_matches_eager():
     for sa, sb in zip(Ga.species, Gb.species):
         assert sa.query() == sb.query()
     assert Ga.diagnostics().particles == Gb.diagnostics().particles
+
+
+def test_created_particle_ids_follow_set_next_id():
+    """Pairs take ids from each species' next-id counter, which the caller
+    can place past every id in use (depths and draws are keyed by id)."""
+    wl, G = _grid(eps_ref=2e-5)
+    n = 256
+    el = G.add_empty_species(-1.0, 1.0, 512, max_weight=1.0)
+    po = G.add_empty_species(1.0, 1.0, 512, max_weight=1.0)
+    ph = G.add_species(_photons(wl, n, seed=81, kmin=1e3, kmax=1e3, below=0))
+    el.set_next_id(10_000)
+    po.set_next_id(20_000)
+    g = O.Grid(2, wl.n, wl.h, wl.dt, 1)
+    _set_fields(G, g, wl, E0=2e4, B0=2e4)
+    G.qed_breit_wheeler(ph, el, po, torch.full((n,), -1.0, dtype=torch.float32, device=G.device), 0)
+    assert G.check_status() == 0
+    ie, ip = np.sort(el.state()["id"]), np.sort(po.state()["id"])
+    assert len(ie) == len(ip) == n
+    assert np.array_equal(ie, 10_000 + np.arange(n)) and np.array_equal(ip, 20_000 + np.arange(n))
+    from paper_2607_13507_b300 import lpic
+    with pytest.raises(lpic.LpicError):
+        el.set_next_id(1 << 31)
