@@ -92,3 +92,18 @@ def test_pair_event_kinematics():
     assert np.array_equal(el.x[:2], x[:, 10:]) and np.array_equal(el.w, ph.w[10:])
     eta = el.u[0] / 2000.0
     assert 0.3 < eta.mean() < 0.7
+
+
+def test_large_chi_asymptote():
+    # chi -> inf: z -> 0 over the bulk of eta, K_{2/3}(z) -> Gamma(2/3) (z/2)^{-2/3} / 2 and
+    # the K_{1/3} tail stays finite, so int F deta -> Gamma(2/3) (3 chi)^{2/3} B(8/3, 2/3),
+    # approached like 1 - a chi^{-2/3}
+    c = special.gamma(2.0 / 3.0) * 3.0 ** (2.0 / 3.0) * special.beta(8.0 / 3.0, 2.0 / 3.0)
+
+    def ratio(chi):
+        H = O.bw_rate(chi, 10.0, 1.0) * 10.0 * math.sqrt(3.0) * math.pi / ALPHA
+        return H / (c * chi ** (2.0 / 3.0))
+
+    r2, r3 = ratio(1e2), ratio(1e3)
+    assert 0.0 < 1.0 - r3 < 1.0 - r2 < 0.1
+    assert abs((1.0 - r3) - (1.0 - r2) * 10.0 ** (-2.0 / 3.0)) < 2e-3
