@@ -99,3 +99,19 @@ def test_emission_conserves_momentum():
     assert ph.n == n
     assert np.allclose(sp.u + ph.u, p0, rtol=0, atol=1e-9)
     assert np.all(tau > 0)
+
+
+def test_large_chi_asymptote_of_the_rate():
+    # chi -> inf: delta -> 0 over the bulk of xi, K_{2/3}(delta) -> Gamma(2/3) (delta/2)^{-2/3} / 2
+    # and the K_{1/3} tail stays finite, so int S dxi -> Gamma(2/3) (3 chi)^{2/3}
+    # (B(1/3, 8/3) + B(1/3, 2/3)) / 2, approached like 1 - a chi^{-2/3}
+    c = 0.5 * special.gamma(2.0 / 3.0) * 3.0 ** (2.0 / 3.0) * (special.beta(1.0 / 3.0, 8.0 / 3.0)
+                                                                  + special.beta(1.0 / 3.0, 2.0 / 3.0))
+
+    def ratio(chi):
+        h = O.compton_rate(chi, 1.0, 1.0) * math.sqrt(3.0) * math.pi / ALPHA
+        return h / (c * chi ** (2.0 / 3.0))
+
+    r2, r3 = ratio(1e2), ratio(1e3)
+    assert 0.0 < 1.0 - r3 < 1.0 - r2 < 0.05
+    assert abs((1.0 - r3) - (1.0 - r2) * 10.0 ** (-2.0 / 3.0)) < 2e-3
