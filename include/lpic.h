@@ -331,9 +331,11 @@ lpic_status lpic_ensemble_launches(lpic_ensemble_t ensemble, long long *launches
  * synchronisation of cudaMalloc/cudaFree).  It needs no grid: the geometry is
  * given directly.  src and dst are two distinct buffers in the FP32_FIXED
  * particle layout above (capacity entries per array, multiple of 64, 256-byte
- * aligned); count_in (device int) is the number of particles in src;
+ * aligned); count_in (device int) is the number of particles in src (a
+ * value above capacity is taken as capacity, a negative one as 0);
  * count_out (device int) receives the number of particles written to dst
- * (removed particles, cell < 0, are dropped); tile_start (device array of
+ * (removed particles, cell < 0, and cells at or beyond nx ny nz, are
+ * dropped); tile_start (device array of
  * ntiles + 1 ints, tiles numbered x fastest) receives each tile's first index
  * in dst and, last, the total.  Order inside a tile is not specified.
  * Scratch: one fixed array in device global memory, held by every device that

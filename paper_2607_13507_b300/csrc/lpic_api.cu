@@ -106,7 +106,6 @@ struct lpic_grid {
     size_t smem32 = 0;
     long long launches = 0;
     int P = 4096;                              // particles per work item (FP32 path)
-    int R = 1;                                 // rounds of 256 moves between int32-box folds
     int K = 1;                                 // sort interval (steps)
     int m[3] = {0, 0, 0};                      // drift margin of the tiles (cells)
     CellDecode dec{};
@@ -190,17 +189,22 @@ __global__ void k_absmax_f64(const double* w, const int* n, unsigned long long* 
     atomicMax(out, m);
 }
 
-// Divisors of the tile kernel's field and current boxes (T + 2m + 4 and
+// Divisors of the tile kernel's field and current boxes (T + 2m + 3 and
 // T + 2m + 5 nodes per dimension).
 void box_divisors(const lpic_grid* g, Tiles& t) {
-    const int G0 = g->T[0] + 2 * g->m[0] + 4, G1 = g->T[1] + 2 * g->m[1] + 4;
-    const int G2 = g->d.dim == 3 ? g->T[2] + 2 * g->m[2] + 4 : 1;
-    const int H0 = G0 + 1, H1 = G1 + 1, H2 = g->d.dim == 3 ? G2 + 1 : 1;
-    t.fG0 = make_fastdiv((unsigned)G0); t.fG1 = make_fastdiv((unsigned)G1);
-    t.fF = make_fastdiv((unsigned)(G0 * G1 * G2));
-    t.fH0 = make_fastdiv((unsigned)H0); t.fH1 = make_fastdiv((unsigned)H1);
-    t.fJ = make_fastdiv((unsigned)(H0 * H1 * H2));
+    const TileSmem L = tile_smem(g->d.dim, g->T, g->m);
+    t.fG0 = make_fastdiv((unsigned)L.G[0]); t.fG1 = make_fastdiv((unsigned)L.G[1]);
+    t.fF = make_fastdiv((unsigned)L.fsz);
+    t.fH0 = make_fastdiv((unsigned)L.H[0]); t.fH1 = make_fastdiv((unsigned)L.H[1]);
+    t.fJ = make_fastdiv((unsigned)L.jsz);
 }
+
+// Bound (units of kBoundUnit) of one move's current at any node for a
+// species: S b + 1024 with S = rint(2^F |q| w_max) the largest integer charge
+// and b the per-move factor of move_factor().
+unsigned move_bound(const lpic_grid* g, const Species& s);
+// 2D: rounds of the tile kernel between folds of its int32 current boxes.
+int fold_rounds(const lpic_grid_desc& d);
 
 // Arguments of the tile kernel for one species.
 GpdArgs gpd_args(lpic_grid* g, Species& s, bool count_next) {
@@ -214,7 +218,8 @@ GpdArgs gpd_args(lpic_grid* g, Species& s, bool count_next) {
     t.items = s.d_items;
     t.nitems = s.d_nitems;
     t.P = g->P;
-    t.R = g->R;
+    t.bmax = move_bound(g, s);
+    t.R = fold_rounds(g->d);
     box_divisors(g, t);
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
@@ -404,24 +409,33 @@ lpic_status check_species(lpic_grid_t g, int sid) {
     return LPIC_OK;
 }
 
-// Rounds of 256 moves the int32 current box can take between folds into the
-// int64 box.  One move adds at most S b + 1024 to a node: S <= 2^22 is the
-// particle's integer charge (the shift F guarantees it), the 1024 units cover
-// the roundings and closures, and b bounds the current of one move in units
-// of S.  J_d along d is s (C1 - C0) K with C the running sum of the shape
-// weights (|C1 - C0| <= the displacement nu <= c dt / h cells, since the
-// running sum of a B-spline's weights moves with slope at most 1) and K the
-// transverse factor: 2D A_y <= k, 3D A_y A_z + DS_y DS_z / 12 <= k^2 + 1/12
-// (k = 0.75 TSC, 1 CIC).  2D J_z = s v_z W_z, |v_z| < 1, W_z <= k^2 + 1/12.
-int fold_rounds(const lpic_grid_desc& d) {
+// Largest current one move adds to any node, in units of the particle's
+// integer charge S.  J_d along d is s (C1 - C0) K with C the running sum of
+// the shape weights (|C1 - C0| <= the displacement nu <= c dt / h cells,
+// since the running sum of a B-spline's weights moves with slope at most 1)
+// and K the transverse factor: 2D A_y <= k, 3D A_y A_z + DS_y DS_z / 12 <=
+// k^2 + 1/12 (k = 0.75 TSC, 1 CIC); 2D J_z = s v_z W_z with |v_z| < 1 and
+// W_z <= k^2 + 1/12.  Roundings and closures add less than 1024 units.
+double move_factor(const lpic_grid_desc& d) {
     double nu = std::max(d.dt / d.dx, d.dt / d.dy);
     if (d.dim == 3) nu = std::max(nu, d.dt / d.dz);
     nu = std::min(nu, 1.0);                     // the kernel rejects longer moves
     const double k = d.shape_order == 2 ? 0.75 : 1.0;
     double b = nu * (d.dim == 3 ? k * k + 1.0 / 12.0 : k);
     if (d.dim == 2) b = std::max(b, k * k + 1.0 / 12.0);
-    const double per_move = 4194304.0 * b + 1024.0;
-    const int R = (int)std::floor(2147483647.0 / (256.0 * per_move));
+    return b;
+}
+
+unsigned move_bound(const lpic_grid* g, const Species& s) {
+    const double S = std::rint(std::ldexp(std::fabs(s.q) * s.wmax, g->F));
+    return (unsigned)std::ceil((S * move_factor(g->d) + 1024.0) / kBoundUnit) + 1u;
+}
+
+// 2D: rounds of 256 moves the int32 current boxes take between folds into
+// the int64 boxes, with every particle's integer charge S <= 2^22.
+int fold_rounds(const lpic_grid_desc& d) {
+    const double per_move = 4194304.0 * move_factor(d) + 1024.0;
+    const int R = (int)std::floor(2147483647.0 / (kGpdThreads * per_move));
     return std::max(1, std::min(R, 64));
 }
 
@@ -434,9 +448,15 @@ void recompute_shift(lpic_grid* g) {
     }
     if (mx <= 0.0) { g->F = 0; }
     else {
+        // S <= 2^22 (float rounding of the per-particle integers), no int64
+        // sum can overflow, and (3D) two deposit phases of the tile kernel
+        // (256 moves each) keep the int32 current boxes in range
         const int f1 = (int)std::floor(22.0 - std::log2(mx));
         const int f2 = (int)std::floor(61.0 - std::log2(total));
-        g->F = std::min(f1, f2);
+        const double phase = (g->d.dim == 3 ? 2.0 : 1.0) * kGpdThreads;
+        const double smax = (kBoundLimit * (double)kBoundUnit / phase - 2048.0) / move_factor(g->d);
+        const int f3 = (int)std::floor(std::log2(smax) - std::log2(mx));
+        g->F = std::min(f1, std::min(f2, f3));
     }
     const double u = std::ldexp(1.0, -g->F);
     const lpic_grid_desc& d = g->d;
@@ -529,7 +549,6 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     for (int k = 0; k < 3; ++k) g->fT[k] = make_fastdiv((unsigned)g->T[k]);
     g->dec = CellDecode{make_fastdiv((unsigned)d.nx), make_fastdiv((unsigned)d.ny)};
     if (d.block_particles > 0) g->P = d.block_particles;
-    g->R = fold_rounds(d);
     g->K = d.sort_interval > 1 ? d.sort_interval : 1;
     {
         // a particle moves less than c dt / h cells per step (Courant limit)
@@ -538,11 +557,7 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     }
     // shrink the margin until the tile's boxes fit in shared memory; particles
     // that drift further take the global-memory path
-    auto smem_for = [&](const int* m) {
-        long long G = 1, H = 1;
-        for (int k = 0; k < d.dim; ++k) { G *= g->T[k] + 2 * m[k] + 4; H *= g->T[k] + 2 * m[k] + 5; }
-        return (size_t)((6 * G + 3) & ~3LL) * 4 + (size_t)((3 * H + 3) & ~3LL) * 12 + (d.dim == 3 ? (size_t)kStageBytes : (size_t)kPrefBytes);
-    };
+    auto smem_for = [&](const int* m) { return (size_t)tile_smem(d.dim, g->T, m).words * 4; };
     while (smem_for(g->m) > 227 * 1024 && (g->m[0] > 0 || g->m[1] > 0 || g->m[2] > 0))
         for (int k = 0; k < 3; ++k) g->m[k] = g->m[k] > 0 ? g->m[k] - 1 : 0;
     {
@@ -1306,7 +1321,7 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
                 so.mv[b] = MoveFP32{src, dst, g->d.dim};
                 Tiles t{};
                 for (int d = 0; d < 3; ++d) { t.T[d] = g->T[d]; t.nt[d] = g->nt[d]; t.m[d] = g->m[d]; t.fT[d] = g->fT[d]; }
-                t.start = s.d_start; t.items = s.d_items; t.nitems = s.d_nitems; t.P = g->P; t.R = g->R;
+                t.start = s.d_start; t.items = s.d_items; t.nitems = s.d_nitems; t.P = g->P; t.bmax = move_bound(g, s); t.R = fold_rounds(g->d);
                 box_divisors(g, t);
                 t.next_count = s.d_count; t.esc = s.d_esc; t.nesc = s.d_nesc;
                 // the push runs after the step's sort flipped the parity: it

@@ -106,14 +106,16 @@ template <int ORDER> struct NodeW;
 
 template <> struct NodeW<1> {
     int base; float w[2];
-    __device__ inline NodeW(int lc, float f) {
+    __device__ __forceinline__ static int base_of(int lc, float) { return lc; }
+    __device__ __forceinline__ NodeW(int lc, float f) {
         base = lc; w[0] = __fsub_rn(1.0f, f); w[1] = f;
     }
 };
 
 template <> struct NodeW<2> {
     int base; float w[3];
-    __device__ inline NodeW(int lc, float f) {
+    __device__ __forceinline__ static int base_of(int lc, float f) { return f < 0.5f ? lc - 1 : lc; }
+    __device__ __forceinline__ NodeW(int lc, float f) {
         float d;
         if (f < 0.5f) { base = lc - 1; d = f; }
         else          { base = lc;     d = __fsub_rn(f, 1.0f); }   // exact for f in [0.5, 1)
@@ -129,7 +131,7 @@ template <int ORDER> struct HalfW;
 
 template <> struct HalfW<1> {
     int base; float w[2];
-    __device__ inline HalfW(int lc, float f) {
+    __device__ __forceinline__ HalfW(int lc, float f) {
         float t;
         if (f >= 0.5f) { base = lc; t = f - 0.5f; } else { base = lc - 1; t = f + 0.5f; }
         w[0] = 1.0f - t; w[1] = t;
@@ -138,7 +140,7 @@ template <> struct HalfW<1> {
 
 template <> struct HalfW<2> {
     int base; float w[3];
-    __device__ inline HalfW(int lc, float f) {
+    __device__ __forceinline__ HalfW(int lc, float f) {
         const float d = f - 0.5f;           // distance to half node lc (position lc + 1/2)
         base = lc - 1;
         const float a = 0.5f - d, b = 0.5f + d;
@@ -185,7 +187,7 @@ __device__ inline void boris(R& ux, R& uy, R& uz, R k, R ex, R ey, R ez, R bx, R
 
 // FP32 Boris with hardware reciprocal square root and fast division (a few
 // ulp, within the FP32 path's error budget).
-__device__ inline void boris_f32(float& ux, float& uy, float& uz, float k, float ex, float ey,
+__device__ __forceinline__ void boris_f32(float& ux, float& uy, float& uz, float k, float ex, float ey,
                                  float ez, float bx, float by, float bz) {
     const float mx = ux + k * ex, my = uy + k * ey, mz = uz + k * ez;
     const float kg = k * rsqrtf(1.0f + mx * mx + my * my + mz * mz);

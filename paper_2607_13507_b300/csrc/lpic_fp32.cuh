@@ -27,18 +27,10 @@
 // integers that follow the 1D shapes to within a unit or two.  Weights are
 // computed from the stored (cell, offset) pair with explicitly rounded
 // arithmetic, so the charge at the end of one step's path is bit-identical
-// to the charge at the start of the next step's path.  The Esirkepov weights
-// W_d (Sec. 3.1) are quantised with closures that make the integer current
-// a valid flow for the integer charge change dQ = Q1 - Q0:
-//   2D: W_x = rint(s DS_x A_y) except the last column (b), fixed so that
-//       sum_b W_x(a, .) = M(a) = qx1(a) - qx0(a), and the last row (a), fixed
-//       so that sum_a W_x(., b) = 0; W_y = dQ - W_x.
-//   3D: the same construction on the column sums over c (targets X, Y for
-//       sum_c W_x, sum_c W_y with X + Y = qxy1 - qxy0), then W_x, W_y per node
-//       with closures along c (to X, Y) and along a / b (to 0);
-//       W_z = dQ - W_x - W_y.
-// J_d is then the running sum of -W_d along d and satisfies, node by node,
-// J_d(i+1/2) - J_d(i-1/2) summed over d = -(Q1 - Q0) exactly.
+// to the charge at the start of the next step's path.  The Esirkepov fluxes
+// (Sec. 3.1) are rounded directly and closed level by level (1D flow, 2D
+// column sums, 3D nodes; see the deposit below), so that node by node
+// sum_d J_d(i+1/2) - J_d(i-1/2) = -(Q1 - Q0) exactly.
 #pragma once
 #include "lpic_common.cuh"
 
@@ -61,7 +53,8 @@ struct Tiles {
     const int2* items;   // (tile, chunk) work items
     const int* nitems;   // device count of work items
     int P;               // particles per chunk
-    int R;               // rounds between folds of the int32 current box
+    unsigned bmax;       // 3D: bound of one move's current at any node, units of 256 (int32 box guard)
+    int R;               // 2D: rounds of 256 moves between folds of the int32 current boxes
     FastDiv fT[3];       // division by T (tile keys of the next sort)
     FastDiv fG0, fG1, fF;  // division by the field box rows, planes, size
     FastDiv fH0, fH1, fJ;  // and by those of the current box
@@ -71,7 +64,7 @@ struct Tiles {
 };
 
 template <int ORDER, class W>
-__device__ inline void place32(float (&S)[ORDER + 2], const W& w, int off) {
+__device__ __forceinline__ void place32(float (&S)[ORDER + 2], const W& w, int off) {
 #pragma unroll
     for (int a = 0; a < ORDER + 2; ++a) {
         const float lo = (a <= ORDER) ? w.w[a < ORDER + 1 ? a : 0] : 0.0f;
@@ -80,16 +73,21 @@ __device__ inline void place32(float (&S)[ORDER + 2], const W& w, int off) {
     }
 }
 
-// Adds a lane's value to the int32 round box with a native 32-bit atomic.
-// SKIP_ZERO: only nonzero values (2D: slowly moving particles leave most
-// window values at zero and lanes of one cell would otherwise all hit the same
-// addresses; 3D: most values are nonzero and the test costs more than it saves
-// -- both measured).
+// Adds a lane's value to the int32 current box with a shared-memory
+// reduction.  SKIP_ZERO: predicated on a nonzero value, without a branch (2D:
+// slowly moving particles leave most window values at zero; 3D: most values
+// are nonzero).
 template <bool SKIP_ZERO>
 struct Acc32 {
     int* sJ;
-    __device__ inline void operator()(int idx, int v) const {
-        if (!SKIP_ZERO || v != 0) atomicAdd(sJ + idx, v);
+    __device__ __forceinline__ void operator()(int idx, int v) const {
+        if constexpr (SKIP_ZERO) {
+            const unsigned a = (unsigned)__cvta_generic_to_shared(sJ + idx);
+            asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}"
+                         :: "r"(a), "r"(v));
+        } else {
+            atomicAdd(sJ + idx, v);
+        }
     }
 };
 
@@ -119,258 +117,327 @@ __device__ inline void charge_levels_2d(const int (&qx)[WN], const float (&Sy)[W
     }
 }
 
-// ----------------------------------------------------------- 2D deposit
-// The construction on a window of WN nodes per dimension starting at
-// (basex, basey); the start/end stencils sit at offsets o0*/o1* in it.
-// Node (a, b) of component c lives at c * jsz + (b + 2) * H0 + (a + 2) of the
-// box (coordinates relative to the box's local frame).
-// The rounding residuals of W_x go to row cx and column cy: the stencil's
-// last node where both stencils coincide in that dimension (so that the
-// window size never changes the integers), else the window's last node.
-template <int ORDER, int WN, class Acc>
-__device__ inline void deposit2d_core(const Acc& acc, int jsz, int H0, int basex, int basey, int o0x,
-                                      int o1x, int o0y, int o1y, int cx, int cy,
-                                      const float (&S0x)[WN], const float (&S1x)[WN],
-                                      const float (&S0y)[WN], const float (&S1y)[WN], float s, float vz) {
-    const int sint = rint22(s);
-    int qx0[WN], qx1[WN], dQ[WN][WN], M[WN];
-    {
-        int qxy0[WN][WN], qxy1[WN][WN];
-        charge_levels_1d<WN>(s, sint, S0x, o0x, qx0);
-        charge_levels_1d<WN>(s, sint, S1x, o1x, qx1);
-        charge_levels_2d<WN>(qx0, S0y, o0y, qxy0);
-        charge_levels_2d<WN>(qx1, S1y, o1y, qxy1);
-#pragma unroll
-        for (int a = 0; a < WN; ++a) {
-            M[a] = qx1[a] - qx0[a];
-#pragma unroll
-            for (int b = 0; b < WN; ++b) dQ[a][b] = qxy1[a][b] - qxy0[a][b];
-        }
-    }
+// ----------------------------------------------------------- deposit (Sec. 3.1)
+// Integer Esirkepov current of one move, written directly as fluxes.
+//
+// Window of WN nodes per dimension (WN = ORDER + 1: both stencils start at
+// the same node; WN = ORDER + 2: they differ by one in some dimension), the
+// start / end stencils at offsets o0 / o1 in it.  With A = (S0 + S1) / 2,
+// DS = S1 - S0 and C(a) = sum_{a' <= a} DS(a') per dimension, the exact
+// Esirkepov fluxes are J_x(a+1/2, b, c) = -s C_x(a) (A_y A_z + DS_y DS_z / 12)
+// and cyclically (2D: J_x = -s C_x(a) A_y(b), J_y likewise).  The integer
+// construction, level by level:
+//   1D: the x flow Mx(a+1/2) = -sum_{a' <= a} (qx1 - qx0)(a').
+//   2D: X(a+1/2, b) = rint(-s C_x(a) A_y(b)) except on the closure column
+//       b = cy, fixed so that sum_b X(a+1/2, .) = Mx(a+1/2); Y(a, b+1/2) is
+//       the running sum over b of -(dqxy + X(a+1/2) - X(a-1/2)), which closes
+//       to zero at the window's end because every row sum of X is the 1D flow.
+//       (In 2D X and Y are the currents J_x and J_y.)
+//   3D: J_x(a+1/2, b, c) = rint(-s C_x(a) K_x(b, c)) except on c = cz, fixed
+//       so that sum_c J_x = X(a+1/2, b); J_y likewise with sum_c J_y =
+//       Y(a, b+1/2); J_z(a, b, c+1/2) is the running sum over c of
+//       -(dQ + dJ_x/dx + dJ_y/dy), which closes at both window ends.
+// The closure column of each dimension is the stencil's last node when both
+// stencils start at the same node in that dimension, else the window's last
+// node, and every rounded value off the stencils is rint(0) = 0: a
+// same-stencil move gives identical integers in both window sizes.  Node by
+// node, sum_d J_d(+1/2) - J_d(-1/2) = -(Q1 - Q0) exactly.
 
-    float DSx[WN], DSy[WN], Ax[WN], Ay[WN];
+constexpr float kRound = 12582912.0f;      // 1.5 * 2^23
+// nearest integer of a * b (|a b| < 2^22)
+__device__ __forceinline__ int irnd_mul(float a, float b) { return __float_as_int(__fmaf_rn(a, b, kRound)) - 0x4B400000; }
+
+// One level of the hierarchical charge: out[k] = rint(scale S[k]) except at
+// the stencil's index 1 (window index o + 1), which takes total - the sum of
+// the others (the same integers as charge_levels_1d / _2d).
+template <int WN, bool FIXED>
+__device__ __forceinline__ void leveli(float scale, int total, const float (&S)[WN], int o, int (&out)[WN]) {
+    if constexpr (FIXED) {
+        int sum = 0;
 #pragma unroll
-    for (int a = 0; a < WN; ++a) {
-        DSx[a] = S1x[a] - S0x[a]; DSy[a] = S1y[a] - S0y[a];
-        Ax[a] = 0.5f * (S0x[a] + S1x[a]); Ay[a] = 0.5f * (S0y[a] + S1y[a]);
-    }
-    // W_x with closures on row cx and column cy; W_y = dQ - W_x
-    int Wx[WN][WN];
+        for (int k = 0; k < WN; ++k)
+            if (k != 1) { out[k] = irnd_mul(scale, S[k]); sum += out[k]; }
+        out[1] = total - sum;
+    } else {
+        int sum = 0;
 #pragma unroll
-    for (int a = 0; a < WN; ++a) {
-        int row = 0;
-        const float sdx = s * DSx[a];
+        for (int k = 0; k < WN; ++k) { out[k] = irnd_mul(scale, S[k]); sum += out[k]; }
 #pragma unroll
-        for (int b = 0; b < WN; ++b) {
-            const int v = (b == cy) ? 0 : rint22_mul(sdx, Ay[b]);
-            Wx[a][b] = v; row += v;
-        }
-#pragma unroll
-        for (int b = 0; b < WN; ++b)
-            if (b == cy) Wx[a][b] = M[a] - row;
-    }
-#pragma unroll
-    for (int b = 0; b < WN; ++b) {
-        int col = 0;
-#pragma unroll
-        for (int a = 0; a < WN; ++a) col += (a == cx) ? 0 : Wx[a][b];
-#pragma unroll
-        for (int a = 0; a < WN; ++a)
-            if (a == cx) Wx[a][b] = -col;
-    }
-    // J_x: running sum along a; J_y: running sum along b
-#pragma unroll
-    for (int b = 0; b < WN; ++b) {
-        int run = 0;
-#pragma unroll
-        for (int a = 0; a < WN - 1; ++a) {
-            run -= Wx[a][b];
-            acc((basey + b + 2) * H0 + (basex + a + 2), run);
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < WN; ++a) {
-        int run = 0;
-#pragma unroll
-        for (int b = 0; b < WN - 1; ++b) {
-            run -= dQ[a][b] - Wx[a][b];
-            acc(jsz + (basey + b + 2) * H0 + (basex + a + 2), run);
-        }
-    }
-    // J_z: s v_z W_z, W_z = A_x A_y + DS_x DS_y / 12 (needs no closure in 2D,
-    // so any fixed integer rounding of it will do: the DS term is rounded to an
-    // integer first, then the sum)
-    const float svz = s * vz, svz12 = svz * (1.0f / 12.0f);
-#pragma unroll
-    for (int a = 0; a < WN; ++a) {
-        const float pa = svz * Ax[a], qa = svz12 * DSx[a];
-#pragma unroll
-        for (int b = 0; b < WN; ++b) {
-            const float t = __fmaf_rn(qa, DSy[b], 12582912.0f);
-            acc(2 * jsz + (basey + b + 2) * H0 + (basex + a + 2),
-                __float_as_int(__fmaf_rn(pa, Ay[b], t)) - 0x4B400000);
-        }
+        for (int k = 0; k < WN; ++k)
+            if (k == o + 1) out[k] += total - sum;
     }
 }
 
-// General case: the window of ORDER + 2 nodes holds both stencils.
+// 2D.  SAME: WN = ORDER + 1 and all offsets 0 (compile-time closures).
+// Node (a, b) of component c lives at c * jsz + n0 + b * H0 + a of the box.
+// Evaluated column by column in x, so that only the previous column's J_x
+// crosses columns.
+template <int ORDER, int WN, bool SAME, class Acc>
+__device__ __forceinline__ void deposit2d_core(const Acc& acc, int jsz, int H0, int n0, int o0x, int o1x, int o0y,
+                                      int o1y, const float (&S0x)[WN], const float (&S1x)[WN],
+                                      const float (&S0y)[WN], const float (&S1y)[WN], float s, float vz) {
+    constexpr int L = WN - 1;
+    const int S = rint22(s);
+    int qx0[WN], qx1[WN];
+    leveli<WN, SAME>(s, S, S0x, o0x, qx0);
+    leveli<WN, SAME>(s, S, S1x, o1x, qx1);
+    const int cy = SAME ? ORDER : ((o0y == o1y) ? o0y + ORDER : L);
+    const float svz = s * vz, svz12 = svz * (1.0f / 12.0f);
+    int jxp[WN];                       // J_x(a - 1/2, b)
+#pragma unroll
+    for (int b = 0; b < WN; ++b) jxp[b] = 0;
+    float Cx = 0.0f;
+    int Mx = 0;
+#pragma unroll
+    for (int a = 0; a < WN; ++a) {
+        // J_x(a+1/2, b) with the closure column cy
+        int jx[WN];
+        if (a < L) {
+            Cx = Cx + (S1x[a] - S0x[a]);
+            Mx += qx0[a] - qx1[a];
+            const float sc = -s * Cx;
+            int row = 0;
+#pragma unroll
+            for (int b = 0; b < WN; ++b) {
+                jx[b] = (b == cy) ? 0 : irnd_mul(sc, 0.5f * (S0y[b] + S1y[b]));
+                row += jx[b];
+            }
+#pragma unroll
+            for (int b = 0; b < WN; ++b)
+                if (b == cy) jx[b] = Mx - row;
+#pragma unroll
+            for (int b = 0; b < WN; ++b) acc(n0 + b * H0 + a, jx[b]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < WN; ++b) jx[b] = 0;
+        }
+        // J_y(a, b+1/2), b < L: running sums of -(dq + dJ_x)
+        int r0[WN], r1[WN];
+        leveli<WN, SAME>((float)qx0[a], qx0[a], S0y, o0y, r0);
+        leveli<WN, SAME>((float)qx1[a], qx1[a], S1y, o1y, r1);
+        int run = 0;
+#pragma unroll
+        for (int b = 0; b < L; ++b) {
+            run -= (r1[b] - r0[b]) + jx[b] - jxp[b];
+            acc(jsz + n0 + b * H0 + a, run);
+        }
+        // J_z: s v_z W_z, W_z = A_x A_y + DS_x DS_y / 12 (no closure in 2D; the
+        // DS term is added to the rounding constant first, then the A term)
+        const float pa = svz * (0.5f * (S0x[a] + S1x[a])), qa = svz12 * (S1x[a] - S0x[a]);
+#pragma unroll
+        for (int b = 0; b < WN; ++b) {
+            const float t = __fmaf_rn(qa, S1y[b] - S0y[b], kRound);
+            acc(2 * jsz + n0 + b * H0 + a,
+                __float_as_int(__fmaf_rn(pa, 0.5f * (S0y[b] + S1y[b]), t)) - 0x4B400000);
+        }
+#pragma unroll
+        for (int b = 0; b < WN; ++b) jxp[b] = jx[b];
+    }
+}
+
+// From the start and end stencils' weights: SAME (both start at the same
+// node in both dimensions) uses the stencil-sized window, else the window of
+// ORDER + 2 nodes.
+template <int ORDER, bool SAME, class Acc>
+__device__ __forceinline__ void deposit2d_w(const Acc& acc, int jsz, int H0, const NodeW<ORDER>& ax, const NodeW<ORDER>& ay,
+                                   const NodeW<ORDER>& bx, const NodeW<ORDER>& by, float s, float vz) {
+    if constexpr (SAME) {
+        constexpr int WN = ORDER + 1;
+        float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
+#pragma unroll
+        for (int a = 0; a < WN; ++a) { S0x[a] = ax.w[a]; S1x[a] = bx.w[a]; S0y[a] = ay.w[a]; S1y[a] = by.w[a]; }
+        deposit2d_core<ORDER, WN, true>(acc, jsz, H0, (ay.base + 2) * H0 + ax.base + 2, 0, 0, 0, 0, S0x, S1x,
+                                        S0y, S1y, s, vz);
+    } else {
+        constexpr int WN = ORDER + 2;
+        const int basex = min(ax.base, bx.base), basey = min(ay.base, by.base);
+        const int o0x = ax.base - basex, o1x = bx.base - basex;
+        const int o0y = ay.base - basey, o1y = by.base - basey;
+        float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
+        place32<ORDER>(S0x, ax, o0x); place32<ORDER>(S1x, bx, o1x);
+        place32<ORDER>(S0y, ay, o0y); place32<ORDER>(S1y, by, o1y);
+        deposit2d_core<ORDER, WN, false>(acc, jsz, H0, (basey + 2) * H0 + basex + 2, o0x, o1x, o0y, o1y, S0x,
+                                         S1x, S0y, S1y, s, vz);
+    }
+}
+
+// General case from (cell, offset) pairs: the window of ORDER + 2 nodes.
 template <int ORDER, class Acc>
-__device__ inline void deposit2d(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
+__device__ __forceinline__ void deposit2d(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
                                  const int* ce, const float* fe, float s, float vz) {
-    constexpr int WN = ORDER + 2;
-    const NodeW<ORDER> ax(lc[0], f[0]), ay(lc[1], f[1]), bx(ce[0], fe[0]), by(ce[1], fe[1]);
-    const int basex = min(ax.base, bx.base), basey = min(ay.base, by.base);
-    const int o0x = ax.base - basex, o1x = bx.base - basex;
-    const int o0y = ay.base - basey, o1y = by.base - basey;
-    float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
-    place32<ORDER>(S0x, ax, o0x); place32<ORDER>(S1x, bx, o1x);
-    place32<ORDER>(S0y, ay, o0y); place32<ORDER>(S1y, by, o1y);
-    const int cx = (o0x == o1x) ? o0x + ORDER : WN - 1;
-    const int cy = (o0y == o1y) ? o0y + ORDER : WN - 1;
-    deposit2d_core<ORDER, WN>(acc, jsz, H0, basex, basey, o0x, o1x, o0y, o1y, cx, cy, S0x, S1x, S0y, S1y,
-                              s, vz);
+    deposit2d_w<ORDER, false>(acc, jsz, H0, NodeW<ORDER>(lc[0], f[0]), NodeW<ORDER>(lc[1], f[1]),
+                              NodeW<ORDER>(ce[0], fe[0]), NodeW<ORDER>(ce[1], fe[1]), s, vz);
 }
 
 // Both stencils start at the same node in both dimensions (the particle kept
 // its nearest node): the window is the stencil itself, ORDER + 1 nodes.
 template <int ORDER, class Acc>
-__device__ inline void deposit2d_same(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
+__device__ __forceinline__ void deposit2d_same(const Acc& acc, int jsz, int H0, const int* lc, const float* f,
                                       const int* ce, const float* fe, float s, float vz) {
-    constexpr int WN = ORDER + 1;
-    const NodeW<ORDER> ax(lc[0], f[0]), ay(lc[1], f[1]), bx(ce[0], fe[0]), by(ce[1], fe[1]);
-    float S0x[WN], S1x[WN], S0y[WN], S1y[WN];
-#pragma unroll
-    for (int a = 0; a < WN; ++a) { S0x[a] = ax.w[a]; S1x[a] = bx.w[a]; S0y[a] = ay.w[a]; S1y[a] = by.w[a]; }
-    deposit2d_core<ORDER, WN>(acc, jsz, H0, ax.base, ay.base, 0, 0, 0, 0, ORDER, ORDER, S0x, S1x, S0y, S1y,
-                              s, vz);
+    deposit2d_w<ORDER, true>(acc, jsz, H0, NodeW<ORDER>(lc[0], f[0]), NodeW<ORDER>(lc[1], f[1]),
+                             NodeW<ORDER>(ce[0], fe[0]), NodeW<ORDER>(ce[1], fe[1]), s, vz);
 }
 
-// ----------------------------------------------------------- 3D deposit
-// Same construction as the 2D deposit one level up, evaluated slab by slab
-// in y (b) so that only the closure sums cross slabs: X(a, b) (target of
-// sum_c W_x) per slab with running row sums, W_y(a, b, c) with running sums
-// over b (their negative is J_y), and W_z = dQ - W_x - W_y inside the slab.
-// Window of WN nodes per dimension from (bs0, bs1, bs2); the start/end
-// stencils sit at offsets o*0 / o*1 in it; residuals go to the window's last
-// node.
-template <int ORDER, int WN, class Acc>
-__device__ inline void deposit3d_core(const Acc& acc, int jsz, int H0, int H1, int bs0, int bs1, int bs2,
+// 3D.  Node (a, b, c) of component k lives at k * jsz + n0 + (c H1 + b) H0 + a.
+// Evaluated slab by slab in x and column by column in y inside a slab, so
+// that only the previous slab's J_x, the previous column's J_y and the
+// previous slab's X cross.  SAME: WN = ORDER + 1, all offsets 0; then the 3D
+// charge level is needed only off the stencil's index 1 (J_z runs forward
+// below it and backward above it).
+template <int ORDER, int WN, bool SAME, class Acc>
+__device__ __forceinline__ void deposit3d_core(const Acc& acc, int jsz, int H0, int H1, int n0,
                                       int ox0, int ox1, int oy0, int oy1, int oz0, int oz1,
                                       const float (&S0x)[WN], const float (&S1x)[WN],
                                       const float (&S0y)[WN], const float (&S1y)[WN],
                                       const float (&S0z)[WN], const float (&S1z)[WN], float s) {
     constexpr int L = WN - 1;
-    const int sint = rint22(s);
-
-    int qx0[WN], qx1[WN], qxy0[WN][WN], qxy1[WN][WN];
-    charge_levels_1d<WN>(s, sint, S0x, ox0, qx0);
-    charge_levels_1d<WN>(s, sint, S1x, ox1, qx1);
-    charge_levels_2d<WN>(qx0, S0y, oy0, qxy0);
-    charge_levels_2d<WN>(qx1, S1y, oy1, qxy1);
-
-    int xrow[WN];          // running sum over b of X(a, b), a < L
-    int wys[WN][WN];       // running sum over b of W_y(a, b, c)
-#pragma unroll
-    for (int a = 0; a < WN; ++a) {
-        xrow[a] = 0;
-#pragma unroll
-        for (int c = 0; c < WN; ++c) wys[a][c] = 0;
-    }
-    float sdx[WN], Az[WN], DSz[WN];
-#pragma unroll
-    for (int a = 0; a < WN; ++a) {
-        sdx[a] = s * (S1x[a] - S0x[a]);
-        Az[a] = 0.5f * (S0z[a] + S1z[a]); DSz[a] = S1z[a] - S0z[a];
-    }
+    const int P = H0 * H1;
+    const int S = rint22(s);
+    int qx0[WN], qx1[WN];
+    leveli<WN, SAME>(s, S, S0x, ox0, qx0);
+    leveli<WN, SAME>(s, S, S1x, ox1, qx1);
+    const int cy = SAME ? ORDER : ((oy0 == oy1) ? oy0 + ORDER : L);
+    const int cz = SAME ? ORDER : ((oz0 == oz1) ? oz0 + ORDER : L);
+    int Xp[WN];                        // X(a - 1/2, b)
+    // SAME: J_x(a - 1/2, b, c) kept for the next slab's J_z; otherwise each
+    // J_x column's running sum over c is added to the next slab's J_z at once
+    // (fewer live registers for the larger window)
+    int jxp[SAME ? WN : 1][SAME ? WN : 1];
 #pragma unroll
     for (int b = 0; b < WN; ++b) {
-        const float ay = 0.5f * (S0y[b] + S1y[b]), dsy = S1y[b] - S0y[b];
-        const float sdy = s * dsy, dsy12 = dsy * (1.0f / 12.0f);
-        // X(., b) with its closures; Y(., b) = Z(., b) - X(., b)
+        Xp[b] = 0;
+        if constexpr (SAME) {
+#pragma unroll
+            for (int c = 0; c < WN; ++c) jxp[b][c] = 0;
+        }
+    }
+    float Cx = 0.0f;
+    int Mx = 0;
+#pragma unroll
+    for (int a = 0; a < WN; ++a) {
+        // 2D charges of slab a, X(a+1/2, .) with the closure column cy
+        int r0[WN], r1[WN];
+        leveli<WN, SAME>((float)qx0[a], qx0[a], S0y, oy0, r0);
+        leveli<WN, SAME>((float)qx1[a], qx1[a], S1y, oy1, r1);
         int X[WN];
-        {
-            int col = 0;
+        float sCx = 0.0f;
+        if (a < L) {
+            Cx = Cx + (S1x[a] - S0x[a]);
+            Mx += qx0[a] - qx1[a];
+            sCx = -s * Cx;
+            int row = 0;
 #pragma unroll
-            for (int a = 0; a < L; ++a) {
-                const int v = (b < L) ? rint22_mul(sdx[a], ay) : (qx1[a] - qx0[a]) - xrow[a];
-                X[a] = v; xrow[a] += v; col += v;
-            }
-            X[L] = -col;
-        }
-        // dQ of the slab (levels continued along z with the column remainders)
-        int dq[WN][WN];
-#pragma unroll
-        for (int a = 0; a < WN; ++a) {
-            const float f0 = (float)qxy0[a][b], f1 = (float)qxy1[a][b];
-            int sum0 = 0, sum1 = 0;
-#pragma unroll
-            for (int c = 0; c < WN; ++c) {
-                const int q0 = rint22_mul(f0, S0z[c]);
-                const int q1 = rint22_mul(f1, S1z[c]);
-                dq[a][c] = q1 - q0; sum0 += q0; sum1 += q1;
+            for (int b = 0; b < WN; ++b) {
+                X[b] = (b == cy) ? 0 : irnd_mul(sCx, 0.5f * (S0y[b] + S1y[b]));
+                row += X[b];
             }
 #pragma unroll
-            for (int c = 0; c < WN; ++c)
-                dq[a][c] += ((c == oz1 + 1) ? qxy1[a][b] - sum1 : 0) - ((c == oz0 + 1) ? qxy0[a][b] - sum0 : 0);
+            for (int b = 0; b < WN; ++b)
+                if (b == cy) X[b] = Mx - row;
+        } else {
+#pragma unroll
+            for (int b = 0; b < WN; ++b) X[b] = 0;
         }
-        // W_x(a, b, c) = s DS_x(a) (A_y A_z + DS_y DS_z / 12); J_x runs along a
-        {
-            int cs[WN];
+        const float ax = 0.5f * (S0x[a] + S1x[a]), dx12 = (S1x[a] - S0x[a]) * (1.0f / 12.0f);
+        int Y = 0;                     // Y(a, b+1/2), running over b
+        float Cy = 0.0f;
+        int jyp[WN];                   // J_y(a, b - 1/2, c)
 #pragma unroll
-            for (int a = 0; a < WN; ++a) cs[a] = 0;
+        for (int c = 0; c < WN; ++c) jyp[c] = 0;
 #pragma unroll
-            for (int c = 0; c < WN; ++c) {
-                const float kyz = __fmaf_rn(ay, Az[c], dsy12 * DSz[c]);
-                int colsum = 0, run = 0;
+        for (int b = 0; b < WN; ++b) {
+            const int nb = n0 + b * H0 + a;
+            // J_x(a+1/2, b, c) with the closure row cz: sum_c = X(a+1/2, b)
+            int jx[WN];
+            if (a < L) {
+                const float ay = 0.5f * (S0y[b] + S1y[b]), dy12 = (S1y[b] - S0y[b]) * (1.0f / 12.0f);
+                int col = 0;
 #pragma unroll
-                for (int a = 0; a < L; ++a) {
-                    const int v = (c < L) ? rint22_mul(sdx[a], kyz) : X[a] - cs[a];
-                    cs[a] += v; colsum += v;
-                    dq[a][c] -= v;
-                    run -= v;
-                    acc(((bs2 + c + 2) * H1 + (bs1 + b + 2)) * H0 + (bs0 + a + 2), run);
+                for (int c = 0; c < WN; ++c) {
+                    jx[c] = (c == cz) ? 0 : irnd_mul(sCx, __fmaf_rn(ay, 0.5f * (S0z[c] + S1z[c]), dy12 * (S1z[c] - S0z[c])));
+                    col += jx[c];
                 }
-                dq[L][c] += colsum;
-            }
-        }
-        // W_y(a, b, c) = s DS_y(b) (A_x A_z + DS_x DS_z / 12) with sum_c W_y = Y(a, b);
-        // the last slab closes sum_b W_y = 0.  J_y is minus the running sum over b.
 #pragma unroll
-        for (int a = 0; a < WN; ++a) {
-            const float ax = 0.5f * (S0x[a] + S1x[a]), dsx12 = (S1x[a] - S0x[a]) * (1.0f / 12.0f);
-            const int Y = (qxy1[a][b] - qxy0[a][b]) - X[a];
-            int cs = 0;
+                for (int c = 0; c < WN; ++c) {
+                    if (c == cz) jx[c] = X[b] - col;
+                    acc(nb + c * P, jx[c]);
+                }
+                if constexpr (!SAME) {
+                    // -J_x(a+1/2) enters D of slab a + 1: its running sum over c,
+                    // with the sign of J_z = -sum D, goes to J_z(a + 1, b, .)
+                    int px = 0;
+#pragma unroll
+                    for (int c = 0; c < L; ++c) {
+                        px += jx[c];
+                        acc(2 * jsz + nb + 1 + c * P, px);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < WN; ++c) jx[c] = 0;
+            }
+            // J_y(a, b+1/2, c) with the closure row cz: sum_c = Y(a, b+1/2)
+            int jy[WN];
+            if (b < L) {
+                Y -= (r1[b] - r0[b]) + X[b] - Xp[b];
+                Cy = Cy + (S1y[b] - S0y[b]);
+                const float sCy = -s * Cy;
+                int col = 0;
+#pragma unroll
+                for (int c = 0; c < WN; ++c) {
+                    jy[c] = (c == cz) ? 0 : irnd_mul(sCy, __fmaf_rn(ax, 0.5f * (S0z[c] + S1z[c]), dx12 * (S1z[c] - S0z[c])));
+                    col += jy[c];
+                }
+#pragma unroll
+                for (int c = 0; c < WN; ++c) {
+                    if (c == cz) jy[c] = Y - col;
+                    acc(jsz + nb + c * P, jy[c]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < WN; ++c) jy[c] = 0;
+            }
+            // J_z(a, b, c+1/2): D(c) = dQ + J_x(a+1/2) - J_x(a-1/2) + J_y(b+1/2) - J_y(b-1/2)
+            if constexpr (SAME) {
+                int fw = 0;
+#pragma unroll
+                for (int c = 0; c < 1; ++c) {
+                    const int dq = irnd_mul((float)r1[b], S1z[c]) - irnd_mul((float)r0[b], S0z[c]);
+                    fw -= dq + jx[c] - jxp[b][c] + jy[c] - jyp[c];
+                    acc(2 * jsz + nb + c * P, fw);
+                }
+                int bw = 0;
+#pragma unroll
+                for (int c = L; c >= 2; --c) {
+                    const int dq = irnd_mul((float)r1[b], S1z[c]) - irnd_mul((float)r0[b], S0z[c]);
+                    bw += dq + jx[c] - jxp[b][c] + jy[c] - jyp[c];
+                    acc(2 * jsz + nb + (c - 1) * P, bw);
+                }
+            } else {
+                int z0[WN], z1[WN];
+                leveli<WN, false>((float)r0[b], r0[b], S0z, oz0, z0);
+                leveli<WN, false>((float)r1[b], r1[b], S1z, oz1, z1);
+                int fw = 0;
+#pragma unroll
+                for (int c = 0; c < L; ++c) {
+                    fw -= (z1[c] - z0[c]) + jx[c] + jy[c] - jyp[c];
+                    acc(2 * jsz + nb + c * P, fw);
+                }
+            }
 #pragma unroll
             for (int c = 0; c < WN; ++c) {
-                int v;
-                if (b < L) {
-                    v = (c < L) ? rint22_mul(sdy, __fmaf_rn(ax, Az[c], dsx12 * DSz[c])) : Y - cs;
-                    cs += v;
-                    wys[a][c] += v;
-                    acc(jsz + ((bs2 + c + 2) * H1 + (bs1 + b + 2)) * H0 + (bs0 + a + 2), -wys[a][c]);
-                } else {
-                    v = -wys[a][c];
-                }
-                dq[a][c] -= v;
+                if constexpr (SAME) jxp[b][c] = jx[c];
+                jyp[c] = jy[c];
             }
         }
-        // W_z = what is left; J_z runs along c
 #pragma unroll
-        for (int a = 0; a < WN; ++a) {
-            int run = 0;
-#pragma unroll
-            for (int c = 0; c < L; ++c) {
-                run -= dq[a][c];
-                acc(2 * jsz + ((bs2 + c + 2) * H1 + (bs1 + b + 2)) * H0 + (bs0 + a + 2), run);
-            }
-        }
+        for (int b = 0; b < WN; ++b) Xp[b] = X[b];
     }
 }
 
-
 // General case: the window of ORDER + 2 nodes per dimension holds both stencils.
 template <int ORDER, class Acc>
-__device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const int* lc,
+__device__ __forceinline__ void deposit3d(const Acc& acc, int jsz, int H0, int H1, const int* lc,
                                  const float* f, const int* ce, const float* fe, float s) {
     constexpr int WN = ORDER + 2;
     const NodeW<ORDER> a0(lc[0], f[0]), a1(lc[1], f[1]), a2(lc[2], f[2]);
@@ -380,33 +447,40 @@ __device__ inline void deposit3d(const Acc& acc, int jsz, int H0, int H1, const 
     place32<ORDER>(S0x, a0, a0.base - bs0); place32<ORDER>(S1x, b0, b0.base - bs0);
     place32<ORDER>(S0y, a1, a1.base - bs1); place32<ORDER>(S1y, b1, b1.base - bs1);
     place32<ORDER>(S0z, a2, a2.base - bs2); place32<ORDER>(S1z, b2, b2.base - bs2);
-    deposit3d_core<ORDER, WN>(acc, jsz, H0, H1, bs0, bs1, bs2, a0.base - bs0, b0.base - bs0,
-                              a1.base - bs1, b1.base - bs1, a2.base - bs2, b2.base - bs2,
-                              S0x, S1x, S0y, S1y, S0z, S1z, s);
+    deposit3d_core<ORDER, WN, false>(acc, jsz, H0, H1, ((bs2 + 2) * H1 + bs1 + 2) * H0 + bs0 + 2,
+                                     a0.base - bs0, b0.base - bs0, a1.base - bs1, b1.base - bs1,
+                                     a2.base - bs2, b2.base - bs2, S0x, S1x, S0y, S1y, S0z, S1z, s);
 }
 
 // Both stencils start at the same node in every dimension: the window is the
-// stencil itself, ORDER + 1 nodes per dimension.
+// stencil itself, ORDER + 1 nodes per dimension (from the stencils' weights).
 template <int ORDER, class Acc>
-__device__ inline void deposit3d_same(const Acc& acc, int jsz, int H0, int H1, const int* lc,
-                                      const float* f, const int* ce, const float* fe, float s) {
+__device__ __forceinline__ void deposit3d_w(const Acc& acc, int jsz, int H0, int H1, const NodeW<ORDER>& a0,
+                                   const NodeW<ORDER>& a1, const NodeW<ORDER>& a2, const NodeW<ORDER>& b0,
+                                   const NodeW<ORDER>& b1, const NodeW<ORDER>& b2, float s) {
     constexpr int WN = ORDER + 1;
-    const NodeW<ORDER> a0(lc[0], f[0]), a1(lc[1], f[1]), a2(lc[2], f[2]);
-    const NodeW<ORDER> b0(ce[0], fe[0]), b1(ce[1], fe[1]), b2(ce[2], fe[2]);
     float S0x[WN], S1x[WN], S0y[WN], S1y[WN], S0z[WN], S1z[WN];
 #pragma unroll
     for (int a = 0; a < WN; ++a) {
         S0x[a] = a0.w[a]; S1x[a] = b0.w[a]; S0y[a] = a1.w[a]; S1y[a] = b1.w[a];
         S0z[a] = a2.w[a]; S1z[a] = b2.w[a];
     }
-    deposit3d_core<ORDER, WN>(acc, jsz, H0, H1, a0.base, a1.base, a2.base, 0, 0, 0, 0, 0, 0,
-                              S0x, S1x, S0y, S1y, S0z, S1z, s);
+    deposit3d_core<ORDER, WN, true>(acc, jsz, H0, H1, ((a2.base + 2) * H1 + a1.base + 2) * H0 + a0.base + 2,
+                                    0, 0, 0, 0, 0, 0, S0x, S1x, S0y, S1y, S0z, S1z, s);
+}
+
+template <int ORDER, class Acc>
+__device__ __forceinline__ void deposit3d_same(const Acc& acc, int jsz, int H0, int H1, const int* lc,
+                                      const float* f, const int* ce, const float* fe, float s) {
+    deposit3d_w<ORDER>(acc, jsz, H0, H1, NodeW<ORDER>(lc[0], f[0]), NodeW<ORDER>(lc[1], f[1]),
+                       NodeW<ORDER>(lc[2], f[2]), NodeW<ORDER>(ce[0], fe[0]), NodeW<ORDER>(ce[1], fe[1]),
+                       NodeW<ORDER>(ce[2], fe[2]), s);
 }
 
 // Whether the start and end stencils of a move begin at the same node in
 // every dimension (then the stencil-sized window holds the whole deposit).
 template <int DIM, int ORDER>
-__device__ inline bool same_stencils(const int* lc, const float* f, const int* ce, const float* fe) {
+__device__ __forceinline__ bool same_stencils(const int* lc, const float* f, const int* ce, const float* fe) {
     bool same = true;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) same &= NodeW<ORDER>(lc[d], f[d]).base == NodeW<ORDER>(ce[d], fe[d]).base;
@@ -497,14 +571,14 @@ __device__ __forceinline__ void gather32(const Load& ld, const NodeW<ORDER>& nx_
 }
 
 // Field components staged in shared memory: box of G0 x G1 (x G2) nodes per
-// component with a halo of 2, local node (x, y, z) at ((z+2) G1 + y+2) G0 + x+2
-// (2D: y+2) G0 + x+2).
+// component from local node -1, local node (x, y, z) at ((z+1) G1 + y+1) G0 + x+1
+// (2D: (y+1) G0 + x+1).
 template <int DIM>
 struct LoadShared {
     const float* sF;
     int fsz, G0, G1;
     __device__ inline float operator()(int comp, int x, int y, int z) const {
-        return sF[comp * fsz + ((DIM == 3 ? z + 2 : 0) * G1 + (y + 2)) * G0 + (x + 2)];
+        return sF[comp * fsz + ((DIM == 3 ? z + 1 : 0) * G1 + (y + 1)) * G0 + (x + 1)];
     }
 };
 
@@ -525,67 +599,139 @@ struct LoadGlobal {
 };
 
 // ----------------------------------------------------------- the tile kernel
-// Shared memory: 6 field boxes (T+4 per dimension, halo 2 below and 2 above),
-// an int64 total box and an int32 round box for J (T+5 per dimension), then in
-// 3D the deposit staging and in 2D the particle prefetch buffers.
-// Blocks per SM the register allocation targets (2D: the kernel fits 80
-// registers with negligible spills; 3D: 128 registers, a few spills, measured
-// 1.57x faster than one block per SM at 255 registers).
+// Blocks per SM the register allocation targets (2D: 64 registers, 4 blocks
+// of 256; 3D: 80 registers, 3 blocks, which the shared memory of an 8x8x4
+// tile also allows).
 #ifndef LPIC_GPD2D_MINB
 #define LPIC_GPD2D_MINB 4
 #endif
 #ifndef LPIC_GPD3D_MINB
-#define LPIC_GPD3D_MINB 2
+#define LPIC_GPD3D_MINB 3
 #endif
 
-// Threads per block of the tile kernel, and the 3D deposit staging in shared
-// memory (words per slot: packed start cell, packed end-cell carries, start
-// offsets, end offsets, charge): 256 slots for a round's same-stencil moves
-// and a ring of 512 for the other moves, deposited 256 at a time.
+// Shared memory of one work item, in 4-byte words, each part 16-byte aligned:
+//   fields     6 boxes of G0 x G1 (x G2) floats, G = T + 2m + 3: local nodes
+//              -1 .. T + 2m + 1, which hold the gather stencil of any particle
+//              in local cells [0, T + 2m) for either shape order;
+//   current    3 boxes of H0 x H1 (x H2) int32, H = T + 2m + 5: local nodes
+//              -2 .. T + 2m + 2, which hold both stencils of any move;
+//   current64  (2D) the same boxes in int64, into which the int32 boxes are
+//              folded when they could overflow (in 3D they are flushed to the
+//              global current instead: its boxes are large and shared memory
+//              bounds the blocks per SM);
+//   particles  two round buffers of DIM + 5 arrays (cell, offsets, momenta,
+//              weight) of kRoundWords words: the next round's particles are
+//              copied in asynchronously while the current round runs;
+//   ring       (3D) moves whose two stencils start at different nodes, deposited
+//              256 at a time so that every warp runs one form of the deposit;
+//   counters   the bound of the current accumulated in the int32 boxes
+//              (three, by round modulo 3) and the ring's fill count.
 constexpr int kGpdThreads = 256;
-constexpr int kStageWords = 9;
+constexpr int kRoundWords = kGpdThreads + 8;
 constexpr int kRing = 2 * kGpdThreads;
-constexpr int kStageBytes = (kStageWords * (kGpdThreads + kRing) + 4) * 4;
-// 2D: the next round's particles (cell, 2 offsets, 3 momenta, weight) are
-// copied into shared memory asynchronously while the current round runs, two
-// buffers of one word per thread and array.
-constexpr int kPrefWords = 7;
-constexpr int kPrefBytes = 2 * kPrefWords * kGpdThreads * 4;
+constexpr int kCntWords = 8;
+enum { kCntBound = 0, kCntRing = 3 };
+
+struct TileSmem {
+    int G[3], H[3], fsz, jsz, off_r, off_64, off_p, off_ring, off_cnt, words;
+};
+
+__host__ __device__ inline int up4(int w) { return (w + 3) & ~3; }
+
+__host__ __device__ inline TileSmem tile_smem(int dim, const int* T, const int* m) {
+    TileSmem s{};
+    s.fsz = 1;
+    s.jsz = 1;
+    for (int d = 0; d < 3; ++d) {
+        s.G[d] = d < dim ? T[d] + 2 * m[d] + 3 : 1;
+        s.H[d] = d < dim ? T[d] + 2 * m[d] + 5 : 1;
+        s.fsz *= s.G[d];
+        s.jsz *= s.H[d];
+    }
+    s.off_r = up4(6 * s.fsz);
+    s.off_64 = s.off_r + up4(3 * s.jsz);
+    s.off_p = s.off_64 + (dim == 2 ? 2 * up4(3 * s.jsz) : 0);
+    s.off_ring = s.off_p + 2 * (dim + 5) * kRoundWords;
+    s.off_cnt = s.off_ring + (dim == 3 ? (dim + 5) * kRing : 0);
+    s.words = s.off_cnt + kCntWords;
+    return s;
+}
+
+// Overflow guard of the int32 current boxes.  One move adds at most
+// S |d|max (k^2 + 1/12) + 1024 to any node in 3D (S the particle's integer
+// charge, |d|max its largest displacement in cells, k the largest 1D shape
+// weight; the slack covers roundings and closures), and in 2D at most
+// S max(|d|max k, |v_z| (k^2 + 1/12)) + 1024.  3D: the kernel sums these
+// bounds (in units of 256) over the moves deposited since the boxes were
+// last flushed, and flushes before a phase whose worst case could take the
+// sum past 2^31 - 1 (a thermal plasma never needs to within a work item).
+// 2D: the boxes are folded into the int64 boxes every R rounds, R from the
+// largest move (host side).
+constexpr unsigned kBoundUnit = 256;
+constexpr unsigned kBoundLimit = 0x7fffffffu / kBoundUnit;
 
 __device__ inline void cp_async4(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ inline void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// One staged move: write / read kStageWords words at slot stride `stride`.
-__device__ inline void stage_move(int* w, int stride, const int* lc, const int* ce, const float* f0,
-                                  const float* f1, float s) {
-    w[0] = lc[0] | (lc[1] << 16);
-    w[stride] = lc[2] | (((ce[0] - lc[0] + 1) | ((ce[1] - lc[1] + 1) << 2) | ((ce[2] - lc[2] + 1) << 4)) << 16);
+// A move in DIM + 5 words at stride `stride`: word 0 packs the start cell in
+// the box's local frame (8 bits per dimension) with the end cell's carries
+// (2 bits each, from bit 24) and bit 30 set when both stencils start at the
+// same node in every dimension (-1: no move); then the start offsets, the
+// end offsets, the charge s and (2D) v_z.
+template <int DIM>
+struct Move {
+    int lc[3], ce[3];
+    float f[3], fe[3], s, vz;
+    bool same;
+    __device__ __forceinline__ static bool valid(const int* w) { return w[0] >= 0; }
+    __device__ __forceinline__ void write(int* w, int stride) const {
+        int carries = 0;
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        w[(2 + d) * stride] = __float_as_int(f0[d]);
-        w[(5 + d) * stride] = __float_as_int(f1[d]);
+        for (int d = 0; d < DIM; ++d) carries |= (ce[d] - lc[d] + 1) << (2 * d);
+        int h = lc[0] | (lc[1] << 8) | (carries << 24) | (same ? (1 << 30) : 0);
+        if (DIM == 3) h |= lc[2] << 16;
+        w[0] = h;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            w[(1 + d) * stride] = __float_as_int(f[d]);
+            w[(1 + DIM + d) * stride] = __float_as_int(fe[d]);
+        }
+        w[(1 + 2 * DIM) * stride] = __float_as_int(s);
+        if (DIM == 2) w[(2 + 2 * DIM) * stride] = __float_as_int(vz);
     }
-    w[8 * stride] = __float_as_int(s);
-}
-
-template <int ORDER, bool SAME, class Acc>
-__device__ inline void deposit_staged3d(const Acc& acc, int jsz, int H0, int H1, const int* w, int stride) {
-    const int w0 = w[0], w1 = w[stride];
-    const int lc[3] = {w0 & 0xffff, (int)((unsigned)w0 >> 16), w1 & 0xffff};
-    const int cc = (int)((unsigned)w1 >> 16);
-    const int ce[3] = {lc[0] + (cc & 3) - 1, lc[1] + ((cc >> 2) & 3) - 1, lc[2] + ((cc >> 4) & 3) - 1};
-    const float f[3] = {__int_as_float(w[2 * stride]), __int_as_float(w[3 * stride]),
-                        __int_as_float(w[4 * stride])};
-    const float fe[3] = {__int_as_float(w[5 * stride]), __int_as_float(w[6 * stride]),
-                         __int_as_float(w[7 * stride])};
-    const float s = __int_as_float(w[8 * stride]);
-    if (SAME) deposit3d_same<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
-    else      deposit3d<ORDER>(acc, jsz, H0, H1, lc, f, ce, fe, s);
-}
+    __device__ __forceinline__ void read(const int* w, int stride) {
+        const int h = w[0];
+        lc[0] = h & 0xff; lc[1] = (h >> 8) & 0xff; lc[2] = DIM == 3 ? (h >> 16) & 0xff : 0;
+        same = (h >> 30) & 1;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            ce[d] = d < DIM ? lc[d] + ((h >> (24 + 2 * d)) & 3) - 1 : 0;
+            f[d] = d < DIM ? __int_as_float(w[(1 + d) * stride]) : 0.0f;
+            fe[d] = d < DIM ? __int_as_float(w[(1 + DIM + d) * stride]) : 0.0f;
+        }
+        s = __int_as_float(w[(1 + 2 * DIM) * stride]);
+        vz = DIM == 2 ? __int_as_float(w[(2 + 2 * DIM) * stride]) : 0.0f;
+    }
+    // bound of this move's current at any node (units of kBoundUnit)
+    template <int ORDER>
+    __device__ __forceinline__ unsigned bound() const {
+        constexpr float k = ORDER == 2 ? 0.75f : 1.0f;
+        constexpr float k2 = k * k + 1.0f / 12.0f;
+        float dm = 0.0f;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) dm = fmaxf(dm, fabsf((float)(ce[d] - lc[d]) + (fe[d] - f[d])));
+        const float b = DIM == 3 ? dm * k2 : fmaxf(dm * k, fabsf(vz) * k2);
+        return __float2uint_ru(b * fabsf(s) * (1.0f / kBoundUnit)) + 5u;
+    }
+};
 
 // Everything the fused kernel needs for one species of one grid.
 struct GpdArgs {
@@ -611,14 +757,12 @@ enum { kGpdFused = 0, kGpdGather = 1, kGpdFieldsIn = 2 };
 template <int DIM, int ORDER, int MODE = kGpdFused>
 __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float4* smem4) {
     const Geo& g = A.g;
-    const Ptr3<const float>& E = A.E;
-    const Ptr3<const float>& B = A.B;
     const Ptr3<unsigned long long>& J = A.J;
     const P32& p = A.p;
     const Tiles& t = A.t;
     const CellDecode& dec = A.dec;
-    const float k = A.k, sq = A.sq, dth0 = A.dth0, dth1 = A.dth1, dth2 = A.dth2;
     unsigned* st = A.st;
+    const int tid = threadIdx.x;
 
     const int2 item = t.items[item_index];
     const int tile = item.x;
@@ -631,102 +775,155 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     const int t0[3] = {(tile % t.nt[0]) * t.T[0] - t.m[0], ((tile / t.nt[0]) % t.nt[1]) * t.T[1] - t.m[1],
                        DIM == 3 ? (tile / (t.nt[0] * t.nt[1])) * t.T[2] - t.m[2] : 0};
     const int Te[3] = {t.T[0] + 2 * t.m[0], t.T[1] + 2 * t.m[1], t.T[2] + 2 * t.m[2]};
-    const int G0 = Te[0] + 4, G1 = Te[1] + 4, G2 = (DIM == 3) ? Te[2] + 4 : 1;
-    const int H0 = Te[0] + 5, H1 = Te[1] + 5, H2 = (DIM == 3) ? Te[2] + 5 : 1;
-    const int fsz = G0 * G1 * G2, jsz = H0 * H1 * H2;
-    const int n4 = (3 * jsz + 3) >> 2;     // the J boxes in groups of 4 nodes
-    float* sF = reinterpret_cast<float*>(smem4);
-    long long* sJ = reinterpret_cast<long long*>(sF + ((6 * fsz + 3) & ~3));
-    int* sR = reinterpret_cast<int*>(sJ + 4 * n4);
-    longlong2* sJ2 = reinterpret_cast<longlong2*>(sJ);
-    int4* sR4 = reinterpret_cast<int4*>(sR);
-    // 3D deposit staging: same-stencil slots, the ring, then the counters:
-    // [round & 1] same-stencil moves of the round, [2] moves ever queued
-    int* sSt = sR + 4 * n4;
-    int* sRing = sSt + kStageWords * kGpdThreads;
-    int* sCnt = sRing + kStageWords * kRing;
+    const TileSmem L = tile_smem(DIM, t.T, t.m);
+    const int G0 = L.G[0], G1 = L.G[1], H0 = L.H[0], H1 = L.H[1];
+    const int fsz = L.fsz, jsz = L.jsz;
+    int* smw = reinterpret_cast<int*>(smem4);
+    float* sF = reinterpret_cast<float*>(smw);
+    int* sR = smw + L.off_r;
+    int* sP = smw + L.off_p;
+    int* sRing = smw + L.off_ring;
+    int* sCnt = smw + L.off_cnt;
 
-    for (int idx = threadIdx.x; MODE != kGpdFieldsIn && idx < 6 * fsz; idx += blockDim.x) {
+    // the next round's particles (cell, offsets, momenta, weight; the arrays
+    // lie cap words apart).  3D: copied in 16-byte chunks, warp w copying
+    // array w (a barrier orders them before use).  2D: each thread copies
+    // its own particle's words, so a round needs no barrier.
+    constexpr int NARR = DIM + 5;
+    const long long astride = (long long)(reinterpret_cast<const char*>(p.off[0]) - reinterpret_cast<const char*>(p.cell));
+    const int nround = (end - beg + kGpdThreads - 1) / kGpdThreads;
+    auto prefetch = [&](int r) {
+        const int rb = beg + r * kGpdThreads, re = min(rb + kGpdThreads, end);
+        if constexpr (DIM == 2) {
+            if (rb + tid < re) {
+                const char* src = reinterpret_cast<const char*>(p.cell) + 4LL * (rb + tid);
+                int* dst = sP + (r & 1) * NARR * kRoundWords + tid;
+#pragma unroll
+                for (int k = 0; k < NARR; ++k) cp_async4(dst + k * kRoundWords, src + k * astride);
+            }
+        } else {
+            const int a0 = rb & ~3, nch = (re - a0 + 3) >> 2;
+            const int arr = tid >> 5;
+            if (arr < NARR) {
+                const char* src = reinterpret_cast<const char*>(p.cell) + arr * astride + 4LL * a0;
+                int* dst = sP + ((r & 1) * NARR + arr) * kRoundWords;
+                for (int q = tid & 31; q < nch; q += 32) cp_async16(dst + 4 * q, src + 16 * q);
+            }
+        }
+    };
+    prefetch(0);
+    cp_async_commit();
+
+    // fields of the box (local node x at index x + 1), zeroed current boxes
+    for (int idx = tid; MODE != kGpdFieldsIn && idx < 6 * fsz; idx += kGpdThreads) {
         const int c = fdiv(idx, t.fF), r = idx - c * fsz;
         const int q = fdiv(r, t.fG0), lx = r - q * G0;
         const int lz = (DIM == 3) ? fdiv(q, t.fG1) : 0, ly = q - lz * G1;
-        const long long m = fidx_near(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
-        const float* src = c == 0 ? E.p[0] : c == 1 ? E.p[1] : c == 2 ? E.p[2]
-                         : c == 3 ? B.p[0] : c == 4 ? B.p[1] : B.p[2];
-        sF[idx] = (m < 0) ? 0.0f : src[m];
+        const long long m = fidx_near(g, t0[0] - 1 + lx, t0[1] - 1 + ly, DIM == 3 ? t0[2] - 1 + lz : 0);
+        const float* src = c == 0 ? A.E.p[0] : c == 1 ? A.E.p[1] : c == 2 ? A.E.p[2]
+                         : c == 3 ? A.B.p[0] : c == 4 ? A.B.p[1] : A.B.p[2];
+        sF[idx] = (m < 0) ? 0.0f : __ldg(src + m);
     }
-    for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-        sJ2[2 * q] = make_longlong2(0, 0);
-        sJ2[2 * q + 1] = make_longlong2(0, 0);
-        sR4[q] = make_int4(0, 0, 0, 0);
-    }
-    if (DIM == 3 && threadIdx.x < 4) sCnt[threadIdx.x] = 0;
-    __syncthreads();
+    for (int q = tid; q < (L.off_p - L.off_r) / 4; q += kGpdThreads)
+        reinterpret_cast<int4*>(sR)[q] = make_int4(0, 0, 0, 0);
+    if (tid < kCntWords) sCnt[tid] = 0;
+    constexpr bool BOX64 = DIM == 2;
+    const int n4 = (L.off_64 - L.off_r) / 4;          // int32 boxes in groups of 4 nodes
+    int4* sR4 = reinterpret_cast<int4*>(sR);
+    longlong2* s64 = reinterpret_cast<longlong2*>(smw + L.off_64);
 
-    const float dth[3] = {dth0, dth1, dth2};
-    const Acc32<DIM == 2> acc{sR};
-    // adds the int32 box into the int64 box, four nodes at a time, and clears
-    // it (callers place the barriers)
+    // flush of the current boxes into the global int64 current (all threads;
+    // callers place the barriers): the int64 boxes (2D), or the int32 boxes
+    auto flush = [&]() {
+        bool outside = false;
+        for (int idx = tid; idx < 3 * jsz; idx += kGpdThreads) {
+            long long v;
+            if constexpr (BOX64) {
+                v = reinterpret_cast<const long long*>(s64)[idx];
+            } else {
+                v = sR[idx];
+                if (v != 0) sR[idx] = 0;
+            }
+            if (v == 0) continue;
+            const int c = fdiv(idx, t.fJ), r = idx - c * jsz;
+            const int q = fdiv(r, t.fH0), lx = r - q * H0;
+            const int lz = (DIM == 3) ? fdiv(q, t.fH1) : 0, ly = q - lz * H1;
+            const long long m = fidx_near(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
+            if (m < 0) { outside = true; continue; }
+            unsigned long long* dst = c == 0 ? J.p[0] : c == 1 ? J.p[1] : J.p[2];
+            atomicAdd(dst + m, static_cast<unsigned long long>(v));
+        }
+        if (outside) set_status(st, LPIC_ST_OUTSIDE);
+    };
+    // 2D: adds the int32 boxes into the int64 boxes, four nodes at a time, and
+    // clears them (callers place the barriers)
     auto fold = [&]() {
-        for (int q = threadIdx.x; q < n4; q += kGpdThreads) {
+        for (int q = tid; q < n4; q += kGpdThreads) {
             const int4 v = sR4[q];
             if ((v.x | v.y | v.z | v.w) != 0) {
-                longlong2 a = sJ2[2 * q], b = sJ2[2 * q + 1];
+                longlong2 a = s64[2 * q], b = s64[2 * q + 1];
                 a.x += v.x; a.y += v.y; b.x += v.z; b.y += v.w;
-                sJ2[2 * q] = a; sJ2[2 * q + 1] = b;
+                s64[2 * q] = a; s64[2 * q + 1] = b;
                 sR4[q] = make_int4(0, 0, 0, 0);
             }
         }
     };
-    // 3D (block-uniform): moves deposited since the last fold, moves queued in
-    // and taken from the ring
-    int moves = 0, queued = 0, consumed = 0;
-    const int nround = (end - beg + kGpdThreads - 1) / kGpdThreads;
-    // 2D: this thread's particle of round r, prefetched into buffer r & 1
-    int* sPf = sR + 4 * n4;
-    auto prefetch = [&](int r) {
-        const int ii = beg + r * kGpdThreads + threadIdx.x;
-        if (r < nround && ii < end) {
-            int* b = sPf + (r & 1) * kPrefWords * kGpdThreads + threadIdx.x;
-            cp_async4(b, p.cell + ii);
-            cp_async4(b + 1 * kGpdThreads, p.off[0] + ii);
-            cp_async4(b + 2 * kGpdThreads, p.off[1] + ii);
-            cp_async4(b + 3 * kGpdThreads, p.u[0] + ii);
-            cp_async4(b + 4 * kGpdThreads, p.u[1] + ii);
-            cp_async4(b + 5 * kGpdThreads, p.u[2] + ii);
-            cp_async4(b + 6 * kGpdThreads, p.w + ii);
-        }
-        cp_async_commit();
+    // makes room in the int32 boxes
+    auto drain = [&]() {
+        if constexpr (BOX64) fold(); else flush();
     };
-    if constexpr (DIM == 2) prefetch(0);
-    for (int rnd = 0; rnd < nround; ++rnd) {
-        const int i = beg + rnd * kGpdThreads + threadIdx.x;
-        int cell = -1;
-        // off0, off1, u0, u1, u2, then 2D: w / 3D: off2 (3D weight in pf3w)
-        float pf[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, pf3w = 0.0f;
-        if constexpr (DIM == 2) {
-            cp_async_wait_all();
-            const int* b = sPf + (rnd & 1) * kPrefWords * kGpdThreads + threadIdx.x;
-            if (i < end) {
-                cell = b[0];
-#pragma unroll
-                for (int k2 = 0; k2 < 6; ++k2) pf[k2] = __int_as_float(b[(1 + k2) * kGpdThreads]);
+    // 3D: the ring's general-form moves (full warps of one form)
+    auto deposit_ring = [&](int slot) -> unsigned {
+        Move<DIM> mv;
+        mv.read(sRing + (slot & (kRing - 1)), kRing);
+        deposit3d<ORDER>(Acc32<false>{sR}, jsz, H0, H1, mv.lc, mv.f, mv.ce, mv.fe, mv.s);
+        return mv.template bound<ORDER>();
+    };
+
+    const float dth[3] = {A.dth0, A.dth1, A.dth2};
+    const unsigned bmax = t.bmax;          // bound of any one move (units)
+    unsigned total = 0;                    // bound accumulated since the boxes were emptied (block-uniform)
+    int consumed = 0;                      // 3D ring entries deposited (block-uniform)
+
+    // bound counters: round r adds to [r % 3], which every thread reads after
+    // the first barrier of round r + 1; thread 0 clears [(r + 1) % 3] in round
+    // r, after all threads read it (round r - 1) and before anyone adds to it
+    int cc = 0;
+    for (int rnd = 0; rnd < nround; ++rnd, cc = (cc == 2) ? 0 : cc + 1) {
+        const int cprev = (cc == 0) ? 2 : cc - 1, cnext = (cc == 2) ? 0 : cc + 1;
+        cp_async_wait_all();
+        if (DIM == 3 || rnd == 0) __syncthreads();
+        if (rnd + 1 < nround) prefetch(rnd + 1);
+        cp_async_commit();
+        if (DIM == 3 && MODE != kGpdGather) {
+            // the previous round's moves are all accounted for: empty the boxes
+            // if this round's (its own moves and a batch from the ring) could
+            // overflow them (the host keeps 2 x 256 bmax within the limit)
+            if (rnd > 0) total += (unsigned)sCnt[kCntBound + cprev];
+            if (total + 2u * kGpdThreads * bmax > kBoundLimit) {
+                drain();
+                __syncthreads();
+                total = 0;
             }
-            prefetch(rnd + 1);
-        } else {
-            // 3D: all of the particle's loads in flight together
-            if (i < end) {
-                cell = p.cell[i];
-                pf[0] = p.off[0][i]; pf[1] = p.off[1][i]; pf[5] = p.off[2][i];
-                pf[2] = p.u[0][i]; pf[3] = p.u[1][i]; pf[4] = p.u[2][i];
-                pf3w = p.w[i];
-            }
+            if (tid == 0) sCnt[kCntBound + cnext] = 0;
         }
-        int cell_out = cell;      // the particle's cell after this round (-1: removed)
-        // 3D: the move this particle deposits (if dep), staged below
-        bool dep = false, same = false;
-        int mlc[3] = {0, 0, 0}, mce[3] = {0, 0, 0};
-        float mf0[3] = {0.0f, 0.0f, 0.0f}, mf1[3] = {0.0f, 0.0f, 0.0f}, ms = 0.0f;
+
+        const int rb = beg + rnd * kGpdThreads;
+        const int i = rb + tid;
+        const int* slot = sP + (rnd & 1) * NARR * kRoundWords + (DIM == 3 ? rb - (rb & ~3) : 0) + tid;
+        int cell = -1;
+        float f[3] = {0.0f, 0.0f, 0.0f}, ux = 0.0f, uy = 0.0f, uz = 0.0f, w = 0.0f;
+        if (i < end) {
+            cell = slot[0];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) f[d] = __int_as_float(slot[(1 + d) * kRoundWords]);
+            ux = __int_as_float(slot[(1 + DIM) * kRoundWords]);
+            uy = __int_as_float(slot[(2 + DIM) * kRoundWords]);
+            uz = __int_as_float(slot[(3 + DIM) * kRoundWords]);
+            w = __int_as_float(slot[(4 + DIM) * kRoundWords]);
+        }
+        int cell_out = cell;            // the particle's cell after this round (-1: removed)
+        unsigned bnd = 0;               // bound of the move this thread deposited
         if (cell >= 0) {
             int gc[3];
             dec(cell, gc);
@@ -754,15 +951,6 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 }
                 cell_out = -1;
             } else {
-                float f[3], ux, uy, uz, w;
-                if constexpr (DIM == 2) {
-                    f[0] = pf[0]; f[1] = pf[1]; f[2] = 0.0f;
-                    ux = pf[2]; uy = pf[3]; uz = pf[4]; w = pf[5];
-                } else {
-                    f[0] = pf[0]; f[1] = pf[1]; f[2] = pf[5];
-                    ux = pf[2]; uy = pf[3]; uz = pf[4]; w = pf3w;
-                }
-
                 // gather at x^{n+1/2} from the shared-memory halo
                 const NodeW<ORDER> nx_(lc[0], f[0]), ny_(lc[1], f[1]), nz_(lc[2], f[2]);
                 const HalfW<ORDER> hx_(lc[0], f[0]), hy_(lc[1], f[1]), hz_(lc[2], f[2]);
@@ -777,7 +965,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 #pragma unroll
                     for (int c = 0; c < 6; ++c) A.fields[c * A.fcap + i] = fld[c];
                 } else {
-                boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
+                boris_f32(ux, uy, uz, A.k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
                 if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
                     set_status(st, LPIC_ST_NAN);
                     p.cell[i] = -1;
@@ -785,42 +973,30 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 } else {
                     const float ig = rsqrtf(1.0f + ux * ux + uy * uy + uz * uz);
                     const float uu[3] = {ux, uy, uz};
-                    int ce[3] = {0, 0, 0};
-                    float fe[3] = {0.0f, 0.0f, 0.0f};
+                    Move<DIM> mv;
                     bool cfl = false;
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
+                    for (int d = 0; d < 3; ++d) {
+                        mv.lc[d] = lc[d]; mv.f[d] = f[d]; mv.ce[d] = lc[d]; mv.fe[d] = f[d];
+                        if (d >= DIM) continue;
                         const float dl = uu[d] * ig * dth[d];
                         cfl |= !(fabsf(dl) < 1.0f);
                         const float fr = f[d] + dl;
                         int carry = (int)floorf(fr);
                         float fn = fr - (float)carry;
                         if (fn >= 1.0f) { fn -= 1.0f; carry += 1; }
-                        ce[d] = lc[d] + carry;
-                        fe[d] = fn;
+                        mv.ce[d] = lc[d] + carry;
+                        mv.fe[d] = fn;
                     }
                     if (cfl) {
                         set_status(st, LPIC_ST_CFL);
                         p.cell[i] = -1;
                         cell_out = -1;
                     } else {
-                        same = same_stencils<DIM, ORDER>(lc, f, ce, fe);
-                        if constexpr (DIM == 2) {
-                            // the stencil-sized window when every converged lane allows it
-                            if (__all_sync(__activemask(), same))
-                                deposit2d_same<ORDER>(acc, jsz, H0, lc, f, ce, fe, sq * w, uz * ig);
-                            else
-                                deposit2d<ORDER>(acc, jsz, H0, lc, f, ce, fe, sq * w, uz * ig);
-                        } else {
-                            dep = true;
-#pragma unroll
-                            for (int d = 0; d < 3; ++d) { mlc[d] = lc[d]; mce[d] = ce[d]; mf0[d] = f[d]; mf1[d] = fe[d]; }
-                            ms = sq * w;
-                        }
                         // store x^{n+3/2} and u^{n+1}
                         int ng[3];
 #pragma unroll
-                        for (int d = 0; d < 3; ++d) ng[d] = (d < DIM) ? t0[d] + ce[d] : 0;
+                        for (int d = 0; d < 3; ++d) ng[d] = (d < DIM) ? t0[d] + mv.ce[d] : 0;
                         bool dead = false;
                         if (g.absorb) dead = (ng[0] < 2 || ng[0] >= g.nx - 2);
                         else ng[0] = wrapi(ng[0], g.nx);
@@ -829,8 +1005,30 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                         cell_out = dead ? -1 : (ng[2] * g.ny + ng[1]) * g.nx + ng[0];
                         p.cell[i] = cell_out;
 #pragma unroll
-                        for (int d = 0; d < DIM; ++d) p.off[d][i] = fe[d];
+                        for (int d = 0; d < DIM; ++d) p.off[d][i] = mv.fe[d];
                         p.u[0][i] = ux; p.u[1][i] = uy; p.u[2][i] = uz;
+
+                        mv.s = A.sq * w;
+                        mv.vz = uz * ig;
+                        const NodeW<ORDER> ex(mv.ce[0], mv.fe[0]), ey(mv.ce[1], mv.fe[1]), ez(mv.ce[2], mv.fe[2]);
+                        mv.same = ex.base == nx_.base && ey.base == ny_.base && (DIM == 2 || ez.base == nz_.base);
+                        if constexpr (DIM == 2) {
+                            const Acc32<true> acc{sR};
+                            // the stencil-sized window when every converged lane allows it
+                            if (__all_sync(__activemask(), mv.same))
+                                deposit2d_w<ORDER, true>(acc, jsz, H0, nx_, ny_, ex, ey, mv.s, mv.vz);
+                            else
+                                deposit2d_w<ORDER, false>(acc, jsz, H0, nx_, ny_, ex, ey, mv.s, mv.vz);
+                        } else {
+                            if (mv.same) {
+                                bnd = mv.template bound<ORDER>();
+                                deposit3d_w<ORDER>(Acc32<false>{sR}, jsz, H0, H1, nx_, ny_, nz_, ex, ey, ez, mv.s);
+                            } else {
+                                // staged: deposited with the other general-form moves
+                                const int to = atomicAdd(sCnt + kCntRing, 1) & (kRing - 1);
+                                mv.write(sRing + to, kRing);
+                            }
+                        }
                     }
                 }
                 }   // not the gather stage
@@ -845,88 +1043,43 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 key = (fdiv(gc2[2], t.fT[2]) * t.nt[1] + fdiv(gc2[1], t.fT[1])) * t.nt[0] + fdiv(gc2[0], t.fT[0]);
             }
             const unsigned peers = __match_any_sync(0xffffffffu, key);
-            if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            if (key >= 0 && (tid & 31) == __ffs(peers) - 1)
                 atomicAdd(t.next_count + key, __popc(peers));
         }
+        if (MODE == kGpdGather) continue;
         if constexpr (DIM == 3) {
-            // 3D: same-stencil moves go to this round's slots; the others to
-            // the ring, deposited 256 at a time, so that each warp runs one
-            // form of the deposit with full lanes (most particles keep their
-            // stencil, but few warps are uniform; the order of the integer
-            // sums does not matter)
-            int* cf = sCnt + (rnd & 1);
-            const unsigned lane = threadIdx.x & 31u;
-            const unsigned mfast = __ballot_sync(0xffffffffu, dep && same);
-            const unsigned mgen = __ballot_sync(0xffffffffu, dep && !same);
-            int bf = 0, bg = 0;
-            if (lane == 0) {
-                if (mfast) bf = atomicAdd(cf, __popc(mfast));
-                if (mgen) bg = atomicAdd(sCnt + 2, __popc(mgen));
-            }
-            bf = __shfl_sync(0xffffffffu, bf, 0);
-            bg = __shfl_sync(0xffffffffu, bg, 0);
-            if (dep) {
-                const unsigned below = (1u << lane) - 1u;
-                if (same) stage_move(sSt + bf + __popc(mfast & below), kGpdThreads, mlc, mce, mf0, mf1, ms);
-                else      stage_move(sRing + ((bg + __popc(mgen & below)) & (kRing - 1)), kRing, mlc, mce, mf0,
-                                     mf1, ms);
-            }
+            // a full batch of general-form moves from the ring
             __syncthreads();
-            const int nf = *cf;
-            queued = sCnt[2];
-            // the other parity's counter was last read before this barrier
-            if (threadIdx.x == 0) sCnt[(rnd + 1) & 1] = 0;
-            if (moves + nf > kGpdThreads * t.R) { fold(); moves = 0; __syncthreads(); }
-            if ((int)threadIdx.x < nf)
-                deposit_staged3d<ORDER, true>(acc, jsz, H0, H1, sSt + threadIdx.x, kGpdThreads);
-            moves += nf;
-            if (queued - consumed >= kGpdThreads) {
-                if (moves + kGpdThreads > kGpdThreads * t.R) {
-                    __syncthreads(); fold(); moves = 0; __syncthreads();
-                }
-                deposit_staged3d<ORDER, false>(acc, jsz, H0, H1,
-                                               sRing + ((consumed + threadIdx.x) & (kRing - 1)), kRing);
+            if (sCnt[kCntRing] - consumed >= kGpdThreads) {
+                bnd += deposit_ring(consumed + tid);
                 consumed += kGpdThreads;
-                moves += kGpdThreads;
             }
-            // the staging slots are rewritten by the next round
-            __syncthreads();
+            const unsigned wb = __reduce_add_sync(0xffffffffu, bnd);
+            if ((tid & 31) == 0 && wb) atomicAdd(reinterpret_cast<unsigned*>(sCnt) + kCntBound + cc, wb);
         } else {
-            // 2D: every R rounds (and at the end) fold the int32 box into the
-            // int64 box (block-uniform condition)
+            // 2D: every R rounds (and after the last) fold the int32 boxes
+            // into the int64 boxes (the host's R keeps them in range)
             if ((rnd + 1) % t.R == 0 || rnd + 1 == nround) { __syncthreads(); fold(); __syncthreads(); }
         }
     }
+    if (MODE == kGpdGather) return;
     if constexpr (DIM == 3) {
-        // the moves still in the ring, then the last fold
-        const int rest = queued - consumed;
-        if (rest > 0) {
-            if (moves + rest > kGpdThreads * t.R) { fold(); __syncthreads(); }
-            if ((int)threadIdx.x < rest)
-                deposit_staged3d<ORDER, false>(acc, jsz, H0, H1,
-                                               sRing + ((consumed + threadIdx.x) & (kRing - 1)), kRing);
+        __syncthreads();
+        // the moves still in the ring (fewer than 512), in batches of 256
+        total += (unsigned)sCnt[kCntBound + (nround - 1) % 3];
+        const int queued = sCnt[kCntRing];
+        while (queued - consumed > 0) {
+            if (total + kGpdThreads * bmax > kBoundLimit) { drain(); __syncthreads(); total = 0; }
+            if (tid < queued - consumed) deposit_ring(consumed + tid);
+            consumed += kGpdThreads;
+            total += kGpdThreads * bmax;
             __syncthreads();
         }
-        fold();
-        __syncthreads();
     }
-
-    // one flush of the item's current to the global int64 arrays
-    bool outside = false;
-    for (int idx = threadIdx.x; idx < 3 * jsz; idx += blockDim.x) {
-        const long long v = sJ[idx];
-        if (v == 0) continue;
-        const int c = fdiv(idx, t.fJ), r = idx - c * jsz;
-        const int q = fdiv(r, t.fH0), lx = r - q * H0;
-        const int lz = (DIM == 3) ? fdiv(q, t.fH1) : 0, ly = q - lz * H1;
-        const long long m = fidx_near(g, t0[0] - 2 + lx, t0[1] - 2 + ly, DIM == 3 ? t0[2] - 2 + lz : 0);
-        if (m < 0) { outside = true; continue; }
-        unsigned long long* dst = c == 0 ? J.p[0] : c == 1 ? J.p[1] : J.p[2];
-        atomicAdd(dst + m, static_cast<unsigned long long>(v));
-    }
-    if (outside) set_status(st, LPIC_ST_OUTSIDE);
+    // one flush of the item's current to the global int64 arrays (2D: the
+    // int64 boxes, folded after the last round)
+    flush();
 }
-
 
 template <int DIM, int ORDER, int MODE = kGpdFused>
 __global__ void __launch_bounds__(256, DIM == 2 ? LPIC_GPD2D_MINB : LPIC_GPD3D_MINB) k_gpd32(GpdArgs A) {
@@ -970,7 +1123,7 @@ struct AccGlobal {
     Ptr3<unsigned long long> J;
     int gc[3];
     unsigned* st;
-    __device__ inline void operator()(int idx, int v) const {
+    __device__ __forceinline__ void operator()(int idx, int v) const {
         if (v == 0) return;
         constexpr int jsz = (DIM == 3) ? HV * HV * HV : HV * HV;
         const int c = idx / jsz, r = idx - c * jsz;

@@ -32,22 +32,24 @@ namespace {
 
 constexpr int kMaxTiles = LPIC_NOALLOC_MAX_TILES;
 // histogram (ntiles + 1), scan output (ntiles + 2), cursors (ntiles + 1),
-// work-item offsets (ntiles + 1); each part starts on a 256-byte boundary.
+// work-item offsets (ntiles + 1), then the particle count actually sorted;
+// each part starts on a 256-byte boundary.
 constexpr int kPart = (kMaxTiles + 2 + 63) / 64 * 64;
-static __device__ __align__(256) int lpic_noalloc_scratch[4 * kPart];
+static __device__ __align__(256) int lpic_noalloc_scratch[4 * kPart + 64];
 
 std::mutex g_mu;
 int* g_scratch[64] = {nullptr};
+int g_nsm[64] = {0};
 
 lpic_status nfail(lpic_status s, const char* m) {
     set_last_error(m);
     return s;
 }
 
-// Device address of the scratch array for the current device; the first call
-// on a device looks it up (so that first call must not happen while the
-// calling thread captures a graph).
-lpic_status scratch_ptr(int** out) {
+// Device address of the scratch array and the SM count of the current
+// device; the first call on a device looks both up (so that first call must
+// not happen while the calling thread captures a graph).
+lpic_status scratch_ptr(int** out, int* nsm) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return nfail(LPIC_ECUDA, "lpic_sort_tiles_static: no current CUDA device");
@@ -57,10 +59,35 @@ lpic_status scratch_ptr(int** out) {
         const cudaError_t e = cudaGetSymbolAddress(&p, lpic_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return nfail(LPIC_ECUDA, "lpic_sort_tiles_static: cudaGetSymbolAddress failed");
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1)
+            return nfail(LPIC_ECUDA, "lpic_sort_tiles_static: cannot query the SM count");
+        g_nsm[dev] = n;
         g_scratch[dev] = static_cast<int*>(p);
     }
     *out = g_scratch[dev];
+    *nsm = g_nsm[dev];
     return LPIC_OK;
+}
+
+// Tile key of a caller's particle: cells outside [0, ncells) are treated as
+// removed (key ntiles), like cell < 0, so that no histogram entry outside the
+// scratch array is touched.
+struct KeyChecked {
+    KeyFP32 key;
+    int ncells;
+    __device__ inline int operator()(int i) const {
+        const int c = key.cell[i];
+        return (c >= ncells) ? key.ntiles : key(i);
+    }
+};
+
+// The number of particles sorted: the caller's count, clamped to [0, capacity].
+__global__ void k_clamp_count(const int* count_in, long long capacity, int* n) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int c = *count_in;
+        *n = c < 0 ? 0 : (c > capacity ? (int)capacity : c);
+    }
 }
 
 P32 view(void* buf, long long cap, int dim, const int* n) {
@@ -110,27 +137,32 @@ extern "C" lpic_status lpic_sort_tiles_static(int dim, int nx, int ny, int nz, c
         return nfail(LPIC_EINVAL, "lpic_sort_tiles_static: buffers must be 256-byte aligned");
 
     int* scratch = nullptr;
-    if (lpic_status r = scratch_ptr(&scratch)) return r;
+    int nsm = 0;
+    if (lpic_status r = scratch_ptr(&scratch, &nsm)) return r;
     int* count = scratch;
     int* start = scratch + kPart;
     int* cursor = scratch + 2 * kPart;
     int* coff = scratch + 3 * kPart;
+    int* n_sorted = scratch + 4 * kPart;
     const int nt1 = (int)ntiles;
     // the array keeps the previous call's contents: clear what must start at zero
     if (cudaMemsetAsync(count, 0, sizeof(int) * (nt1 + 1), stream) != cudaSuccess ||
         cudaMemsetAsync(cursor, 0, sizeof(int) * (nt1 + 1), stream) != cudaSuccess)
         return nfail(LPIC_ECUDA, "lpic_sort_tiles_static: cudaMemsetAsync failed");
 
-    const P32 s = view(const_cast<void*>(src), capacity, dim, count_in);
+    const P32 s = view(const_cast<void*>(src), capacity, dim, n_sorted);
     const P32 d = view(dst, capacity, dim, count_out);
     const CellDecode dec{make_fastdiv((unsigned)nx), make_fastdiv((unsigned)ny)};
-    KeyFP32 key{s.cell, dec, make_fastdiv((unsigned)T[0]), make_fastdiv((unsigned)T[1]),
-                make_fastdiv((unsigned)T[2]), nt[0], nt[1], nt1};
+    const KeyChecked key{KeyFP32{s.cell, dec, make_fastdiv((unsigned)T[0]), make_fastdiv((unsigned)T[1]),
+                                 make_fastdiv((unsigned)T[2]), nt[0], nt[1], nt1},
+                         nx * ny * nz};
+    // grid-stride kernels: at most 16 blocks of 256 per SM
     int blocks = (int)((capacity + 255) / 256);
-    if (blocks > 148 * 16) blocks = 148 * 16;
-    k_sort_count<<<blocks, 256, 0, stream>>>(key, count_in, count);
+    if (blocks > nsm * 16) blocks = nsm * 16;
+    k_clamp_count<<<1, 32, 0, stream>>>(count_in, capacity, n_sorted);
+    k_sort_count<<<blocks, 256, 0, stream>>>(key, n_sorted, count);
     k_sort_scan<<<1, 1024, 0, stream>>>(count, start, nt1, 1 << 30, coff);
-    k_sort_scatter<<<blocks, 256, 0, stream>>>(key, MoveFP32{s, d, dim}, count_in, start, cursor, nt1);
+    k_sort_scatter<<<blocks, 256, 0, stream>>>(key, MoveFP32{s, d, dim}, n_sorted, start, cursor, nt1);
     k_sort_finalize<<<1, 32, 0, stream>>>(start, nt1, count_out);
     k_copy_starts<<<(nt1 + 1 + 255) / 256, 256, 0, stream>>>(start, tile_start, nt1 + 1);
     if (cudaGetLastError() != cudaSuccess) return nfail(LPIC_ECUDA, "lpic_sort_tiles_static: kernel launch failed");

@@ -130,7 +130,75 @@ def test_static_sort_rejects_too_many_tiles():
     from paper_2607_13507_b300 import lpic
     L = lpic.load()
     t3 = (ctypes.c_int * 3)(1, 1, 1)
-    z = ctypes.c_void_p(256)
-    rc = L.lpic_sort_tiles_static(2, 512, 512, 1, t3, z, ctypes.c_void_p(512), 64, z, z, z, None)
+    # real, aligned device buffers, so that no order of the host checks can
+    # hand the kernels an invalid address
+    nbytes = lpic.species_bytes(2, lpic.FP32_FIXED, 64)
+    src = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
+    dst = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
+    s_ptr = src.data_ptr() + (-src.data_ptr()) % 256
+    d_ptr = dst.data_ptr() + (-dst.data_ptr()) % 256
+    cnt = torch.zeros(2, dtype=torch.int32, device="cuda")
+    starts = torch.zeros(16, dtype=torch.int32, device="cuda")
+    rc = L.lpic_sort_tiles_static(2, 512, 512, 1, t3, s_ptr, d_ptr, 64, cnt.data_ptr(),
+                                  cnt.data_ptr() + 4, starts.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
     assert rc == 1
     assert b"LPIC_NOALLOC_MAX_TILES" in L.lpic_last_error()
+    torch.cuda.synchronize()
+
+
+def test_static_sort_clamps_count_and_drops_cells_off_the_grid():
+    """A count above the capacity is taken as the capacity and a cell at or
+    beyond nx ny is dropped like a removed particle: nothing outside dst, the
+    counts and the starts is written."""
+    from paper_2607_13507_b300 import lpic
+    L = lpic.load()
+    nx, ny, tile, cap = 16, 8, (8, 4), 64
+    nbytes = lpic.species_bytes(2, lpic.FP32_FIXED, cap)
+    src = torch.zeros(nbytes + 256, dtype=torch.uint8, device="cuda")
+    guard = 4096
+    dst = torch.full((nbytes + 256 + guard,), 0xA5, dtype=torch.uint8, device="cuda")
+    s_off = (-src.data_ptr()) % 256
+    d_off = (-dst.data_ptr()) % 256
+    rng = np.random.default_rng(5)
+    cell = rng.integers(0, nx * ny, cap).astype(np.int32)
+    cell[3] = nx * ny            # just off the grid
+    cell[9] = 1 << 30            # far off the grid
+    cell[20] = -1                # removed
+    ids = np.arange(cap, dtype=np.int32)
+    a = 4 * cap
+    body = src[s_off:s_off + nbytes]
+    body[0:a].view(torch.int32).copy_(torch.from_numpy(cell))
+    for k in range(1, 7):
+        body[k * a:(k + 1) * a].view(torch.float32).copy_(torch.from_numpy(rng.random(cap).astype(np.float32)))
+    body[7 * a:8 * a].view(torch.int32).copy_(torch.from_numpy(ids))
+    cnt_in = torch.tensor([10 * cap], dtype=torch.int32, device="cuda")
+    cnt_out = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    nt = (nx // tile[0]) * (ny // tile[1])
+    starts = torch.full((nt + 1 + 64,), -7, dtype=torch.int32, device="cuda")
+    t3 = (ctypes.c_int * 3)(tile[0], tile[1], 1)
+    for _ in range(2):
+        rc = L.lpic_sort_tiles_static(2, nx, ny, 1, t3, src.data_ptr() + s_off, dst.data_ptr() + d_off,
+                                      cap, cnt_in.data_ptr(), cnt_out.data_ptr(), starts.data_ptr(),
+                                      torch.cuda.current_stream().cuda_stream)
+        assert rc == 0, L.lpic_last_error()
+        torch.cuda.synchronize()
+        keep = (cell >= 0) & (cell < nx * ny)
+        n = int(cnt_out.item())
+        assert n == int(keep.sum())
+        st = starts.cpu().numpy()
+        assert st[nt] == n and np.all(st[nt + 1:] == -7)
+        got = _arrays(dst[d_off:d_off + nbytes], cap, 2, n)
+        assert np.array_equal(np.sort(got["id"]), ids[keep])
+        assert np.all(np.diff(_tile_key(got["cell"], nx, ny, tile, 2)) >= 0)
+        # the guard bytes after dst are untouched
+        assert bool(torch.all(dst[d_off + nbytes:d_off + nbytes + guard] == 0xA5))
+    # the shared scratch still serves a normal call afterwards
+    cnt_in.fill_(cap // 2)
+    rc = L.lpic_sort_tiles_static(2, nx, ny, 1, t3, src.data_ptr() + s_off, dst.data_ptr() + d_off,
+                                  cap, cnt_in.data_ptr(), cnt_out.data_ptr(), starts.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream)
+    assert rc == 0
+    torch.cuda.synchronize()
+    keep = (cell[:cap // 2] >= 0) & (cell[:cap // 2] < nx * ny)
+    assert int(cnt_out.item()) == int(keep.sum())
