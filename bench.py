@@ -11,13 +11,19 @@ HBM copy bandwidth as the roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
 
---workload selects the set-up (laser2d by default; thermal3d, laser3d,
-thermal2d, heating2d, ensemble, and qed2d, whose steps also run the nonlinear
-Compton and Breit-Wheeler passes, reported in a "qed" object).
+--workload selects the set-up (thermal3d, the 3D TSC roofline run, by default;
+laser2d, laser3d, thermal2d, heating2d, ensemble, and qed2d, whose steps also
+run the nonlinear Compton and Breit-Wheeler passes, reported in a "qed"
+object).  The default run adds, on the same line: the FP64 path on the same
+workload ("fp64"), the 2D laser-plasma workload ("laser2d"), the issue-rate
+roof of the fused kernel ("issue_roof"), and in the CPU-baseline leg the
+oracle's error on the run's own final state ("oracle_error") and the oracle
+timed on all host cores and on one ("cpu_baseline").
 
 Under torchrun each rank runs an independent replica of the workload (the
 problems do not exchange data; "scaling": "weak").  --impl reference times
-the FP64 CPU oracle on a bounded sample of the same workload on the host.
+the FP64 CPU oracle on a bounded sample of the same workload on the host's
+cores (the particle loop split over threads with private currents).
 """
 from __future__ import annotations
 
@@ -565,12 +571,75 @@ def run_e2e(args, st):
 
 
 # ------------------------------------------------------------------ the oracle
-def oracle_sample(args, budget_s, max_steps):
-    """Time the FP64 CPU oracle, as it stands (one thread), on a bounded
-    sample of the workload: the full x extent with the first 16 rows (2D),
-    the full x extent with 8 x 8 cells across (3D laser-target: the slab lies
-    along x) or a 32^3 box (3D thermal), same cell size, density profile and
-    particles per cell."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class _ThreadedOracleStep:
+    """One step of the FP64 oracle with its particle loop split over threads:
+    the unchanged oracle functions (Yee half steps, per-species push with
+    gather, Boris and Esirkepov deposit) called on per-thread slices of the
+    particles, each slice depositing into a private current array that shares
+    the grid's E and B; the private currents are summed before the second
+    half step (the OpenMP-over-patches scheme of Sec. 2.3, with threads in
+    place of patches).  The oracle releases the interpreter lock while it
+    runs, so the slices run concurrently."""
+
+    def __init__(self, O, g, species, threads):
+        import numpy as np
+        from concurrent.futures import ThreadPoolExecutor
+        self.O, self.g, self.threads = O, g, max(1, int(threads))
+        self.jobs = []
+        self.grids = []
+        for k in range(self.threads):
+            gk = O.Grid(g.dim, (g.nx, g.ny, g.nz)[:g.dim], (g.dx, g.dy, g.dz)[:g.dim], g.dt, g.order,
+                        absorb_x=g.absorb_x)
+            gk.E, gk.B = g.E, g.B
+            self.grids.append(gk)
+        for sp in species:
+            cuts = np.linspace(0, sp.n, self.threads + 1).astype(np.int64)
+            for k in range(self.threads):
+                a, b = int(cuts[k]), int(cuts[k + 1])
+                if b > a:
+                    part = O.Species(sp.q, sp.m, sp.x[:g.dim, a:b], sp.u[:, a:b], sp.w[a:b],
+                                     alive=sp.alive[a:b])
+                    self.jobs.append((k, part))
+        self.pool = ThreadPoolExecutor(max_workers=self.threads) if self.threads > 1 else None
+
+    def alive(self):
+        return sum(int(part.alive.sum()) for _, part in self.jobs)
+
+    def __call__(self, t):
+        O, g = self.O, self.g
+        O.maxwell_half(g, 0, t)
+        for gk in self.grids:
+            for c in range(3):
+                gk.J[c][...] = 0.0
+
+        def run(k):
+            for kk, part in self.jobs:
+                if kk == k:
+                    O.push_species(self.grids[k], part)
+
+        if self.pool is None:
+            run(0)
+        else:
+            list(self.pool.map(run, range(self.threads)))
+        for c in range(3):
+            g.J[c][...] = sum(gk.J[c] for gk in self.grids)
+        O.maxwell_half(g, 1, t + 0.5 * g.dt)
+
+
+def oracle_sample(args, budget_s, max_steps, threads=1):
+    """Time the FP64 CPU oracle on a bounded sample of the workload: the full
+    x extent with the first 16 rows (2D), the full x extent with 8 x 8 cells
+    across (3D laser-target: the slab lies along x) or a 32^3 box (3D
+    thermal), same cell size, density profile and particles per cell.  With
+    threads > 1 the particle loop runs on that many host threads (private
+    currents, summed); the QED set-up runs on one thread."""
     import numpy as np
     from oracle import oracle as O
     from paper_2607_13507_b300 import workloads as W
@@ -579,6 +648,7 @@ def oracle_sample(args, budget_s, max_steps):
         # the oracle's emission rate integrates the spectrum afresh for every
         # particle (about 0.07 s each): a 4 x 4-cell box
         sample = dict(n=(4, 4))
+        threads = 1
     elif wl.dim == 2:
         sample = dict(n=(wl.n[0], min(16, wl.n[1])))
     elif wl.laser is not None:
@@ -603,12 +673,20 @@ def oracle_sample(args, budget_s, max_steps):
         ids = np.concatenate([p.id for p in parts])
         tau = [O.qed_initial_tau(p.id, wl.seed) for p in parts]
         assert len(set(ids.tolist())) == len(ids)
+    stepper = _ThreadedOracleStep(O, g, sps, threads) if (threads > 1 and tau is None and pml is None) else None
+    if stepper is None:
+        threads = 1
     phots = []
     nemit = len(sps)
     t0 = time.perf_counter()
     steps = 0
     psteps = 0
     while steps < max_steps and (time.perf_counter() - t0) < budget_s:
+        if stepper is not None:
+            psteps += stepper.alive()
+            stepper(steps * wl.dt)
+            steps += 1
+            continue
         psteps += sum(int(sp.alive.sum()) for sp in sps)
         O.step(g, sps, steps * wl.dt)
         if tau is not None:
@@ -623,15 +701,88 @@ def oracle_sample(args, budget_s, max_steps):
         steps += 1
     el = time.perf_counter() - t0
     desc = (f"{'x'.join(str(v) for v in wl.n)} cells of the workload (same dx, profile, ppc), "
-            f"{npart} particles, {steps} steps, FP64 oracle, 1 thread")
-    return psteps / el, desc, steps, el
+            f"{npart} particles, {steps} steps, FP64 oracle, {threads} thread{'s' if threads > 1 else ''}")
+    return psteps / el, desc, steps, el, threads
+
+
+def oracle_error(state, n_sample=2000):
+    """The run's own final state against the oracle: 2000 particles drawn at
+    random are pushed by the FP64 oracle in the GPU's own (float) fields and
+    compared with the GPU's push of the same step (momenta relative to |u|,
+    positions in cells at the integer time), and the integer continuity
+    residual rho1 - rho0 + div J of that step over the whole grid (periodic
+    grids; interior columns with absorbing x), which the fixed-point deposit
+    makes exactly zero."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    G, stream, wl = state["G"], state["stream"], state["wl"]
+    if G.precision != 1:
+        return None
+    t = state["step"] * wl.dt
+    G.maxwell_half(0, t, stream)
+    G.zero_current(stream)
+    sp = max(G.species, key=lambda s: s.query(stream)[1])
+    G.sort(sp.id, stream)
+    st = sp.state(stream)
+    n = st["id"].shape[0]
+    rng = np.random.Generator(np.random.Philox(20261204))
+    pick = rng.choice(n, size=min(n_sample, n), replace=False)
+    ids = st["id"][pick]
+    rho0 = sp.charge(stream)
+    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x)
+    for c in range(3):
+        g.E[c][...] = G.E[c].cpu().numpy().astype(np.float64)
+        g.B[c][...] = G.B[c].cpu().numpy().astype(np.float64)
+    h = np.array(wl.h)[:, None]
+    u = st["u"][:, pick].astype(np.float64)
+    gam = np.sqrt(1.0 + (u ** 2).sum(0))
+    cell = st["cell"][pick].astype(np.int64)
+    coords = [cell % wl.n[0], (cell // wl.n[0]) % wl.n[1]]
+    if wl.dim == 3:
+        coords.append(cell // (wl.n[0] * wl.n[1]))
+    x_half = (np.stack(coords).astype(np.float64) + st["off"][:, pick].astype(np.float64)) * h
+    x_int = x_half - 0.5 * wl.dt * u[:wl.dim] / gam
+    osp = O.Species(sp.q, sp.m, x_int, u, st["w"][pick].astype(np.float64))
+    O.push_species(g, osp)
+    G.gather_push_deposit(sp.id, stream)
+    torch.cuda.synchronize()
+    st1 = sp.state(stream)
+    x1 = sp.positions_at_step(stream)
+    order = np.argsort(st1["id"])
+    pos = np.searchsorted(st1["id"][order], ids)
+    pos = np.clip(pos, 0, len(order) - 1)
+    rows = order[pos]
+    keep = (st1["id"][rows] == ids) & (osp.alive != 0)
+    ug = st1["u"][:, rows[keep]].astype(np.float64)
+    uo = osp.u[:, keep]
+    rel_u = float(np.max(np.linalg.norm(ug - uo, axis=0) / np.maximum(np.linalg.norm(uo, axis=0), 1e-30)))
+    diff = x1[:, rows[keep]] - osp.x[:wl.dim, keep]
+    L = np.array(wl.n)[:, None] * h
+    for d in range(wl.dim):
+        if d > 0 or not wl.absorb_x:
+            diff[d] = np.remainder(diff[d] + 0.5 * L[d], L[d]) - 0.5 * L[d]
+    dx = float(np.max(np.abs(diff) / h))
+    rho1 = sp.charge(stream)
+    J = G.J
+    div = (J[0] - torch.roll(J[0], 1, -1)) + (J[1] - torch.roll(J[1], 1, -2))
+    if wl.dim == 3:
+        div = div + (J[2] - torch.roll(J[2], 1, -3))
+    res = rho1 - rho0 + div
+    if wl.absorb_x:
+        res = res[..., 4:-4]
+    return {"species": "the most populous species", "sampled_particles": int(keep.sum()),
+            "momentum_rel_max": rel_u, "position_cells_max": dx,
+            "continuity_nonzero_nodes": int(torch.count_nonzero(res).item()),
+            "continuity_nodes": int(res.numel()),
+            "reference": "FP64 oracle push of the sample in the GPU's fields, same step"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return None
-    val, desc, steps, el = oracle_sample(args, budget_s=max(10.0, 0.5 * (args.steps + args.warmup)),
-                                         max_steps=args.steps + args.warmup)
+    val, desc, steps, el, used = oracle_sample(args, budget_s=max(10.0, 0.5 * (args.steps + args.warmup)),
+                                               max_steps=args.steps + args.warmup, threads=host_cores())
     return {
         "metric": metric_name(args.workload),
         "value": val, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -640,11 +791,60 @@ def run_reference(args, rank, world):
         "data": "synthetic (seeded Philox initial conditions)",
         "config": {"workload": WORKLOADS[args.workload][0], "sample": desc},
         "impl": "reference",
-        "cpu_baseline": {"value": val, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": val, "unit": "particle-steps/s", "cores": used, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": val, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
+
+
+def issue_roof(res, workload, clocks):
+    """The fused kernel against the instruction-issue roof: warp instructions
+    per particle from the committed ncu capture of the same kernel source
+    (profiles/issue.json) times the measured particle rate of the kernel,
+    over SMs x 4 schedulers x the median SM clock seen in the timed region."""
+    path = os.path.join(ROOT, "profiles", "issue.json")
+    try:
+        rec = json.load(open(path)).get(workload)
+    except Exception:
+        rec = None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    import torch
+    nsm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or 2032.0
+    rate = res.get("gpd_particle_steps_per_s")
+    if not rate:
+        return None
+    achieved = rec["warp_inst_per_particle"] * rate
+    peak = nsm * 4 * mhz * 1e6
+    return {"warp_inst_per_particle": rec["warp_inst_per_particle"], "achieved": achieved, "peak": peak,
+            "unit": "warp instructions/s", "frac": achieved / peak, "captured": rec.get("captured")}
+
+
+def side_line(args, workload, precision, steps, warmup):
+    """The same contract's numbers for another workload or precision, run in
+    this process after the main line (no e2e, no baseline)."""
+    import copy
+    import torch
+    sub = copy.copy(args)
+    sub.workload, sub.precision, sub.steps, sub.warmup = workload, precision, steps, warmup
+    sub.pre_steps = None
+    sub.tile, sub.block_particles, sub.sort_interval = None, 0, 0
+    res, state = run_b300(sub, 0, 1, 0)
+    del state
+    torch.cuda.empty_cache()
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "gpd_particle_steps_per_s", "clocks")
+    out = {k: res[k] for k in keep if k in res}
+    out["workload"] = res["config"]["workload"]
+    out["particles"] = res["config"]["particles"]
+    r = res["roofline"]
+    out["roofline"] = {k: r[k] for k in ("bound", "kernel", "achieved", "peak", "unit", "frac", "peak_source",
+                                         "bytes_per_particle_step", "launch_ms", "traffic")}
+    if precision == "fp32":
+        out["config"] = {"tuning": res["config"].get("tuning")}
+        out["issue_roof"] = issue_roof(res, workload, res.get("clocks"))
+    return out
 
 
 def main():
@@ -653,7 +853,7 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["b300", "reference"], default="b300")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="laser2d")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="thermal3d")
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--pre-steps", type=int, default=None,
                     help="untimed steps before warm-up (default: bring the laser onto the target)")
@@ -674,6 +874,9 @@ def main():
                     help="time the unfused path (gather stage + push/deposit stage) instead of the fused kernel")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side", action="store_true",
+                    help="skip the FP64 and 2D laser-plasma lines of the default run")
+    ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -703,13 +906,34 @@ def main():
         return
     res, state = run_b300(args, rank, world, local_rank)
     if rank == 0:
+        if args.precision == "fp32" and not args.unfused:
+            res["issue_roof"] = issue_roof(res, args.workload, res.get("clocks"))
         if not args.no_e2e:
             res["e2e"] = run_e2e(args, state)
+        leg = None
         if world == 1 and not args.no_cpu_baseline:
-            val, desc, steps, el = oracle_sample(args, args.cpu_budget, 60)
-            res["cpu_baseline"] = {"value": val, "unit": "particle-steps/s", "cores": 1,
-                                   "kind": "oracle", "sample": desc}
+            # the oracle's error on this run's state, before the state goes
+            leg = {"oracle_error": oracle_error(state)} if args.precision == "fp32" and not args.unfused else {}
+        del state
+        torch.cuda.empty_cache()
+        default_run = (args.workload == "thermal3d" and args.n3 is None and args.precision == "fp32"
+                       and world == 1 and not args.no_side and not args.unfused)
+        if default_run:
+            res["fp64"] = side_line(args, "thermal3d", "fp64", args.fp64_steps, 3)
+            res["laser2d"] = side_line(args, "laser2d", "fp32", 20, 3)
+        if leg is not None:
+            n = host_cores()
+            val, desc, steps, el, used = oracle_sample(args, args.cpu_budget, 60, threads=n)
+            v1, d1, s1, e1, _ = oracle_sample(args, args.cpu_budget, 60, threads=1)
+            res["cpu_baseline"] = {"value": val, "unit": "particle-steps/s", "cores": used, "nproc": n,
+                                   "kind": "oracle", "sample": desc,
+                                   "one_core": {"value": v1, "unit": "particle-steps/s", "cores": 1,
+                                                "sample": d1}}
+            if "oracle_error" in leg:
+                res["oracle_error"] = leg["oracle_error"]
         print(json.dumps(res), flush=True)
+    else:
+        del state
     if world > 1:
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
