@@ -75,12 +75,12 @@ typedef enum {
 
 /* device status bits (lpic_check_status) */
 #define LPIC_ST_CFL       0x1u  /* a particle moved >= 1 cell in a step */
-#define LPIC_ST_HALO      0x2u  /* reserved (particles beyond a tile's margin take the
-                                   global-memory path instead) */
+#define LPIC_ST_HALO      0x2u  /* a particle outside its tile's box where no global-
+                                   memory path exists (unfused stages, ensembles); it is
+                                   skipped */
 #define LPIC_ST_NAN       0x4u  /* non-finite momentum */
 #define LPIC_ST_OUTSIDE   0x8u  /* a deposit or gather reached past an absorbing edge */
 #define LPIC_ST_OVERFLOW  0x10u /* a fixed-point value exceeded its bound */
-#define LPIC_ST_TIMEOUT   0x20u /* a bounded device wait gave up */
 
 enum { LPIC_FP64 = 0, LPIC_FP32_FIXED = 1 };
 
@@ -267,7 +267,7 @@ lpic_status lpic_push_deposit_fields(lpic_grid_t grid, int species_id, const flo
 lpic_status lpic_step_resolved(lpic_grid_t grid, double t, int species_id, lpic_grid_t aux,
                                cudaStream_t stream);
 
-/* Gauss's law diagnostic/* Gauss's law diagnostic (Sec. 3.2; Sec. 4.1 checks charge conservation):
+/* Gauss's law diagnostic (Sec. 3.2; Sec. 4.1 checks charge conservation):
  * the discrete divergence of the current E at the integer nodes,
  * sum_d (E_d(i+1/2) - E_d(i-1/2)) / h_d, in double, written to the caller's
  * device array out[nz][ny][fx] (overwritten; periodic wrap, E_x = 0 below an
@@ -397,9 +397,9 @@ lpic_status lpic_qed_initial_tau(lpic_grid_t grid, float *tau, long long n_ids, 
  * Photons are appended to `photon_species` (a species added with m = 0 and
  * q = 0), which gets new particle ids count, count + 1, ... (count = its
  * particles at add time) in an unspecified order.  A particle id outside
- * [0, n_ids), or more photons than the photon species' capacity (the extra
- * photons are dropped, the momentum loss is still applied), sets
- * LPIC_ST_OVERFLOW; a gather past an absorbing edge sets LPIC_ST_OUTSIDE and
+ * [0, n_ids), or more photons than the photon species' capacity (an emitter
+ * whose photon finds no room keeps its momentum and its spent depth, and
+ * emits at a later pass), sets LPIC_ST_OVERFLOW; a gather past an absorbing edge sets LPIC_ST_OUTSIDE and
  * skips the particle.  step is the counter word (0 <= step < 2^32).
  * Asynchronous. */
 lpic_status lpic_qed_compton(lpic_grid_t grid, int electron_species, int photon_species, float *tau,
@@ -431,8 +431,8 @@ lpic_status lpic_species_set_next_id(lpic_grid_t grid, int species_id, long long
  * One pass over `photon_species` with depths tau[photon id] (n_ids entries).
  * New particles get ids count, count + 1, ... of their species; a pair that
  * exceeds a capacity or whose weight exceeds a receiving species' bound
- * (max_weight at add time) is dropped and sets LPIC_ST_OVERFLOW (its photon
- * is still removed).  The two pair species need a sort before their next
+ * (max_weight at add time) is not created and sets LPIC_ST_OVERFLOW: its
+ * photon stays, with its spent depth, and converts at a later pass.  The two pair species need a sort before their next
  * push (lpic_step does it).  Asynchronous. */
 lpic_status lpic_qed_breit_wheeler(lpic_grid_t grid, int photon_species, int electron_species,
                                    int positron_species, float *tau, long long n_ids, long long step,

@@ -102,7 +102,7 @@ struct lpic_grid {
     double* d_acc = nullptr;
     unsigned long long* d_cnt = nullptr;
     bool started = false;
-    int nsm = 148;
+    int nsm = 0;                 // SMs of the device (queried at create)
     size_t smem32 = 0;
     long long launches = 0;
     int P = 4096;                              // particles per work item (FP32 path)
@@ -570,9 +570,11 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         }
     }
     int dev = 0;
-    cudaDeviceProp prop{};
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
-        g->nsm = prop.multiProcessorCount;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || g->nsm < 1) {
+        delete g;
+        return fail(LPIC_ECUDA, "cannot query the device's SM count");
+    }
     const size_t fbytes = d.precision == LPIC_FP64 ? 8 : 4;
     const int plane = d.ny * nz;
     if (cudaMalloc(&g->d_status, 64) != cudaSuccess ||
@@ -1156,7 +1158,7 @@ lpic_status lpic_check_status(lpic_grid_t g, cudaStream_t st, unsigned* bits) {
 // ======================================================================= ensembles
 struct lpic_ensemble {
     std::vector<lpic_grid_t> grids;
-    int dim = 2, order = 1, nsm = 148, blocks = 1;
+    int dim = 2, order = 1, nsm = 0, blocks = 1;
     int ninst = 0, nslots = 0;
     size_t smem = 0;
     EnsField* d_fields = nullptr;

@@ -261,7 +261,14 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
         const float umag = sqrtf(u2);
         const float k = xi * gam;
         const int j = atomicAdd(A.ph_n, 1);
-        if ((long long)j < A.ph_cap) {
+        if ((long long)j >= A.ph_cap) {
+            // no room for the photon: no event this time, so the emitter keeps
+            // its momentum and its spent depth, and emits once room exists
+            set_status(A.st, LPIC_ST_OVERFLOW);
+            A.tau[id] = t;
+            continue;
+        }
+        {
             const float s = k / umag;
             A.ph.cell[j] = cell;
 #pragma unroll
@@ -280,8 +287,6 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
                     set_status(A.st, LPIC_ST_OVERFLOW);
                 }
             }
-        } else {
-            set_status(A.st, LPIC_ST_OVERFLOW);
         }
         const float keep = 1.0f - k / umag;
 #pragma unroll
@@ -457,11 +462,11 @@ __global__ void __launch_bounds__(256) k_qed_bw32(BwArgs A) {
         const float r = fminf((float)u01d(o.x), 0.99999994f);
         const float eta = bw_eta(A.T, chi, r);
         const float w = p.w[i];
-        p.cell[i] = -1;
         const int je = atomicAdd(A.el_n, 1), jp = atomicAdd(A.po_n, 1);
         // a pair that does not fit (capacity, or a weight above the receiving
-        // species' fixed-point bound) is dropped; a slot already taken is
-        // written as a removed particle, which the next sort discards
+        // species' fixed-point bound) is not created: the photon stays, with
+        // its spent depth, and converts at a later pass; a slot already taken
+        // is written as a removed particle, which the next sort discards
         const bool fits = (long long)je < A.el_cap && (long long)jp < A.po_cap && w <= A.el_wmax &&
                           w <= A.po_wmax;
         if (!fits) {
@@ -470,6 +475,7 @@ __global__ void __launch_bounds__(256) k_qed_bw32(BwArgs A) {
             if ((long long)jp < A.po_cap) A.po.cell[jp] = -1;
             continue;
         }
+        p.cell[i] = -1;
         A.el.cell[je] = cell;
         A.po.cell[jp] = cell;
 #pragma unroll

@@ -17,7 +17,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "liblpic.so")
 
 FP64, FP32_FIXED = 0, 1
-ST_CFL, ST_HALO, ST_NAN, ST_OUTSIDE, ST_OVERFLOW, ST_TIMEOUT = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
+ST_CFL, ST_HALO, ST_NAN, ST_OUTSIDE, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
 
 STATUS = {0: "LPIC_OK", 1: "LPIC_EINVAL", 2: "LPIC_ENOMEM", 3: "LPIC_ECUDA", 4: "LPIC_EDEVICE",
           5: "LPIC_EUNSUPPORTED"}

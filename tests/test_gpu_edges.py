@@ -125,3 +125,26 @@ def test_smallest_grid_smaller_than_a_tile(precision):
     for c in range(3):
         if np.linalg.norm(g.E[c]) > 0:
             assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < tol
+
+
+def test_particle_outside_its_tile_sets_halo_status_in_the_unfused_stage():
+    """The unfused stages run on freshly sorted particles, without a
+    global-memory path: a particle that a caller moved out of its tile's box
+    after the sort is skipped and raises LPIC_ST_HALO (made on the host: one
+    cell index rewritten in the buffer, a valid cell of the grid)."""
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal2d(n=64, ppc=2, vth=0.05, order=2, precision="fp32")
+    G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(16, 16))
+    sp = G.add_species(W.load_all(wl)[0])
+    G.sort(sp.id)
+    torch.cuda.synchronize()
+    cur, n = sp.query()
+    cells = sp._views(cur)["cell"]
+    c0 = int(cells[0].item())
+    x, y = c0 % 64, c0 // 64
+    cells[0] = ((y + 32) % 64) * 64 + (x + 32) % 64          # two tiles away in x and y
+    torch.cuda.synchronize()
+    G.gather_fields(sp.id)
+    torch.cuda.synchronize()
+    assert G.check_status() & lpic.ST_HALO
+    assert G.check_status() == 0                                # read and cleared

@@ -7,7 +7,10 @@
 * The 2D laser-plasma at full size (2048 x 1024, 67 M particles, TSC, FP32
   fixed point): a random sample of particles pushed by the oracle in the
   GPU's own fields agrees with the GPU push to float32 precision, and the
-  integer continuity identity holds exactly on the whole grid.
+  integer continuity identity holds exactly on the whole grid.  The same
+  check at full size for the 3D thermal plasma (256^3, TSC), the 3D
+  laser-target (512 x 256^2, CIC, laser on the slab) and one member of the
+  96-member ensemble stepped through the batched path.
 """
 import numpy as np
 import pytest
@@ -15,7 +18,7 @@ import pytest
 from oracle import oracle as O
 from paper_2607_13507_b300 import workloads as W
 
-from pic_cases import gpu_case, oracle_case
+from pic_cases import gpu_case, oracle_case, sampled_push_check
 
 pytestmark = pytest.mark.gpu
 
@@ -149,3 +152,76 @@ def test_laser2d_full_size_sampled_push_and_exact_continuity():
     div = (J[0] - torch.roll(J[0], 1, 2)) + (J[1] - torch.roll(J[1], 1, 1))
     res = (rho1 - rho0 + div)[:, :, 4:-4]
     assert torch.count_nonzero(res).item() == 0
+
+
+def test_thermal3d_full_size_sampled_push_and_exact_continuity():
+    """The 3D roofline workload at its full size (256^3, TSC, 134 M
+    particles, 8x8x4 tiles of 4096 particles per block): after three steps,
+    2000 particles drawn at random are pushed by the oracle in the GPU's own
+    fields (momenta <= 1e-5 relative, positions <= 1e-5 cell), and the
+    integer continuity of the step holds exactly on every node."""
+    from paper_2607_13507_b300 import lpic
+    wl = W.thermal3d()
+    parts = W.load_all(wl)
+    G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(8, 8, 4), block_particles=4096)
+    G.add_species(parts[0])
+    del parts
+    for s in range(3):
+        G.step(s * wl.dt)
+    rel_u, dx, nonzero = sampled_push_check(G, wl, G.species[0], 3 * wl.dt)
+    assert rel_u < 1e-5, rel_u
+    assert dx < 1e-5, dx
+    assert nonzero == 0
+
+
+def test_laser3d_full_size_sampled_push_and_exact_continuity():
+    """The 3D laser-target workload at its full size (512x256^2, CIC, 134 M
+    particles, slab tiles crowded next to empty vacuum tiles) after 400
+    steps, with the laser on the slab: electrons and protons each checked on
+    2000 particles against the oracle and by exact integer continuity."""
+    from paper_2607_13507_b300 import lpic
+    wl = W.laser3d()
+    parts = W.load_all(wl)
+    G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(8, 8, 4), block_particles=8192)
+    for p in parts:
+        G.add_species(p)
+    del parts
+    steps = 400
+    for s in range(steps):
+        G.step(s * wl.dt)
+    torch.cuda.synchronize()
+    assert G.check_status() == 0
+    t = steps * wl.dt
+    for k, sp in enumerate(G.species):
+        rel_u, dx, nonzero = sampled_push_check(G, wl, sp, t, seed=7 + k)
+        assert rel_u < 1e-5, (k, rel_u)
+        assert dx < 1e-5, (k, dx)
+        assert nonzero == 0, k
+        # the next species starts a fresh step on the same fields
+        G.maxwell_half(1, t + 0.5 * wl.dt)
+        t += wl.dt
+
+
+def test_ensemble_member_full_size_sampled_push_and_exact_continuity():
+    """The 96-member batched ensemble (sides 128-768, 4-64 particles per cell,
+    one persistent particle kernel over the device queue, replayed graphs):
+    after three ensemble steps, member 0 is checked like the single grids."""
+    from paper_2607_13507_b300 import lpic
+    members = W.ensemble()
+    grids = []
+    for wl in members:
+        G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(16, 8))
+        G.add_species(W.load_all(wl)[0])
+        grids.append(G)
+    ens = lpic.Ensemble(grids)
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    ens.graph_steps(3, side)
+    torch.cuda.synchronize()
+    assert ens.check_status(side) == 0
+    ens.close()
+    wl, G = members[0], grids[0]
+    rel_u, dx, nonzero = sampled_push_check(G, wl, G.species[0], 3 * wl.dt)
+    assert rel_u < 1e-5, rel_u
+    assert dx < 1e-5, dx
+    assert nonzero == 0

@@ -204,6 +204,10 @@ def test_emission_passes_match_oracle(order):
 
 
 def test_photon_capacity_overflow_sets_status():
+    """More emissions than photon slots: the status is set, 64 events take
+    place (emitter recoil, new depth) and conserve momentum with their
+    photons, and every other emitter keeps its momentum and its spent depth,
+    so that it emits at a later pass once room exists."""
     from paper_2607_13507_b300 import lpic
     wl, G = _grid()
     n = 1024
@@ -211,12 +215,26 @@ def test_photon_capacity_overflow_sets_status():
     ph = G.add_empty_species(0.0, 0.0, 64)
     g = O.Grid(2, wl.n, wl.h, wl.dt, 1)
     _set_fields(G, g, wl, E0=200.0, B0=200.0)
+    st0 = e.state()
+    p0 = (st0["u"].astype(np.float64) * st0["w"]).sum(1)
     tau = torch.zeros(n, dtype=torch.float32, device=G.device)    # every particle emits
     G.qed_compton(e, ph, tau, 0)
     bits = G.check_status()
     assert bits & lpic.ST_OVERFLOW
     assert ph.query()[1] == 64
-    assert torch.all(tau > 0)
+    t = tau.cpu().numpy()
+    st1 = e.state()
+    order0, order1 = np.argsort(st0["id"]), np.argsort(st1["id"])
+    u0, u1 = st0["u"][:, order0], st1["u"][:, order1]
+    emitted = t[st1["id"][order1]] > 0
+    assert emitted.sum() == 64
+    # emitters without a photon: momentum and (non-positive) depth unchanged
+    assert np.array_equal(u1[:, ~emitted], u0[:, ~emitted])
+    assert np.all(t[st1["id"][order1][~emitted]] <= 0)
+    # the 64 events conserve momentum with their photons (float rounding)
+    sph = ph.state()
+    p1 = (st1["u"].astype(np.float64) * st1["w"]).sum(1) + (sph["u"].astype(np.float64) * sph["w"]).sum(1)
+    assert np.linalg.norm(p1 - p0) <= 1e-5 * np.abs(st0["u"] * st0["w"]).sum()
 
 
 def test_tau_array_too_short_sets_status():
@@ -463,6 +481,12 @@ def test_pair_capacity_and_weight_bound_overflow():
         # be dropped while one of its slots fits: at most cap pairs survive
         assert po.query()[1] == kept
         assert kept == 0 if wmax < 1.0 else 0 < kept <= cap
+        # a photon whose pair was not created stays, with its spent depth,
+        # and the photons that remain and the pairs made carry the momentum
+        # of all photons before the pass
+        assert ph.query()[1] == n - kept
+        sph = ph.state()
+        assert np.all(tau.cpu().numpy()[sph["id"]] <= 0)
 
 
 # ------------------------------------------------------------------ 3D passes
