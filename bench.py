@@ -15,8 +15,9 @@ HBM copy bandwidth as the roofline.
 laser2d, laser3d, thermal2d, heating2d, ensemble, and qed2d, whose steps also
 run the nonlinear Compton and Breit-Wheeler passes, reported in a "qed"
 object).  The default run adds, on the same line: the FP64 path on the same
-workload ("fp64"), the 2D laser-plasma workload ("laser2d"), the issue-rate
-roof of the fused kernel ("issue_roof"), and in the CPU-baseline leg the
+workload ("fp64"), the 2D laser-plasma workload ("laser2d"; with FP64 master
+fields, "laser2d_fp64_fields"), the issue-rate roof of the fused kernel
+("issue_roof"), and in the CPU-baseline leg the
 oracle's error on the run's own final state ("oracle_error") and the oracle
 timed on all host cores and on one ("cpu_baseline").
 
@@ -287,7 +288,7 @@ def run_b300(args, rank, world, local_rank):
     tuned = tuned_choice(args, wl)
     parts = W.load_all(wl)
     G = lpic.grid_for(wl, prec, device=dev, tile=tuned["tile"], block_particles=tuned["block_particles"],
-                      sort_interval=tuned["sort_interval"])
+                      sort_interval=tuned["sort_interval"], maxwell_fp64=getattr(args, "maxwell_fp64", False))
     for p in parts:
         # a QED set-up keeps room for the pairs created into the lepton species
         cap = (p.n * 9 // 8 + 63) // 64 * 64 if wl.qed_eps_ref > 0 else None
@@ -421,7 +422,8 @@ def run_b300(args, rank, world, local_rank):
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f32 (int64 fixed-point current)" if args.precision == "fp32" else "f64",
+            "dtype": ("f32 (int64 fixed-point current" + (", f64 fields)" if getattr(args, "maxwell_fp64", False)
+                                                          else ")")) if args.precision == "fp32" else "f64",
             "data": "synthetic (seeded Philox initial conditions)",
             "config": {
                 "workload": WORKLOADS[args.workload][0] + (
@@ -822,13 +824,14 @@ def issue_roof(res, workload, clocks):
             "unit": "warp instructions/s", "frac": achieved / peak, "captured": rec.get("captured")}
 
 
-def side_line(args, workload, precision, steps, warmup):
+def side_line(args, workload, precision, steps, warmup, maxwell_fp64=False):
     """The same contract's numbers for another workload or precision, run in
     this process after the main line (no e2e, no baseline)."""
     import copy
     import torch
     sub = copy.copy(args)
     sub.workload, sub.precision, sub.steps, sub.warmup = workload, precision, steps, warmup
+    sub.maxwell_fp64 = maxwell_fp64
     sub.pre_steps = None
     sub.tile, sub.block_particles, sub.sort_interval = None, 0, 0
     res, state = run_b300(sub, 0, 1, 0)
@@ -877,6 +880,8 @@ def main():
     ap.add_argument("--no-side", action="store_true",
                     help="skip the FP64 and 2D laser-plasma lines of the default run")
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--maxwell-fp64", action="store_true",
+                    help="FP32 particles with FP64 master fields (Maxwell half steps in double)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -921,6 +926,7 @@ def main():
         if default_run:
             res["fp64"] = side_line(args, "thermal3d", "fp64", args.fp64_steps, 3)
             res["laser2d"] = side_line(args, "laser2d", "fp32", 20, 3)
+            res["laser2d_fp64_fields"] = side_line(args, "laser2d", "fp32", 20, 3, maxwell_fp64=True)
         if leg is not None:
             n = host_cores()
             val, desc, steps, el, used = oracle_sample(args, args.cpu_budget, 60, threads=n)

@@ -126,6 +126,13 @@ typedef struct {
      * 2 pml_cells + 8 <= nx; ignored unless absorb_x = 2. */
     int pml_cells;
     double pml_m, pml_sigma_max, pml_kappa_max, pml_alpha_max;
+    /* FP32_FIXED path only: 1 keeps FP64 master fields (E and B are double
+     * arrays; the Maxwell half steps of Sec. 3.2, Eq. 1-4, run in double with
+     * the int64 current converted in double, and the particle kernels round
+     * the fields to float once, when the tile kernel stages them in shared
+     * memory).  The Gauss-law residual then stays constant to double
+     * rounding.  Not with the QED passes or in an ensemble. */
+    int maxwell_fp64;
 } lpic_grid_desc;
 
 typedef struct {

@@ -223,7 +223,10 @@ GpdArgs gpd_args(lpic_grid* g, Species& s, bool count_next) {
     box_divisors(g, t);
     const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
     const float sq = (float)std::ldexp(s.q, g->F);
-    return GpdArgs{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), ptr3<unsigned long long>(g->d.J),
+    const bool f64 = g->d.maxwell_fp64 != 0;
+    return GpdArgs{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B),
+                   ptr3<const double>(g->d.E), ptr3<const double>(g->d.B), f64 ? 1 : 0,
+                   ptr3<unsigned long long>(g->d.J),
                    p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
                    (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status, nullptr, 0};
 }
@@ -516,6 +519,9 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     if (d.block_particles != 0 && (d.block_particles < 256 || d.block_particles > (1 << 20)))
         return fail(LPIC_EINVAL, "block_particles must be 0 or in [256, 2^20]");
     if (d.sort_interval < 0 || d.sort_interval > 64) return fail(LPIC_EINVAL, "sort_interval must be in [0, 64]");
+    if (d.maxwell_fp64 != 0 && d.maxwell_fp64 != 1) return fail(LPIC_EINVAL, "maxwell_fp64 must be 0 or 1");
+    if (d.maxwell_fp64 && d.precision != LPIC_FP32_FIXED)
+        return fail(LPIC_EINVAL, "maxwell_fp64 applies to the FP32_FIXED path (the FP64 path has FP64 fields)");
     for (int c = 0; c < 3; ++c)
         if (!d.E[c] || !d.B[c] || !d.J[c]) return fail(LPIC_EINVAL, "field pointer %d is NULL", c);
     auto* g = new (std::nothrow) lpic_grid;
@@ -575,7 +581,7 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
         delete g;
         return fail(LPIC_ECUDA, "cannot query the device's SM count");
     }
-    const size_t fbytes = d.precision == LPIC_FP64 ? 8 : 4;
+    const size_t fbytes = (d.precision == LPIC_FP64 || d.maxwell_fp64) ? 8 : 4;
     const int plane = d.ny * nz;
     if (cudaMalloc(&g->d_status, 64) != cudaSuccess ||
         cudaMalloc(&g->d_clock, 64) != cudaSuccess ||
@@ -880,6 +886,9 @@ lpic_status lpic_push_deposit_fields(lpic_grid_t g, int sid, const float* fields
 }
 
 static lpic_status maxwell_any(lpic_grid_t g, int half, double t, cudaStream_t st, const double* clock) {
+    if (g->d.precision == LPIC_FP32_FIXED && g->d.maxwell_fp64)
+        return g->d.dim == 3 ? maxwell_impl<3, double, long long>(g, half, t, st, clock)
+                             : maxwell_impl<2, double, long long>(g, half, t, st, clock);
     if (g->d.precision == LPIC_FP32_FIXED)
         return g->d.dim == 3 ? maxwell_impl<3, float, long long>(g, half, t, st, clock)
                              : maxwell_impl<2, float, long long>(g, half, t, st, clock);
@@ -932,8 +941,8 @@ lpic_status lpic_step_resolved(lpic_grid_t g, double t, int sid, lpic_grid_t aux
     const lpic_grid_desc &a = aux->d, &d = g->d;
     if (a.dim != d.dim || a.nx != d.nx || a.ny != d.ny || a.nz != d.nz || a.dx != d.dx || a.dy != d.dy ||
         a.dz != d.dz || a.dt != d.dt || a.precision != d.precision || a.absorb_x != d.absorb_x ||
-        (a.absorb_x == 2 && a.pml_cells != d.pml_cells))
-        return fail(LPIC_EINVAL, "aux must have the grid's geometry, time step, precision and x boundary");
+        (a.absorb_x == 2 && a.pml_cells != d.pml_cells) || a.maxwell_fp64 != d.maxwell_fp64)
+        return fail(LPIC_EINVAL, "aux must have the grid's geometry, time step, precision, field precision and x boundary");
     if (!aux->sp.empty()) return fail(LPIC_EINVAL, "aux must hold no species");
     auto aux_half = [&](int half, double th) -> lpic_status {
         for (int c = 0; c < 3; ++c) aux->jscale[c] = g->jscale[c];
@@ -1054,7 +1063,7 @@ lpic_status lpic_div_e(lpic_grid_t g, double* out, cudaStream_t st) {
     if (!out) return fail(LPIC_EINVAL, "out is NULL");
     const FastDiv dfx = make_fastdiv((unsigned)g->geo.fx), dny = make_fastdiv((unsigned)g->d.ny);
     const int nb = grid_blocks(g->nfield, g->nsm, 16);
-    if (g->d.precision == LPIC_FP32_FIXED)
+    if (g->d.precision == LPIC_FP32_FIXED && !g->d.maxwell_fp64)
         k_div_e<float><<<nb, 256, 0, st>>>(g->geo, ptr3<const float>(g->d.E), out, dfx, dny);
     else
         k_div_e<double><<<nb, 256, 0, st>>>(g->geo, ptr3<const double>(g->d.E), out, dfx, dny);
@@ -1095,7 +1104,7 @@ lpic_status lpic_diagnostics(lpic_grid_t g, lpic_diag* out, cudaStream_t st) {
     }
     const double dV = g->d.dx * g->d.dy * (g->d.dim == 3 ? g->d.dz : 1.0);
     const int nb = grid_blocks(g->nfield, g->nsm, 8);
-    if (g->d.precision == LPIC_FP32_FIXED)
+    if (g->d.precision == LPIC_FP32_FIXED && !g->d.maxwell_fp64)
         k_diag_field<float><<<nb, 256, 0, st>>>(ptr3<const float>(g->d.E), ptr3<const float>(g->d.B), g->nfield, dV, g->d_acc);
     else
         k_diag_field<double><<<nb, 256, 0, st>>>(ptr3<const double>(g->d.E), ptr3<const double>(g->d.B), g->nfield, dV, g->d_acc);
@@ -1269,6 +1278,7 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
         const lpic_grid_t g = grids[i];
         if (!g) return fail(LPIC_EINVAL, "grid %d is NULL", i);
         if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "ensembles need the FP32 path");
+        if (g->d.maxwell_fp64) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles keep float fields (no maxwell_fp64)", i);
         if (g->d.dim != g0->d.dim || g->d.shape_order != g0->d.shape_order)
             return fail(LPIC_EINVAL, "grid %d: dimension and shape order must match grid 0", i);
         for (int k = 0; k < 3; ++k)
@@ -1332,6 +1342,7 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
                 const float k = (float)(s.q * g->d.dt / (2.0 * s.m));
                 const float sq = (float)std::ldexp(s.q, g->F);
                 ha[b].push_back(GpdArgs{g->geo, ptr3<const float>(g->d.E), ptr3<const float>(g->d.B),
+                                        ptr3<const double>(g->d.E), ptr3<const double>(g->d.B), 0,
                                         ptr3<unsigned long long>(g->d.J), pv, t, g->dec, k, sq,
                                         (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
                                         (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status});
@@ -1462,6 +1473,7 @@ lpic_status lpic_ensemble_launches(lpic_ensemble_t e, long long* launches) {
 lpic_status lpic_qed_init(lpic_grid_t g, double eps_ref, uint64_t seed, cudaStream_t st) {
     if (lpic_status r = check_grid(g)) return r;
     if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "QED events need the FP32 path");
+    if (g->d.maxwell_fp64) return fail(LPIC_EUNSUPPORTED, "QED events read float fields (no maxwell_fp64)");
     if (!(eps_ref > 0) || !std::isfinite(eps_ref)) return fail(LPIC_EINVAL, "eps_ref must be positive");
     if (!g->d_qtab) {
         const QedHostTables H = qed_build_tables(1e-4, 1e3, 32, 513);

@@ -589,12 +589,13 @@ template <int DIM>
 struct LoadGlobal {
     const Geo* g;
     const float* F[6];
+    const double* F64[6];     // FP64 master fields, rounded to float (when set)
     int gc[3];
     bool* outside;
     __device__ inline float operator()(int comp, int x, int y, int z) const {
         const long long m = fidx(*g, gc[0] + x - 2, gc[1] + y - 2, DIM == 3 ? gc[2] + z - 2 : 0);
         if (m < 0) { *outside = true; return 0.0f; }
-        return F[comp][m];
+        return F64[0] ? (float)F64[comp][m] : F[comp][m];
     }
 };
 
@@ -737,6 +738,8 @@ struct Move {
 struct GpdArgs {
     Geo g;
     Ptr3<const float> E, B;
+    Ptr3<const double> E64, B64;   // FP64 master fields (used when f64 is set)
+    int f64;
     Ptr3<unsigned long long> J;
     P32 p;
     Tiles t;
@@ -820,9 +823,15 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
         const int q = fdiv(r, t.fG0), lx = r - q * G0;
         const int lz = (DIM == 3) ? fdiv(q, t.fG1) : 0, ly = q - lz * G1;
         const long long m = fidx_near(g, t0[0] - 1 + lx, t0[1] - 1 + ly, DIM == 3 ? t0[2] - 1 + lz : 0);
-        const float* src = c == 0 ? A.E.p[0] : c == 1 ? A.E.p[1] : c == 2 ? A.E.p[2]
-                         : c == 3 ? A.B.p[0] : c == 4 ? A.B.p[1] : A.B.p[2];
-        sF[idx] = (m < 0) ? 0.0f : __ldg(src + m);
+        if (A.f64) {
+            const double* src = c == 0 ? A.E64.p[0] : c == 1 ? A.E64.p[1] : c == 2 ? A.E64.p[2]
+                              : c == 3 ? A.B64.p[0] : c == 4 ? A.B64.p[1] : A.B64.p[2];
+            sF[idx] = (m < 0) ? 0.0f : (float)__ldg(src + m);
+        } else {
+            const float* src = c == 0 ? A.E.p[0] : c == 1 ? A.E.p[1] : c == 2 ? A.E.p[2]
+                             : c == 3 ? A.B.p[0] : c == 4 ? A.B.p[1] : A.B.p[2];
+            sF[idx] = (m < 0) ? 0.0f : __ldg(src + m);
+        }
     }
     for (int q = tid; q < (L.off_p - L.off_r) / 4; q += kGpdThreads)
         reinterpret_cast<int4*>(sR)[q] = make_int4(0, 0, 0, 0);
@@ -1171,6 +1180,8 @@ __global__ void __launch_bounds__(256) k_gpd32_escape(GpdArgs A) {
             float fld[6];
             bool outside = false;
             const LoadGlobal<DIM> ld{&g, {E.p[0], E.p[1], E.p[2], B.p[0], B.p[1], B.p[2]},
+                                     {A.f64 ? A.E64.p[0] : nullptr, A.E64.p[1], A.E64.p[2], A.B64.p[0],
+                                      A.B64.p[1], A.B64.p[2]},
                                      {gc[0], gc[1], gc[2]}, &outside};
             gather32<DIM, ORDER>(ld, nx_, ny_, nz_, hx_, hy_, hz_, fld);
             if (outside) set_status(st, LPIC_ST_OUTSIDE);

@@ -56,7 +56,7 @@ class GridDesc(ctypes.Structure):
                 ("J", ctypes.c_void_p * 3), ("laser", ctypes.POINTER(LaserDesc)),
                 ("pml_cells", ctypes.c_int), ("pml_m", ctypes.c_double),
                 ("pml_sigma_max", ctypes.c_double), ("pml_kappa_max", ctypes.c_double),
-                ("pml_alpha_max", ctypes.c_double)]
+                ("pml_alpha_max", ctypes.c_double), ("maxwell_fp64", ctypes.c_int)]
 
 
 class PmlSpec:
@@ -278,9 +278,11 @@ class Grid:
     """A grid with caller-owned (torch) field arrays and its species."""
 
     def __init__(self, dim, n, h, dt, order, precision, absorb_x=False, laser=None, tile=None,
-                 device="cuda", block_particles=0, sort_interval=0, pml: PmlSpec | None = None):
+                 device="cuda", block_particles=0, sort_interval=0, pml: PmlSpec | None = None,
+                 maxwell_fp64=False):
         load()
         self.dim, self.precision, self.order = dim, precision, order
+        self.maxwell_fp64 = bool(maxwell_fp64)
         self.n = tuple(int(v) for v in n) + ((1,) if dim == 2 else ())
         self.h = tuple(float(v) for v in h) + ((1.0,) if dim == 2 else ())
         self.dt, self.absorb_x = float(dt), bool(absorb_x)
@@ -288,7 +290,7 @@ class Grid:
         fx = self.n[0] + 1 if absorb_x else self.n[0]
         nz = self.n[2] if dim == 3 else 1
         self.field_shape = (nz, self.n[1], fx)
-        ft = torch.float64 if precision == FP64 else torch.float32
+        ft = torch.float64 if (precision == FP64 or self.maxwell_fp64) else torch.float32
         jt = torch.float64 if precision == FP64 else torch.int64
         self.E = [torch.zeros(self.field_shape, dtype=ft, device=self.device) for _ in range(3)]
         self.B = [torch.zeros(self.field_shape, dtype=ft, device=self.device) for _ in range(3)]
@@ -308,7 +310,7 @@ class Grid:
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.B]),
                         (ctypes.c_void_p * 3)(*[a.data_ptr() for a in self.J]),
                         ctypes.pointer(self._laser) if self._laser is not None else None,
-                        P.cells, P.m, smax, P.kappa_max, P.alpha_max)
+                        P.cells, P.m, smax, P.kappa_max, P.alpha_max, int(self.maxwell_fp64))
         h = ctypes.c_void_p()
         _check(load().lpic_create_grid(ctypes.byref(desc), ctypes.byref(h)))
         self.h_ = h
@@ -525,8 +527,10 @@ class Ensemble:
         return n.value
 
 
-def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, sort_interval=0) -> Grid:
-    """A Grid for a workloads.Workload (laser centred transversally)."""
+def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, sort_interval=0,
+             maxwell_fp64=False) -> Grid:
+    """A Grid for a workloads.Workload (laser centred transversally);
+    maxwell_fp64 keeps FP64 master fields on the FP32 path."""
     from . import workloads as W
     prec = precision if precision is not None else (FP64 if wl.precision == "fp64" else FP32_FIXED)
     laser = None
@@ -536,4 +540,4 @@ def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, so
         laser.yc, laser.zc = c[0], (c[1] if wl.dim == 3 else 0.0)
     pml = PmlSpec() if getattr(wl, "boundary", "mur") == "cpml" else None
     return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device,
-                block_particles, sort_interval, pml)
+                block_particles, sort_interval, pml, maxwell_fp64)

@@ -63,4 +63,8 @@ def test_descriptor_errors_are_returned_without_a_device(lib):
     d = lpic.GridDesc(2, 64, 64, 1, 0.1, 0.1, 1.0, 0.2)     # dt above the Courant limit
     assert L.lpic_create_grid(ctypes.byref(d), ctypes.byref(h)) == 1
     assert b"Courant" in L.lpic_last_error()
+    d = lpic.GridDesc(2, 64, 64, 1, 0.1, 0.1, 1.0, 0.05)
+    d.shape_order, d.precision, d.maxwell_fp64 = 1, lpic.FP64, 1     # FP64 master fields need FP32_FIXED
+    assert L.lpic_create_grid(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"maxwell_fp64" in L.lpic_last_error()
     assert L.lpic_gather_push_deposit(None, 0, None) == 1
