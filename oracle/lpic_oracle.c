@@ -652,7 +652,50 @@ void orc_maxwell_half(orc_grid *g, int which, double t)
  * Periodic coordinates of x^{n+1} are wrapped; with absorbing x a particle
  * whose deposit end point leaves [2 dx, (nx-2) dx) is removed after its
  * deposit. */
+/* Nonlinear Compton emission inside the particle loop (Algorithm 1 places
+ * the QED events between the field interpolation and the momentum push), for
+ * orc_push_species_qed below. */
+typedef struct {
+    double eps_ref;
+    uint32_t seed_lo, seed_hi;
+    long step;
+    double *tau;     /* optical depth per particle index */
+    double *ph;      /* photons [8][cap]: x0, x1, x2, u0, u1, u2, w, emitter index */
+    long cap, *nph;
+} orc_qed_push;
+
+static int push_species_impl(orc_grid *g, orc_species *sp, const orc_qed_push *q);
+static void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+static double u01(uint32_t x);
+double orc_chi_e(const double u[3], const double E[3], const double B[3], double eps_ref);
+double orc_compton_rate(double chi, double gamma, double eps_ref);
+double orc_compton_xi(double chi, double r);
+
 int orc_push_species(orc_grid *g, orc_species *sp)
+{
+    return push_species_impl(g, sp, NULL);
+}
+
+/* The particle loop of Algorithm 1 with nonlinear Compton emission (Sec. 3.4)
+ * between "interpolate E, B" and "push momenta": after the gather at
+ * x^{n+1/2}, chi is formed from u^n and those fields, tau[p] decreases by
+ * W(chi, gamma^n) dt, and when it reaches zero a photon of energy fraction
+ * xi = F^-1(r1) (counter (p, step, 0, 0), word 0) is emitted along u^n with
+ * the particle's weight, the particle recoils (u^n -> u^n (1 - k/|u^n|), k =
+ * xi gamma^n) and tau restarts at -ln r2 (word 1); the Boris push, the move
+ * and the deposit then use the recoiled momentum.  The photon leaves from
+ * x^{n+1/2} at the speed of light: it is stored at its position at t_{n+1},
+ * x^{n+1/2} + (dt/2) khat (periodic coordinates wrapped), with the emitter's
+ * index in row 7.  More photons than cap: ORC_EARG. */
+int orc_push_species_qed(orc_grid *g, orc_species *sp, double eps_ref, uint32_t seed_lo, uint32_t seed_hi,
+                         long step, double *tau, double *ph, long cap, long *nph)
+{
+    if (sp->m == 0.0) return ORC_EARG;
+    const orc_qed_push q = {eps_ref, seed_lo, seed_hi, step, tau, ph, cap, nph};
+    return push_species_impl(g, sp, &q);
+}
+
+static int push_species_impl(orc_grid *g, orc_species *sp, const orc_qed_push *q)
 {
     const double dt = g->dt;
     const double L[3] = {g->nx * g->dx, g->ny * g->dy, g->nz * g->dz};
@@ -666,6 +709,40 @@ int orc_push_species(orc_grid *g, orc_species *sp)
         double g0 = massless ? sqrt(uu0) : sqrt(1.0 + uu0);
         for (int d = 0; d < g->dim; ++d) xm[d] = sp->x[d][p] + (g0 > 0 ? 0.5 * dt * u[d] / g0 : 0.0);
         if (orc_gather(g, xm, E, B) != ORC_OK) return ORC_EOUTSIDE;
+        if (q) {
+            const double chi = orc_chi_e(u, E, B, q->eps_ref);
+            if (chi > 0.0) {
+                q->tau[p] -= orc_compton_rate(chi, g0, q->eps_ref) * dt;
+                if (q->tau[p] <= 0.0) {
+                    if (*q->nph >= q->cap) return ORC_EARG;
+                    const uint32_t ctr[4] = {(uint32_t)p, (uint32_t)q->step, 0u, 0u};
+                    const uint32_t key[2] = {q->seed_lo, q->seed_hi};
+                    uint32_t o[4];
+                    philox4x32_10(ctr, key, o);
+                    const double xi = orc_compton_xi(chi, u01(o[0]));
+                    const double umag = sqrt(uu0);
+                    const double k = xi * g0;
+                    const long j = *q->nph;
+                    for (int d = 0; d < 3; ++d) {
+                        double xp = 0.0;
+                        if (d < g->dim) {
+                            xp = xm[d] + 0.5 * dt * u[d] / umag;
+                            if (!(d == 0 && g->absorb_x)) {
+                                if (xp >= L[d]) xp -= L[d];
+                                else if (xp < 0.0) xp += L[d];
+                            }
+                        }
+                        q->ph[d * q->cap + j] = xp;
+                    }
+                    for (int c = 0; c < 3; ++c) q->ph[(3 + c) * q->cap + j] = k * u[c] / umag;
+                    q->ph[6 * q->cap + j] = sp->w[p];
+                    q->ph[7 * q->cap + j] = (double)p;
+                    *q->nph = j + 1;
+                    for (int c = 0; c < 3; ++c) u[c] *= 1.0 - k / umag;
+                    q->tau[p] = -log(u01(o[1]));
+                }
+            }
+        }
         if (!massless) orc_boris(sp->q, sp->m, dt, u, E, B);
         const double uu1 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         double g1 = massless ? (uu1 > 0 ? sqrt(uu1) : 1.0) : sqrt(1.0 + uu1);

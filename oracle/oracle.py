@@ -342,6 +342,26 @@ def qed_compton(grid: Grid, sp: Species, eps_ref, seed, step, tau, cap=1 << 16):
     return Species(0.0, 0.0, ph[:grid.dim].copy(), ph[3:6].copy(), ph[6].copy())
 
 
+def push_species_qed(grid: Grid, sp: Species, eps_ref, seed, step, tau, cap=1 << 16):
+    """One push of `sp` with nonlinear Compton emission between the gather and
+    the momentum push (Algorithm 1); returns the emitted photons as a Species
+    (positions at the end of the step) and the index of each photon's emitter."""
+    L = lib()
+    L.orc_push_species_qed.argtypes = [ctypes.POINTER(_CGrid), ctypes.POINTER(_CSpecies), ctypes.c_double,
+                                       ctypes.c_uint32, ctypes.c_uint32, ctypes.c_long, _dp, _dp,
+                                       ctypes.c_long, ctypes.POINTER(ctypes.c_long)]
+    g, s = grid.c(), sp.c()
+    ph = np.zeros(8 * cap)
+    nph = ctypes.c_long(0)
+    assert tau.dtype == np.float64 and tau.flags.c_contiguous
+    _check(L.orc_push_species_qed(ctypes.byref(g), ctypes.byref(s), eps_ref, int(seed) & 0xFFFFFFFF,
+                                  (int(seed) >> 32) & 0xFFFFFFFF, int(step), _ptr(tau), _ptr(ph), cap,
+                                  ctypes.byref(nph)), "push qed")
+    n = nph.value
+    ph = ph.reshape(8, cap)[:, :n]
+    return Species(0.0, 0.0, ph[:grid.dim].copy(), ph[3:6].copy(), ph[6].copy()), ph[7].astype(np.int64)
+
+
 # Breit-Wheeler pair creation (Sec. 3.4)
 def bw_f(eta, chi):
     return _qed_sigs().orc_bw_f(eta, chi)
