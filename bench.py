@@ -178,7 +178,7 @@ def reduce_over_ranks(elapsed, psteps, device):
 
 
 # the files that define the fused tile kernel k_gpd32 (its code, not its host launcher)
-GPD32_SOURCES = ("lpic_common.cuh", "lpic_fp32.cuh", "lpic_gpd32.h", "lpic_gpd32_impl.cuh",
+GPD32_SOURCES = ("lpic_common.cuh", "lpic_fp32.cuh", "lpic_qed_tab.cuh", "lpic_gpd32.h", "lpic_gpd32_impl.cuh",
                  "lpic_gpd32_21.cu", "lpic_gpd32_22.cu", "lpic_gpd32_31.cu", "lpic_gpd32_32.cu")
 
 
@@ -261,6 +261,12 @@ def qed_summary(qed, wl, counts0, counts1, G, peak, which):
     n_ph = 0.5 * (counts0[ph] + counts1[ph])
     bytes_step = n_emit * per_emitter + created * per_photon + 24 * wl.cells + 16 * n_ph
     t = ms / 1e3 / max(1, n_steps)
+    if qed["fused"]:
+        # the emission runs inside the fused push: its cost is part of the
+        # k_gpd32 launch time (the plasma without QED: --qed-mode off)
+        return {"kernel": "emission inside k_gpd32 (kGpdQed form) + k_qed_bw32 pass",
+                "pair_pass_ms_per_step": 1e3 * t, "emitters": int(n_emit),
+                "photons_created_per_step": created, "photons_alive": int(counts1[ph])}
     achieved = bytes_step / t / 1e9
     return {"kernel": "k_qed_compton32 + k_qed_bw32", "ms_per_step": 1e3 * t,
             "emitters": int(n_emit), "photons_created_per_step": created,
@@ -295,6 +301,10 @@ def run_b300(args, rank, world, local_rank):
         G.add_species(p, capacity=cap, stream=stream)
     loaded = [p.n // wl.species[i].ppc for i, p in enumerate(parts)]
     qed = None
+    if wl.qed_eps_ref > 0 and args.qed_mode == "off":
+        # the same plasma without QED (the baseline of the QED cost)
+        wl.qed_eps_ref = 0.0
+        G.B[2].fill_(wl.b0)
     if wl.qed_eps_ref > 0:
         # photons appended by the emission passes; depths indexed by the
         # (species-unique) particle ids
@@ -311,7 +321,12 @@ def run_b300(args, rank, world, local_rank):
             n_tau += sp.cap
         qed = dict(emitters=emitters, photons=phot, tau=G.qed_initial_tau(n_tau, stream),
                    ph_tau=torch.zeros(phot.cap, dtype=torch.float32, device=dev), events=[],
-                   pairs=(emitters[0], emitters[1]) if len(emitters) == 2 else None)
+                   pairs=(emitters[0], emitters[1]) if len(emitters) == 2 else None,
+                   fused=args.qed_mode == "fused")
+        if qed["fused"]:
+            # emission inside the fused push of each lepton species (Algorithm 1)
+            for sp in emitters:
+                G.qed_fuse(sp, phot, qed["tau"], first_step=0, stream=stream, photon_tau=qed["ph_tau"])
     del parts
     dt = G.dt
     pre = WORKLOADS[args.workload][1] if args.pre_steps is None else args.pre_steps
@@ -324,8 +339,9 @@ def run_b300(args, rank, world, local_rank):
         if timed:
             ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
             ev[0].record(stream)
-        for sp in qed["emitters"]:
-            G.qed_compton(sp, qed["photons"], qed["tau"], k, stream, photon_tau=qed["ph_tau"])
+        if not qed["fused"]:
+            for sp in qed["emitters"]:
+                G.qed_compton(sp, qed["photons"], qed["tau"], k, stream, photon_tau=qed["ph_tau"])
         if qed["pairs"] is not None:
             G.qed_breit_wheeler(qed["photons"], *qed["pairs"], qed["ph_tau"], k, stream)
         if timed:
@@ -472,10 +488,22 @@ def run_ensemble(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.Stream(device=dev)
     members = W.ensemble(count=args.ensemble_count, seed=W.SEED_BASE + 4000 + 97 * rank)
+    if args.ensemble_tuning == "per-member":
+        from paper_2607_13507_b300 import autotune as AT
+        choices, classes = AT.tune_ensemble(members, cache=os.path.join(ROOT, "paper_2607_13507_b300",
+                                                                        "tuned.json"))
+        tuning = {"rule": "per member: the best (tile, block_particles) of its particles-per-cell class, "
+                          "each class timed alone on a 512x512 periodic plasma (autotuner results)",
+                  "classes": {str(c): {"tile": list(v[0].tile), "block_particles": v[0].block_particles}
+                              for c, v in classes.items()}}
+    else:
+        from paper_2607_13507_b300.autotune import Choice
+        choices = [Choice((16, 8), 0, 1)] * len(members)
+        tuning = {"rule": "uniform", "tile": [16, 8]}
     grids, counts, loaded = [], 0, 0
-    for wl in members:
+    for wl, ch in zip(members, choices):
         parts = W.load_all(wl)
-        G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(16, 8), device=dev)
+        G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=ch.tile, device=dev, block_particles=ch.block_particles)
         G.add_species(parts[0], stream=stream)
         counts += parts[0].n
         loaded += parts[0].n // wl.species[0].ppc
@@ -520,7 +548,7 @@ def run_ensemble(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (int64 fixed-point current)",
         "data": "synthetic (seeded Philox initial conditions)",
         "config": {"workload": WORKLOADS["ensemble"][0], "members": len(members),
-                   "particles": int(counts), "l2": "inputs larger than L2",
+                   "particles": int(counts), "l2": "inputs larger than L2", "tuning": tuning,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "kernel": "whole ensemble step", "achieved": achieved,
                      "peak": float(peaks["hbm_gbs"]), "unit": "GB/s",
@@ -672,6 +700,7 @@ def oracle_sample(args, budget_s, max_steps, threads=1):
     tau = None
     if wl.qed_eps_ref > 0:
         g.B[2][...] = wl.b0
+    if wl.qed_eps_ref > 0 and getattr(args, "qed_mode", "fused") != "off":
         ids = np.concatenate([p.id for p in parts])
         tau = [O.qed_initial_tau(p.id, wl.seed) for p in parts]
         assert len(set(ids.tolist())) == len(ids)
@@ -690,6 +719,29 @@ def oracle_sample(args, budget_s, max_steps, threads=1):
             steps += 1
             continue
         psteps += sum(int(sp.alive.sum()) for sp in sps)
+        if tau is not None and getattr(args, "qed_mode", "fused") == "fused":
+            # emission inside the particle loop (Algorithm 1)
+            t = steps * wl.dt
+            O.maxwell_half(g, 0, t)
+            for c in range(3):
+                g.J[c][...] = 0.0
+            new = []
+            for k, sp in enumerate(list(sps)):
+                if k < nemit:
+                    ph, _ = O.push_species_qed(g, sp, wl.qed_eps_ref, wl.seed, steps, tau[k])
+                    if ph.x.shape[1]:
+                        new.append(ph)
+                else:
+                    O.push_species(g, sp)
+            O.maxwell_half(g, 1, t + 0.5 * wl.dt)
+            for ph in new:
+                sps.append(ph)
+                phots.append((ph, O.qed_initial_tau_kind(np.arange(ph.x.shape[1]), 3, wl.seed)))
+            for ph, pt in list(phots):                   # pair creation by the photons
+                e_, p_ = O.qed_bw(g, ph, wl.qed_eps_ref, wl.seed, steps, pt)
+                sps += [s for s in (e_, p_) if s.x.shape[1]]
+            steps += 1
+            continue
         O.step(g, sps, steps * wl.dt)
         if tau is not None:
             for k in range(nemit):
@@ -862,6 +914,11 @@ def main():
                     help="untimed steps before warm-up (default: bring the laser onto the target)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ensemble-count", type=int, default=96)
+    ap.add_argument("--qed-mode", choices=("fused", "passes", "off"), default="fused",
+                    help="qed2d: emission inside the fused push (Algorithm 1), as separate passes after "
+                         "the step, or no QED (the same plasma)")
+    ap.add_argument("--ensemble-tuning", choices=("per-member", "uniform"), default="per-member",
+                    help="ensemble launch choices: per particles-per-cell class (autotuned) or one (16, 8) tile")
     ap.add_argument("--tile", default=None, help="tile shape, e.g. 8x8")
     ap.add_argument("--block-particles", type=int, default=0)
     ap.add_argument("--sort-interval", type=int, default=0)

@@ -310,11 +310,13 @@ lpic_status lpic_check_status(lpic_grid_t grid, cudaStream_t stream, unsigned *b
 /* Ensembles: many independent grids stepped together (batched scheduling).
  * One launch per field pass and per sort pass covers every grid, and one
  * persistent particle kernel takes (species, work item) entries from a
- * device queue that visits the densest species first.  Requirements: at
- * least one grid; all grids on the FP32_FIXED path with the same dimension,
- * shape order, tile shape and block_particles, sort_interval <= 1, periodic
- * boundaries and no laser; every grid has its species added and all species
- * buffers at the same parity.  The grids stay owned by the caller and must
+ * device queue that visits the densest species first.  Each grid keeps its
+ * own tile shape and block_particles (a sparse member can take larger tiles
+ * than a dense one); the persistent kernel reserves the largest member's
+ * shared memory per block.  Requirements: at least one grid; all grids on the
+ * FP32_FIXED path with the same dimension and shape order, sort_interval <= 1,
+ * periodic boundaries and no laser; every grid has its species added and all
+ * species buffers at the same parity.  The grids stay owned by the caller and must
  * outlive the ensemble; while it exists they are stepped through it (queries
  * and diagnostics on the grids remain valid). */
 typedef struct lpic_ensemble *lpic_ensemble_t;
@@ -412,6 +414,32 @@ lpic_status lpic_qed_initial_tau(lpic_grid_t grid, float *tau, long long n_ids, 
 lpic_status lpic_qed_compton(lpic_grid_t grid, int electron_species, int photon_species, float *tau,
                              long long n_ids, float *photon_tau, long long photon_n_ids, long long step,
                              cudaStream_t stream);
+
+/* Nonlinear Compton emission inside the fused particle kernel (Algorithm 1
+ * places the QED events between the field interpolation and the momentum
+ * push).  From this call on, every push of `electron_species` (lpic_step,
+ * lpic_gather_push_deposit, captured steps) runs the kernel form with
+ * emission: after the gather of E and B at x^{n+1/2}, chi is formed from u^n
+ * and those fields, tau[id] decreases by W dt, and on an event (counter
+ * (id, step, 0, 0) as in lpic_qed_compton) a photon of momentum xi gamma
+ * u^n/|u^n| leaves from x^{n+1/2} with the particle's weight, the particle
+ * recoils, its depth restarts, and the Boris push, move and deposit use the
+ * recoiled momentum.  Photons are appended to `photon_species` (massless,
+ * with an index above electron_species, so that the same step's photon push
+ * carries them to x^{n+3/2}); photon_tau as in lpic_qed_compton.  The counter
+ * word is a device counter of the grid: set to first_step here (and by
+ * lpic_qed_set_step), advanced by one at the end of every lpic_step, read by
+ * each fused push.  Overflow and id rules as in lpic_qed_compton (a photon
+ * without room leaves its emitter untouched, which is pushed without recoil).
+ * photon_species = -1 turns the emission of electron_species off.  The
+ * unfused stages and ensembles refuse a species with emission
+ * (LPIC_EUNSUPPORTED).  Drops the grid's captured steps; synchronises the
+ * device. */
+lpic_status lpic_qed_fuse(lpic_grid_t grid, int electron_species, int photon_species, float *tau,
+                          long long n_ids, float *photon_tau, long long photon_n_ids, long long first_step,
+                          cudaStream_t stream);
+/* Set the counter word of the fused emission (0 <= step < 2^32).  Asynchronous. */
+lpic_status lpic_qed_set_step(lpic_grid_t grid, long long step, cudaStream_t stream);
 
 /* Id given to the next particle that species `species_id` gains on the
  * device (emitted photons, Breit-Wheeler pairs); by default its count at add

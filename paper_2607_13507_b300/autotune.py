@@ -10,11 +10,17 @@ times.  The search is staged to keep it short: tile shape x sort interval at
 the default block size, then the other block sizes for the three best pairs.  Results can
 be cached in a JSON file keyed by the workload's signature (grid, cell sizes,
 shape order, species, particles per cell, boundaries).
+
+Ensembles (`tune_ensemble`): members are grouped by particles per cell, the
+quantity that decides how full a tile of a given shape is; one representative
+periodic plasma per group is timed alone over the tile shapes and block sizes
+(sort every step, as ensembles do), and each member takes its group's best.
 """
 from __future__ import annotations
 
 import itertools
 import json
+import math
 import os
 from dataclasses import asdict, dataclass
 
@@ -161,3 +167,54 @@ def autotune(wl: W.Workload, tiles=None, intervals=(1, 2, 4, 8), block_sizes=(20
         with open(cache, "w") as f:
             json.dump(data, f, indent=1)
     return best, table
+
+
+def ppc_class(ppc: int) -> int:
+    """The power of two nearest to ppc in log scale (members are grouped by it)."""
+    return 1 << max(0, int(round(math.log2(max(ppc, 1)))))
+
+
+def _cache_load(cache):
+    if cache and os.path.exists(cache):
+        try:
+            return json.load(open(cache))
+        except ValueError:
+            return {}
+    return {}
+
+
+def tune_ensemble(members, tiles=None, block_sizes=(4096, 8192), side=512, vth=0.05, steps=6, warmup=2,
+                  cache: str | None = None, log=None, refresh=False) -> tuple:
+    """Per-member launch choices for an ensemble of periodic 2D plasmas.
+    Returns (one Choice per member, {ppc class: (Choice, table)})."""
+    wl0 = members[0]
+    classes = sorted({ppc_class(m.species[0].ppc) for m in members})
+    data = _cache_load(cache)
+    best = {}
+    for c in classes:
+        key = f"ensemble-class|{wl0.dim}|{wl0.order}|ppc{c}|side{side}"
+        rec = None if refresh else data.get(key)
+        if rec:
+            ch = rec["choice"]
+            best[c] = (Choice(tuple(ch["tile"]), ch["block_particles"], 1), rec["table"])
+            continue
+        rep = W.thermal2d(n=side, ppc=c, vth=vth, order=wl0.order, precision="fp32", seed=W.SEED_BASE + 7000 + c)
+        parts = W.load_all(rep)
+        stream = torch.cuda.Stream()
+        table = []
+        for t in (tiles or default_tiles(rep.dim, rep.n)):
+            for P in block_sizes:
+                ch = Choice(t, P, 1)
+                ms = time_choice(rep, parts, ch, steps, warmup, stream)
+                table.append((ch, ms))
+                if log:
+                    log(f"ensemble class ppc {c}: {ch} -> {ms:.3f} ms/step")
+        b = min(table, key=lambda e: e[1])[0]
+        best[c] = (b, [[asdict(ch), ms] for ch, ms in table])
+        data[key] = {"choice": asdict(b), "table": best[c][1],
+                     "representative": f"{side}x{side} periodic plasma, {c} particles per cell, v_th {vth}c"}
+        if cache:
+            with open(cache, "w") as f:
+                json.dump(data, f, indent=1)
+    choices = [best[ppc_class(m.species[0].ppc)][0] for m in members]
+    return choices, best

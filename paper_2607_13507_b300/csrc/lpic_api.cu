@@ -74,6 +74,12 @@ struct Species {
     int since_sort = 1 << 30;    // pushes since the last sort
     bool counts_fresh = false;   // d_count holds the histogram of the current cells
     bool massless = false;       // m = 0, q = 0: moves at c along u, no fields, no current
+    // nonlinear Compton emission inside this species' push (lpic_qed_fuse)
+    int q_ph = -1;               // photon species (-1: off)
+    float* q_tau = nullptr;
+    long long q_nids = 0;
+    float* q_phtau = nullptr;
+    long long q_phnids = 0;
 };
 
 }  // namespace
@@ -127,6 +133,7 @@ struct lpic_grid {
     float* d_qtab = nullptr;                   // logh | top | cdf
     BwTab btab{};
     float* d_btab = nullptr;                   // g | cdf (Breit-Wheeler)
+    unsigned* d_qstep = nullptr;               // counter word of the fused emission (lpic_qed_fuse)
 };
 
 namespace {
@@ -228,7 +235,28 @@ GpdArgs gpd_args(lpic_grid* g, Species& s, bool count_next) {
                    ptr3<const double>(g->d.E), ptr3<const double>(g->d.B), f64 ? 1 : 0,
                    ptr3<unsigned long long>(g->d.J),
                    p, t, g->dec, k, sq, (float)(g->d.dt / g->d.dx), (float)(g->d.dt / g->d.dy),
-                   (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status, nullptr, 0};
+                   (float)(g->d.dt / (g->d.dim == 3 ? g->d.dz : 1.0)), g->d_status, nullptr, 0, 0, QedEmit{}};
+}
+
+// The emission state of a species with fused emission (photon buffers of the
+// photon species' current parity).
+QedEmit qed_emit_args(lpic_grid* g, const Species& s) {
+    Species& ph = g->sp[s.q_ph];
+    QedEmit q{};
+    q.T = g->qtab;
+    q.tau = s.q_tau;
+    q.n_ids = s.q_nids;
+    q.ph = view32(g, ph, ph.cur);
+    q.ph_n = ph.d_n;
+    q.ph_next_id = ph.d_n + 1;
+    q.ph_cap = ph.cap;
+    q.ph_tau = s.q_phnids > 0 ? s.q_phtau : nullptr;
+    q.ph_n_ids = s.q_phnids;
+    q.dt = (float)g->d.dt;
+    q.k0 = g->seed[0];
+    q.k1 = g->seed[1];
+    q.step = g->d_qstep;
+    return q;
 }
 
 // tile-kernel instance and its dynamic shared memory
@@ -236,11 +264,24 @@ template <int DIM, int ORDER>
 lpic_status launch_gpd32(lpic_grid* g, Species& s, cudaStream_t st, bool count_next) {
     if (count_next) LPIC_CUDA(cudaMemsetAsync(s.d_count, 0, sizeof(int) * (g->ntiles + 1), st));
     LPIC_CUDA(cudaMemsetAsync(s.d_nesc, 0, sizeof(int), st));
-    const GpdArgs A = gpd_args(g, s, count_next);
-    Gpd32<DIM, ORDER>::tile(A, (unsigned)s.item_cap, g->smem32, st);
-    LPIC_LAUNCHED("k_gpd32");
+    GpdArgs A = gpd_args(g, s, count_next);
+    if (s.q_ph >= 0) {
+        A.qed = 1;
+        A.q = qed_emit_args(g, s);
+        Gpd32Qed<DIM, ORDER>::tile(A, (unsigned)s.item_cap, g->smem32, st);
+        LPIC_LAUNCHED("k_gpd32_qed");
+    } else {
+        Gpd32<DIM, ORDER>::tile(A, (unsigned)s.item_cap, g->smem32, st);
+        LPIC_LAUNCHED("k_gpd32");
+    }
     Gpd32<DIM, ORDER>::escape(A, (unsigned)(2 * g->nsm), st);
     LPIC_LAUNCHED("k_gpd32_escape");
+    if (s.q_ph >= 0) {
+        Species& ph = g->sp[s.q_ph];
+        k_qed_clamp<<<1, 32, 0, st>>>(ph.d_n, ph.cap);
+        LPIC_LAUNCHED("k_qed_clamp");
+        ph.counts_fresh = false;
+    }
     return LPIC_OK;
 }
 
@@ -269,8 +310,9 @@ lpic_status launch_gpd64(lpic_grid* g, Species& s, cudaStream_t st) {
 
 template <int DIM, int ORDER>
 cudaError_t set_smem_attrs(size_t bytes) {
-    const cudaError_t e = Gpd32<DIM, ORDER>::set_smem(bytes);
-    return e != cudaSuccess ? e : Gpd32Stages<DIM, ORDER>::set_smem(bytes);
+    cudaError_t e = Gpd32<DIM, ORDER>::set_smem(bytes);
+    if (e == cudaSuccess) e = Gpd32Stages<DIM, ORDER>::set_smem(bytes);
+    return e != cudaSuccess ? e : Gpd32Qed<DIM, ORDER>::set_smem(bytes);
 }
 
 // clock != nullptr: the laser time is read from the device clock plus t.
@@ -660,6 +702,7 @@ lpic_status lpic_destroy_grid(lpic_grid_t g) {
     cudaFree(g->d_clock);
     cudaFree(g->d_qtab);
     cudaFree(g->d_btab);
+    cudaFree(g->d_qstep);
     delete g;
     return LPIC_OK;
 }
@@ -846,6 +889,7 @@ lpic_status lpic_gather_fields(lpic_grid_t g, int sid, float* fields, cudaStream
     if (lpic_status r = check_species(g, sid)) return r;
     if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "the unfused stages need the FP32 path");
     if (g->sp[sid].massless) return fail(LPIC_EUNSUPPORTED, "a massless species has no field stages");
+    if (g->sp[sid].q_ph >= 0) return fail(LPIC_EUNSUPPORTED, "species %d emits inside its fused push (no stages)", sid);
     if (!fields) return fail(LPIC_EINVAL, "fields is NULL");
     Species& s = g->sp[sid];
     g->started = true;
@@ -866,6 +910,7 @@ lpic_status lpic_push_deposit_fields(lpic_grid_t g, int sid, const float* fields
     if (lpic_status r = check_species(g, sid)) return r;
     if (g->d.precision != LPIC_FP32_FIXED) return fail(LPIC_EUNSUPPORTED, "the unfused stages need the FP32 path");
     if (g->sp[sid].massless) return fail(LPIC_EUNSUPPORTED, "a massless species has no field stages");
+    if (g->sp[sid].q_ph >= 0) return fail(LPIC_EUNSUPPORTED, "species %d emits inside its fused push (no stages)", sid);
     if (!fields) return fail(LPIC_EINVAL, "fields is NULL");
     Species& s = g->sp[sid];
     if (s.gather_gen != s.sort_gen || s.since_sort != 0)
@@ -904,6 +949,17 @@ lpic_status lpic_maxwell_half_step(lpic_grid_t g, int half, double t, cudaStream
 
 // One step; with a device clock the laser time is *clock (+ dt/2 in the
 // second half) and the clock advances by dt at the end.
+// The counter word of the fused emission advances once per full step.
+static lpic_status advance_qed_step(lpic_grid_t g, cudaStream_t st) {
+    for (const Species& s : g->sp)
+        if (s.q_ph >= 0) {
+            k_add_uint<<<1, 32, 0, st>>>(g->d_qstep, 1u);
+            LPIC_LAUNCHED("k_add_uint");
+            break;
+        }
+    return LPIC_OK;
+}
+
 static lpic_status step_impl(lpic_grid_t g, double t, cudaStream_t st, double* clock) {
     if (lpic_status r = maxwell_any(g, 0, clock ? 0.0 : t, st, clock)) return r;
     if (lpic_status r = lpic_zero_current(g, st)) return r;
@@ -923,7 +979,7 @@ static lpic_status step_impl(lpic_grid_t g, double t, cudaStream_t st, double* c
         k_clock_add<<<1, 32, 0, st>>>(clock, g->d.dt);
         LPIC_LAUNCHED("k_clock_add");
     }
-    return LPIC_OK;
+    return advance_qed_step(g, st);
 }
 
 lpic_status lpic_step(lpic_grid_t g, double t, cudaStream_t st) {
@@ -968,7 +1024,8 @@ lpic_status lpic_step_resolved(lpic_grid_t g, double t, int sid, lpic_grid_t aux
                 LPIC_CUDA(cudaMemcpyAsync(aux->d.J[c], g->d.J[c], jbytes, cudaMemcpyDeviceToDevice, st));
     }
     if (lpic_status r = maxwell_any(g, 1, t + 0.5 * d.dt, st, nullptr)) return r;
-    return aux_half(1, t + 0.5 * d.dt);
+    if (lpic_status r = aux_half(1, t + 0.5 * d.dt)) return r;
+    return advance_qed_step(g, st);
 }
 
 lpic_status lpic_set_clock(lpic_grid_t g, double t, cudaStream_t st) {
@@ -1281,14 +1338,13 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
         if (g->d.maxwell_fp64) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles keep float fields (no maxwell_fp64)", i);
         if (g->d.dim != g0->d.dim || g->d.shape_order != g0->d.shape_order)
             return fail(LPIC_EINVAL, "grid %d: dimension and shape order must match grid 0", i);
-        for (int k = 0; k < 3; ++k)
-            if (g->T[k] != g0->T[k]) return fail(LPIC_EINVAL, "grid %d: tile shape must match grid 0", i);
-        if (g->P != g0->P) return fail(LPIC_EINVAL, "grid %d: block_particles must match grid 0", i);
         if (g->K != 1) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles sort every step (sort_interval <= 1)", i);
         if (g->geo.absorb || g->laser.on) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles need periodic grids", i);
         if (g->sp.empty()) return fail(LPIC_EINVAL, "grid %d has no species", i);
-        for (auto& s : g->sp)
+        for (auto& s : g->sp) {
             if (s.cur != g0->sp[0].cur) return fail(LPIC_EINVAL, "grid %d: species buffer parity differs", i);
+            if (s.q_ph >= 0) return fail(LPIC_EUNSUPPORTED, "grid %d: ensembles have no fused emission", i);
+        }
         for (int j = 0; j < i; ++j)
             if (grids[j] == g) return fail(LPIC_EINVAL, "grid %d appears twice", i);
     }
@@ -1296,7 +1352,11 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
     if (!e) return fail(LPIC_ENOMEM, "host allocation failed");
     e->grids.assign(grids, grids + n);
     e->dim = g0->d.dim; e->order = g0->d.shape_order; e->ninst = n; e->nsm = g0->nsm;
-    e->smem = g0->smem32;
+    // members keep their own tile shape and particles per block (each work
+    // item lays out its shared memory from its slot's tiles); the persistent
+    // kernel is launched with the largest member's shared memory
+    e->smem = 0;
+    for (int i = 0; i < n; ++i) e->smem = std::max(e->smem, grids[i]->smem32);
     e->parity = g0->sp[0].cur;
     std::vector<EnsField> hf(n);
     std::vector<EnsSort> hs;
@@ -1569,6 +1629,52 @@ lpic_status lpic_qed_compton(lpic_grid_t g, int sid_e, int sid_ph, float* tau, l
     k_qed_clamp<<<1, 32, 0, st>>>(ph.d_n, ph.cap);
     LPIC_LAUNCHED("k_qed_clamp");
     ph.counts_fresh = false;
+    return LPIC_OK;
+}
+
+lpic_status lpic_qed_fuse(lpic_grid_t g, int sid_e, int sid_ph, float* tau, long long n_ids, float* ph_tau,
+                          long long ph_n_ids, long long first_step, cudaStream_t st) {
+    if (lpic_status r = check_species(g, sid_e)) return r;
+    if (!g->qed) return fail(LPIC_EINVAL, "call lpic_qed_init first");
+    Species& e = g->sp[sid_e];
+    if (e.massless) return fail(LPIC_EINVAL, "species %d is massless and cannot emit", sid_e);
+    if (sid_ph >= 0) {
+        if (lpic_status r = check_species(g, sid_ph)) return r;
+        if (!g->sp[sid_ph].massless) return fail(LPIC_EINVAL, "species %d must be massless and charge-free", sid_ph);
+        if (sid_ph < sid_e)
+            return fail(LPIC_EINVAL, "the photon species (%d) must come after the emitting species (%d): a step "
+                        "moves the photons emitted at x^{n+1/2} with the photon push that follows", sid_ph, sid_e);
+        if (n_ids < 0 || (n_ids > 0 && !tau)) return fail(LPIC_EINVAL, "tau is NULL or n_ids negative");
+        if (ph_n_ids < 0 || (ph_n_ids > 0 && !ph_tau)) return fail(LPIC_EINVAL, "photon_tau is NULL or its length negative");
+        if (first_step < 0 || first_step > 0xffffffffLL) return fail(LPIC_EINVAL, "first_step must fit 32 bits");
+    }
+    // captured steps launch the kernel form of each species: drop them
+    LPIC_CUDA(cudaDeviceSynchronize());
+    for (auto& kv : g->graphs) cudaGraphExecDestroy(kv.second);
+    g->graphs.clear();
+    g->graph_launches.clear();
+    if (sid_ph < 0) {
+        e.q_ph = -1;
+        return LPIC_OK;
+    }
+    if (!g->d_qstep && cudaMalloc(&g->d_qstep, 64) != cudaSuccess)
+        return fail(LPIC_ENOMEM, "step counter allocation failed");
+    e.q_ph = sid_ph;
+    e.q_tau = tau;
+    e.q_nids = n_ids;
+    e.q_phtau = ph_tau;
+    e.q_phnids = ph_n_ids;
+    k_set_uint<<<1, 32, 0, st>>>(g->d_qstep, (unsigned)first_step);
+    LPIC_LAUNCHED("k_set_uint");
+    return LPIC_OK;
+}
+
+lpic_status lpic_qed_set_step(lpic_grid_t g, long long step, cudaStream_t st) {
+    if (lpic_status r = check_grid(g)) return r;
+    if (!g->d_qstep) return fail(LPIC_EINVAL, "no species emits inside its push (lpic_qed_fuse)");
+    if (step < 0 || step > 0xffffffffLL) return fail(LPIC_EINVAL, "step must fit 32 bits");
+    k_set_uint<<<1, 32, 0, st>>>(g->d_qstep, (unsigned)step);
+    LPIC_LAUNCHED("k_set_uint");
     return LPIC_OK;
 }
 

@@ -267,4 +267,13 @@ __global__ void k_clock_set(double* clock, double t) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *clock = t;
 }
 
+// Step counter of the fused emission: advanced at the end of each full step.
+__global__ void k_add_uint(unsigned* p, unsigned v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p += v;
+}
+
+__global__ void k_set_uint(unsigned* p, unsigned v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
 }  // namespace lpic

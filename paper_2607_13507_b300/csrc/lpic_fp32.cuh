@@ -11,11 +11,12 @@
 // the additions, so the result is bitwise deterministic.
 //
 // Shared-memory accumulation: rounds of 256 particles add into an int32 box
-// with native 32-bit atomics; every R rounds the box is folded into an int64
-// box.  The shift F keeps every particle's integer charge S <= 2^22, and the
-// host derives R from a bound on one move's current per node (a fraction of
-// S set by the Courant number and the shape), so the int32 box cannot
-// overflow between folds.
+// with native 32-bit atomics.  In 2D the box is folded into an int64 box
+// every R rounds (R from a host bound on one move's current per node, a
+// fraction of S set by the Courant number and the shape); in 3D it is
+// flushed to the global int64 current whenever a running bound of the moves
+// deposited since the last flush says the next phase could overflow it.  The
+// shift F keeps every particle's integer charge S <= 2^22.
 //
 // Exact charge conservation in integers.  The unit of charge is 2^-F.  A
 // particle of charge s = 2^F q w carries the integer charge S = rint(s),
@@ -33,6 +34,7 @@
 // sum_d J_d(i+1/2) - J_d(i-1/2) = -(Q1 - Q0) exactly.
 #pragma once
 #include "lpic_common.cuh"
+#include "lpic_qed_tab.cuh"
 
 namespace lpic {
 
@@ -44,6 +46,86 @@ struct P32 {
     int* id;
     const int* n;
 };
+
+// Nonlinear Compton emission (Sec. 3.4) of one emitting species into one
+// photon species: the tables, the optical depths by particle id, the photon
+// buffer (appended to), the step's counter word and the Philox key.
+struct QedEmit {
+    QedTab T;
+    float* tau;            // [n_ids] optical depth by particle id
+    long long n_ids;
+    P32 ph;                // photon species (current buffer)
+    int* ph_n;             // == ph.n, appended to
+    int* ph_next_id;       // id of the next created photon
+    long long ph_cap;
+    float* ph_tau;         // optional: pair-creation depths of new photons, by photon id
+    long long ph_n_ids;
+    float dt;
+    uint32_t k0, k1;
+    const unsigned* step;  // fused kernel: device counter holding the counter word
+};
+
+// One particle's emission event in fields fld = (E, B) at its position, with
+// momentum u (m c) and depth tau0 = tau[id] (read by the caller, which can
+// issue that load early): chi = eps_ref gamma sqrt((E + beta x B)^2 -
+// (beta . E)^2), tau[id] = tau0 - W(chi, gamma) dt, and when tau reaches zero a photon of energy
+// k = xi gamma (xi from the spectrum's inverse cumulative at the first Philox
+// word of counter (id, step, 0, 0)) is appended along u at (cell, off) with
+// weight w, u recoils to u (1 - k/|u|) and tau restarts at -ln of the second
+// word.  A photon that finds no room raises LPIC_ST_OVERFLOW and leaves the
+// particle untouched with its spent depth (it emits at a later step).
+// Returns true when u changed.
+__device__ __forceinline__ bool qed_emit(const QedEmit& Q, uint32_t step, int dim, int id, float tau0,
+                                         int cell, const float (&off)[3], float w, float (&u)[3],
+                                         const float (&fld)[6], unsigned* st) {
+    const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const float gam = sqrtf(1.0f + u2);
+    const float ig = 1.0f / gam;
+    const float b0 = u[0] * ig, b1 = u[1] * ig, b2 = u[2] * ig;
+    const float F0 = fld[0] + b1 * fld[5] - b2 * fld[4];
+    const float F1 = fld[1] + b2 * fld[3] - b0 * fld[5];
+    const float F2 = fld[2] + b0 * fld[4] - b1 * fld[3];
+    const float be = b0 * fld[0] + b1 * fld[1] + b2 * fld[2];
+    const float q2 = F0 * F0 + F1 * F1 + F2 * F2 - be * be;
+    const float chi = Q.T.eps_ref * gam * sqrtf(fmaxf(q2, 0.0f));
+    if (!(chi > 0.0f)) return false;
+    const float t = tau0 - Q.T.pref * qed_h(Q.T, chi) * ig * Q.dt;
+    if (t > 0.0f) { Q.tau[id] = t; return false; }
+    // emission: xi from the first word, the new depth from the second
+    const U4 o = philox4x32_10(U4{(uint32_t)id, step, 0u, 0u}, Q.k0, Q.k1);
+    const float r1 = fminf((float)u01d(o.x), 0.99999994f);
+    const float xi = qed_xi(Q.T, chi, r1);
+    const float umag = sqrtf(u2);
+    const float k = xi * gam;
+    const int j = atomicAdd(Q.ph_n, 1);
+    if ((long long)j >= Q.ph_cap) {
+        set_status(st, LPIC_ST_OVERFLOW);
+        Q.tau[id] = t;
+        return false;
+    }
+    const float s = k / umag;
+    Q.ph.cell[j] = cell;
+    for (int d = 0; d < dim; ++d) Q.ph.off[d][j] = off[d];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Q.ph.u[c][j] = s * u[c];
+    Q.ph.w[j] = w;
+    const int pid = atomicAdd(Q.ph_next_id, 1);
+    Q.ph.id[j] = pid;
+    if (Q.ph_tau) {
+        // the new photon's depth for pair creation: counter (id, 0, 3, 0)
+        if (pid >= 0 && (long long)pid < Q.ph_n_ids) {
+            const U4 q = philox4x32_10(U4{(uint32_t)pid, 0u, 3u, 0u}, Q.k0, Q.k1);
+            Q.ph_tau[pid] = (float)(-log(u01d(q.x)));
+        } else {
+            set_status(st, LPIC_ST_OVERFLOW);
+        }
+    }
+    const float keep = 1.0f - k / umag;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] *= keep;
+    Q.tau[id] = (float)(-log(u01d(o.y)));
+    return true;
+}
 
 struct Tiles {
     int T[3];            // cells per tile
@@ -620,9 +702,10 @@ struct LoadGlobal {
 //              folded when they could overflow (in 3D they are flushed to the
 //              global current instead: its boxes are large and shared memory
 //              bounds the blocks per SM);
-//   particles  two round buffers of DIM + 5 arrays (cell, offsets, momenta,
-//              weight) of kRoundWords words: the next round's particles are
-//              copied in asynchronously while the current round runs;
+//   particles  two round buffers of DIM + 6 arrays (cell, offsets, momenta,
+//              weight, and the id for the form with emission) of kRoundWords
+//              words: the next round's particles are copied in asynchronously
+//              while the current round runs;
 //   ring       (3D) moves whose two stencils start at different nodes, deposited
 //              256 at a time so that every warp runs one form of the deposit;
 //   counters   the bound of the current accumulated in the int32 boxes
@@ -652,7 +735,7 @@ __host__ __device__ inline TileSmem tile_smem(int dim, const int* T, const int* 
     s.off_r = up4(6 * s.fsz);
     s.off_64 = s.off_r + up4(3 * s.jsz);
     s.off_p = s.off_64 + (dim == 2 ? 2 * up4(3 * s.jsz) : 0);
-    s.off_ring = s.off_p + 2 * (dim + 5) * kRoundWords;
+    s.off_ring = s.off_p + 2 * (dim + 6) * kRoundWords;
     s.off_cnt = s.off_ring + (dim == 3 ? (dim + 5) * kRing : 0);
     s.words = s.off_cnt + kCntWords;
     return s;
@@ -748,13 +831,15 @@ struct GpdArgs {
     unsigned* st;
     float* fields;       // unfused stages: per-particle E_x..B_z, [6][fcap]
     long long fcap;
+    int qed;             // emission inside the push (kGpdQed form and the escape kernel)
+    QedEmit q;
 };
 
 // Forms of the tile kernel: the fused gather/push/deposit, and the two
 // stages of the unfused path (the gather alone, writing each particle's
 // fields; the push and deposit with fields read back).  Between them the
 // caller may change the fields (an external field, a diagnostic).
-enum { kGpdFused = 0, kGpdGather = 1, kGpdFieldsIn = 2 };
+enum { kGpdFused = 0, kGpdGather = 1, kGpdFieldsIn = 2, kGpdQed = 3 };
 
 // One work item (a tile, or a chunk of a crowded tile) of one species.
 template <int DIM, int ORDER, int MODE = kGpdFused>
@@ -792,7 +877,8 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     // lie cap words apart).  3D: copied in 16-byte chunks, warp w copying
     // array w (a barrier orders them before use).  2D: each thread copies
     // its own particle's words, so a round needs no barrier.
-    constexpr int NARR = DIM + 5;
+    constexpr int NARR = DIM + 5 + (MODE == kGpdQed ? 1 : 0);
+    constexpr int NBUF = DIM + 6;      // arrays per round buffer
     const long long astride = (long long)(reinterpret_cast<const char*>(p.off[0]) - reinterpret_cast<const char*>(p.cell));
     const int nround = (end - beg + kGpdThreads - 1) / kGpdThreads;
     auto prefetch = [&](int r) {
@@ -800,16 +886,15 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
         if constexpr (DIM == 2) {
             if (rb + tid < re) {
                 const char* src = reinterpret_cast<const char*>(p.cell) + 4LL * (rb + tid);
-                int* dst = sP + (r & 1) * NARR * kRoundWords + tid;
+                int* dst = sP + (r & 1) * NBUF * kRoundWords + tid;
 #pragma unroll
                 for (int k = 0; k < NARR; ++k) cp_async4(dst + k * kRoundWords, src + k * astride);
             }
         } else {
             const int a0 = rb & ~3, nch = (re - a0 + 3) >> 2;
-            const int arr = tid >> 5;
-            if (arr < NARR) {
+            for (int arr = tid >> 5; arr < NARR; arr += kGpdThreads / 32) {
                 const char* src = reinterpret_cast<const char*>(p.cell) + arr * astride + 4LL * a0;
-                int* dst = sP + ((r & 1) * NARR + arr) * kRoundWords;
+                int* dst = sP + ((r & 1) * NBUF + arr) * kRoundWords;
                 for (int q = tid & 31; q < nch; q += 32) cp_async16(dst + 4 * q, src + 16 * q);
             }
         }
@@ -919,7 +1004,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 
         const int rb = beg + rnd * kGpdThreads;
         const int i = rb + tid;
-        const int* slot = sP + (rnd & 1) * NARR * kRoundWords + (DIM == 3 ? rb - (rb & ~3) : 0) + tid;
+        const int* slot = sP + (rnd & 1) * NBUF * kRoundWords + (DIM == 3 ? rb - (rb & ~3) : 0) + tid;
         int cell = -1;
         float f[3] = {0.0f, 0.0f, 0.0f}, ux = 0.0f, uy = 0.0f, uz = 0.0f, w = 0.0f;
         if (i < end) {
@@ -930,6 +1015,14 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
             uy = __int_as_float(slot[(2 + DIM) * kRoundWords]);
             uz = __int_as_float(slot[(3 + DIM) * kRoundWords]);
             w = __int_as_float(slot[(4 + DIM) * kRoundWords]);
+        }
+        // form with emission: the particle's id and depth, loaded before the
+        // gather so that the depth's latency overlaps it
+        int qid = -1;
+        float qtau = 0.0f;
+        if (MODE == kGpdQed && cell >= 0) {
+            qid = slot[(5 + DIM) * kRoundWords];
+            if (qid >= 0 && (long long)qid < A.q.n_ids) qtau = A.q.tau[qid];
         }
         int cell_out = cell;            // the particle's cell after this round (-1: removed)
         unsigned bnd = 0;               // bound of the move this thread deposited
@@ -950,7 +1043,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                 inside &= (lc[d] >= 0 && lc[d] < Te[d]);
             }
             if (!inside) {
-                if (MODE == kGpdFused) {
+                if (MODE == kGpdFused || MODE == kGpdQed) {
                     // beyond the tile's drift margin: queued for the global-memory
                     // path, which also counts its new tile key
                     t.esc[atomicAdd(t.nesc, 1)] = i;
@@ -974,6 +1067,19 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 #pragma unroll
                     for (int c = 0; c < 6; ++c) A.fields[c * A.fcap + i] = fld[c];
                 } else {
+                if constexpr (MODE == kGpdQed) {
+                    // emission between the interpolation and the momentum push
+                    // (Algorithm 1), with u^n and the fields at x^{n+1/2}; the
+                    // photon leaves from x^{n+1/2}
+                    if (qid < 0 || (long long)qid >= A.q.n_ids) {
+                        set_status(st, LPIC_ST_OVERFLOW);
+                    } else {
+                        float uq[3] = {ux, uy, uz};
+                        if (qed_emit(A.q, *A.q.step, DIM, qid, qtau, cell, f, w, uq, fld, st)) {
+                            ux = uq[0]; uy = uq[1]; uz = uq[2];
+                        }
+                    }
+                }
                 boris_f32(ux, uy, uz, A.k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
                 if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
                     set_status(st, LPIC_ST_NAN);
@@ -1185,6 +1291,18 @@ __global__ void __launch_bounds__(256) k_gpd32_escape(GpdArgs A) {
                                      {gc[0], gc[1], gc[2]}, &outside};
             gather32<DIM, ORDER>(ld, nx_, ny_, nz_, hx_, hy_, hz_, fld);
             if (outside) set_status(st, LPIC_ST_OUTSIDE);
+            if (A.qed) {
+                // the emission of the tile kernel's kGpdQed form
+                const int id = p.id[i];
+                if (id < 0 || (long long)id >= A.q.n_ids) {
+                    set_status(st, LPIC_ST_OVERFLOW);
+                } else {
+                    float uq[3] = {ux, uy, uz};
+                    if (qed_emit(A.q, *A.q.step, DIM, id, A.q.tau[id], p.cell[i], f, w, uq, fld, st)) {
+                        ux = uq[0]; uy = uq[1]; uz = uq[2];
+                    }
+                }
+            }
             boris_f32(ux, uy, uz, k, fld[0], fld[1], fld[2], fld[3], fld[4], fld[5]);
             if (!isfinite(ux) || !isfinite(uy) || !isfinite(uz)) {
                 set_status(st, LPIC_ST_NAN);

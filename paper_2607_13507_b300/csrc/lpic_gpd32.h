@@ -34,4 +34,13 @@ struct Gpd32Stages {
     static void push(const GpdArgs& A, unsigned blocks, size_t smem, cudaStream_t st);
 };
 
+// The fused kernel with nonlinear Compton emission inside the push
+// (kGpdQed), compiled in translation units of its own
+// (lpic_gpd32q_<dim><order>.cu); its escapes go to Gpd32::escape.
+template <int DIM, int ORDER>
+struct Gpd32Qed {
+    static cudaError_t set_smem(size_t bytes);
+    static void tile(const GpdArgs& A, unsigned blocks, size_t smem, cudaStream_t st);
+};
+
 }  // namespace lpic

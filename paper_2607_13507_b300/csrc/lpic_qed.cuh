@@ -30,92 +30,6 @@
 
 namespace lpic {
 
-// ------------------------------------------------------------ Philox4x32-10
-struct U4 { uint32_t x, y, z, w; };
-
-__host__ __device__ inline void mulhilo32(uint32_t a, uint32_t b, uint32_t& hi, uint32_t& lo) {
-    const uint64_t p = (uint64_t)a * (uint64_t)b;
-    hi = (uint32_t)(p >> 32);
-    lo = (uint32_t)p;
-}
-
-// Ten rounds of the Philox-4x32 bijection (multipliers 0xD2511F53 and
-// 0xCD9E8D57, Weyl key increments 0x9E3779B9 and 0xBB67AE85).
-__host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        uint32_t h0, l0, h1, l1;
-        mulhilo32(0xD2511F53u, c.x, h0, l0);
-        mulhilo32(0xCD9E8D57u, c.z, h1, l1);
-        c = U4{h1 ^ c.y ^ k0, l1, h0 ^ c.w ^ k1, l0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// uniform in (0, 1) from 32 bits: (x + 1/2) 2^-32
-__device__ inline double u01d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
-
-// --------------------------------------------------------------- the tables
-struct QedTab {
-    const float* logh;     // [nchi]
-    const float* cdf;      // [nchi][ny]
-    const float* top;      // [nchi]
-    int nchi, ny;
-    float lchi0, inv_dl;   // ln chi_0, 1 / dl
-    float chi0;
-    float pref;            // alpha / (eps_ref sqrt(3) pi): W = pref h(chi) / gamma
-    float eps_ref;
-};
-
-// h(chi): piecewise linear in (ln chi, ln h); linear extrapolation in the
-// log-log plane past the last node (h grows like chi^{2/3} there).
-__device__ inline float qed_h(const QedTab& T, float chi) {
-    if (chi <= T.chi0) return __expf(T.logh[0]) * (chi / T.chi0);
-    const float u = (logf(chi) - T.lchi0) * T.inv_dl;
-    const int i = min((int)u, T.nchi - 2);
-    const float f = u - (float)i;
-    return expf(T.logh[i] + f * (T.logh[i + 1] - T.logh[i]));
-}
-
-__device__ inline float qed_map(float y, float top) {
-    const float y3 = y * y * y;
-    return top < 1.0f ? top * y3 : y3 * (10.0f + y * (-15.0f + 6.0f * y));
-}
-
-// xi of cumulative probability r in table row i: bisection for the interval
-// of the cumulative holding r, then xi^{1/3} linear in the probability (the
-// cumulative grows like xi^{1/3} at small xi).
-__device__ inline float qed_row_xi(const QedTab& T, int i, float r) {
-    const float* P = T.cdf + (long long)i * T.ny;
-    int lo = 0, hi = T.ny - 1;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (P[mid] <= r) lo = mid; else hi = mid;
-    }
-    const float pa = P[lo], pb = P[hi];
-    const float f = pb > pa ? fminf((r - pa) / (pb - pa), 1.0f) : 0.0f;
-    const float dy = 1.0f / (float)(T.ny - 1);
-    const float za = cbrtf(qed_map((float)lo * dy, T.top[i]));
-    const float zb = cbrtf(qed_map((float)hi * dy, T.top[i]));
-    const float z = za + f * (zb - za);
-    return z * z * z;
-}
-
-// xi(chi, r): rows interpolated in (ln chi, ln xi) (exact in the classical
-// limit, where xi is proportional to chi); clamped to the last row.
-__device__ inline float qed_xi(const QedTab& T, float chi, float r) {
-    if (chi <= T.chi0) return qed_row_xi(T, 0, r) * (chi / T.chi0);
-    float u = (logf(chi) - T.lchi0) * T.inv_dl;
-    u = fminf(u, (float)(T.nchi - 1));
-    const int i = min((int)u, T.nchi - 2);
-    const float f = u - (float)i;
-    const float a = qed_row_xi(T, i, r), b = qed_row_xi(T, i + 1, r);
-    if (!(a > 0.0f) || !(b > 0.0f)) return a + f * (b - a);
-    return expf(logf(a) + f * (logf(b) - logf(a)));
-}
-
 // --------------------------------------------------------------- the kernels
 // Initial optical depths tau[id] = -ln r, r from counter (id, 0, kind, 0):
 // kind 2 for emitting particles, 3 for photons (pair creation).
@@ -222,6 +136,8 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
     const P32& p = A.e;
     const int n = *p.n;
     const float dth[3] = {A.dth0, A.dth1, A.dth2};
+    const QedEmit Q{A.T, A.tau, A.n_ids, A.ph, A.ph_n, A.ph_next_id, A.ph_cap, A.ph_tau, A.ph_n_ids, A.dt,
+                    A.k0, A.k1, nullptr};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int cell = p.cell[i];
         if (cell < 0) continue;
@@ -229,69 +145,26 @@ __global__ void __launch_bounds__(256) k_qed_compton32(QedArgs A) {
         if (id < 0 || (long long)id >= A.n_ids) { set_status(A.st, LPIC_ST_OVERFLOW); continue; }
         float u[3] = {p.u[0][i], p.u[1][i], p.u[2][i]};
         const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const float gam = sqrtf(1.0f + u2);
-        const float ig = 1.0f / gam;
+        const float ig = 1.0f / sqrtf(1.0f + u2);
         int gc[3];
         A.dec(cell, gc);
         if (DIM == 2) gc[2] = 0;
-        float f[3] = {0.0f, 0.0f, 0.0f};
+        float f[3] = {0.0f, 0.0f, 0.0f}, off[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            float fd = p.off[d][i] - 0.5f * dth[d] * u[d] * ig;
+            off[d] = p.off[d][i];
+            float fd = off[d] - 0.5f * dth[d] * u[d] * ig;
             if (fd < 0.0f) { fd += 1.0f; gc[d] -= 1; if (fd >= 1.0f) fd = 0.99999994f; }
             else if (fd >= 1.0f) { fd -= 1.0f; gc[d] += 1; }
             f[d] = fd;
         }
         float fld[6];
         if (!qed_gather<DIM, ORDER>(A, gc, f, fld)) { set_status(A.st, LPIC_ST_OUTSIDE); continue; }
-        const float b0 = u[0] * ig, b1 = u[1] * ig, b2 = u[2] * ig;
-        const float F0 = fld[0] + b1 * fld[5] - b2 * fld[4];
-        const float F1 = fld[1] + b2 * fld[3] - b0 * fld[5];
-        const float F2 = fld[2] + b0 * fld[4] - b1 * fld[3];
-        const float be = b0 * fld[0] + b1 * fld[1] + b2 * fld[2];
-        const float q2 = F0 * F0 + F1 * F1 + F2 * F2 - be * be;
-        const float chi = A.T.eps_ref * gam * sqrtf(fmaxf(q2, 0.0f));
-        if (!(chi > 0.0f)) continue;
-        float t = A.tau[id] - A.T.pref * qed_h(A.T, chi) * ig * A.dt;
-        if (t > 0.0f) { A.tau[id] = t; continue; }
-        // emission: xi from the first word, the new depth from the second
-        const U4 o = philox4x32_10(U4{(uint32_t)id, A.step, 0u, 0u}, A.k0, A.k1);
-        const float r1 = fminf((float)u01d(o.x), 0.99999994f);
-        const float xi = qed_xi(A.T, chi, r1);
-        const float umag = sqrtf(u2);
-        const float k = xi * gam;
-        const int j = atomicAdd(A.ph_n, 1);
-        if ((long long)j >= A.ph_cap) {
-            // no room for the photon: no event this time, so the emitter keeps
-            // its momentum and its spent depth, and emits once room exists
-            set_status(A.st, LPIC_ST_OVERFLOW);
-            A.tau[id] = t;
-            continue;
+        // the photon is stored at the emitter's stored position
+        if (qed_emit(Q, A.step, DIM, id, A.tau[id], cell, off, p.w[i], u, fld, A.st)) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p.u[c][i] = u[c];
         }
-        {
-            const float s = k / umag;
-            A.ph.cell[j] = cell;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) A.ph.off[d][j] = p.off[d][i];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) A.ph.u[c][j] = s * u[c];
-            A.ph.w[j] = p.w[i];
-            const int pid = atomicAdd(A.ph_next_id, 1);
-            A.ph.id[j] = pid;
-            if (A.ph_tau) {
-                // the new photon's depth for pair creation: counter (id, 0, 3, 0)
-                if (pid >= 0 && (long long)pid < A.ph_n_ids) {
-                    const U4 q = philox4x32_10(U4{(uint32_t)pid, 0u, 3u, 0u}, A.k0, A.k1);
-                    A.ph_tau[pid] = (float)(-log(u01d(q.x)));
-                } else {
-                    set_status(A.st, LPIC_ST_OVERFLOW);
-                }
-            }
-        }
-        const float keep = 1.0f - k / umag;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) p.u[c][i] = u[c] * keep;
-        A.tau[id] = (float)(-log(u01d(o.y)));
     }
 }
 

@@ -32,7 +32,8 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_kernel_time", "lpic_create_ensemble", "lpic_destroy_ensemble",
            "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
            "lpic_ensemble_launches", "lpic_qed_init", "lpic_qed_initial_tau", "lpic_qed_compton",
-           "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval", "lpic_species_set_next_id"]
+           "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval", "lpic_species_set_next_id",
+           "lpic_qed_fuse", "lpic_qed_set_step"]
 
 
 class LpicError(RuntimeError):
@@ -137,6 +138,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_qed_breit_wheeler.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, ctypes.c_longlong, st]
     lib.lpic_qed_pair_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
     lib.lpic_species_set_next_id.argtypes = [vp, i, ctypes.c_longlong, st]
+    lib.lpic_qed_fuse.argtypes = [vp, i, i, vp, ctypes.c_longlong, vp, ctypes.c_longlong, ctypes.c_longlong, st]
+    lib.lpic_qed_set_step.argtypes = [vp, ctypes.c_longlong, st]
     lib.lpic_last_error.restype = ctypes.c_char_p
     lib.lpic_last_error.argtypes = []
     for name in EXPORTS:
@@ -366,6 +369,23 @@ class Grid:
             assert photon_tau.dtype == torch.float32 and photon_tau.is_cuda and photon_tau.is_contiguous()
         _check(load().lpic_qed_compton(self.h_, electrons.id, photons.id, tau.data_ptr(), tau.numel(),
                                        pt, pn, int(step), _stream(stream)))
+
+    def qed_fuse(self, electrons, photons, tau, first_step=0, stream=None, photon_tau=None):
+        """Emission of `electrons` into `photons` inside every push of
+        `electrons` (photons=None turns it off); the counter word starts at
+        first_step and advances with each full step."""
+        if photons is None:
+            _check(load().lpic_qed_fuse(self.h_, electrons.id, -1, None, 0, None, 0, 0, _stream(stream)))
+            return
+        assert tau.dtype == torch.float32 and tau.is_cuda and tau.is_contiguous()
+        pt, pn = (None, 0) if photon_tau is None else (photon_tau.data_ptr(), photon_tau.numel())
+        if photon_tau is not None:
+            assert photon_tau.dtype == torch.float32 and photon_tau.is_cuda and photon_tau.is_contiguous()
+        _check(load().lpic_qed_fuse(self.h_, electrons.id, photons.id, tau.data_ptr(), tau.numel(), pt, pn,
+                                    int(first_step), _stream(stream)))
+
+    def qed_set_step(self, step, stream=None):
+        _check(load().lpic_qed_set_step(self.h_, int(step), _stream(stream)))
 
     def qed_breit_wheeler(self, photons, electrons, positrons, tau, step, stream=None):
         """One pair-creation pass of `photons` into `electrons` and `positrons`."""

@@ -58,9 +58,11 @@ def test_ensemble_members_match_oracle(mode):
     from paper_2607_13507_b300 import lpic
     wls = _members()
     grids, orc = [], []
-    for wl in wls:
+    # members keep their own tile shapes and particles per block
+    launch = [((8, 8), 2048), ((16, 8), 4096), ((16, 16), 8192)]
+    for wl, (tile, P) in zip(wls, launch):
         parts = W.load_all(wl)
-        G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(8, 8))
+        G = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile, block_particles=P)
         G.add_species(parts[0])
         grids.append(G)
         orc.append(oracle_case(wl, parts))

@@ -468,11 +468,13 @@ def test_sort_interval_gives_bitwise_identical_state(case):
         assert np.array_equal(sa["u"][:, oa], sb["u"][:, ob])
 
 
-@pytest.mark.parametrize("mode", ["eager", "graph"])
-def test_ensemble_matches_grids_stepped_alone(mode):
+@pytest.mark.parametrize("mode,tiles", [("eager", "uniform"), ("graph", "uniform"), ("eager", "mixed"),
+                                        ("graph", "mixed")])
+def test_ensemble_matches_grids_stepped_alone(mode, tiles):
     """A batch of uneven periodic plasmas stepped through one ensemble (batched
     field and sort kernels, one persistent particle kernel with a device work
-    queue) ends bit for bit where the same grids stepped one by one end."""
+    queue) ends bit for bit where the same grids stepped one by one end; with
+    "mixed", members carry different tile shapes and particles per block."""
     from paper_2607_13507_b300 import lpic
     rng = np.random.Generator(np.random.Philox(11))
     wls = []
@@ -483,10 +485,12 @@ def test_ensemble_matches_grids_stepped_alone(mode):
         wl.n = (nx, ny)
         wls.append(wl)
     A, B = [], []
-    for wl in wls:
+    mixed = [((8, 8), 2048), ((16, 8), 4096), ((16, 16), 8192), ((8, 16), 1024)]
+    for i, wl in enumerate(wls):
         parts = W.load_all(wl)
-        ga = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(8, 8))
-        gb = lpic.grid_for(wl, lpic.FP32_FIXED, tile=(8, 8))
+        tile, P = mixed[i % len(mixed)] if tiles == "mixed" else ((8, 8), 0)
+        ga = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile, block_particles=P)
+        gb = lpic.grid_for(wl, lpic.FP32_FIXED, tile=tile, block_particles=P)
         ga.add_species(parts[0])
         gb.add_species(parts[0])
         A.append(ga)
