@@ -93,7 +93,7 @@ __device__ __forceinline__ bool qed_emit(const QedEmit& Q, uint32_t step, int di
     if (t > 0.0f) { Q.tau[id] = t; return false; }
     // emission: xi from the first word, the new depth from the second
     const U4 o = philox4x32_10(U4{(uint32_t)id, step, 0u, 0u}, Q.k0, Q.k1);
-    const float r1 = fminf((float)u01d(o.x), 0.99999994f);
+    const float r1 = u01f(o.x);
     const float xi = qed_xi(Q.T, chi, r1);
     const float umag = sqrtf(u2);
     const float k = xi * gam;
@@ -115,7 +115,7 @@ __device__ __forceinline__ bool qed_emit(const QedEmit& Q, uint32_t step, int di
         // the new photon's depth for pair creation: counter (id, 0, 3, 0)
         if (pid >= 0 && (long long)pid < Q.ph_n_ids) {
             const U4 q = philox4x32_10(U4{(uint32_t)pid, 0u, 3u, 0u}, Q.k0, Q.k1);
-            Q.ph_tau[pid] = (float)(-log(u01d(q.x)));
+            Q.ph_tau[pid] = neg_log_u01(q.x);
         } else {
             set_status(st, LPIC_ST_OVERFLOW);
         }
@@ -123,7 +123,7 @@ __device__ __forceinline__ bool qed_emit(const QedEmit& Q, uint32_t step, int di
     const float keep = 1.0f - k / umag;
 #pragma unroll
     for (int c = 0; c < 3; ++c) u[c] *= keep;
-    Q.tau[id] = (float)(-log(u01d(o.y)));
+    Q.tau[id] = neg_log_u01(o.y);
     return true;
 }
 

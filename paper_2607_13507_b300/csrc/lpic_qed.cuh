@@ -37,7 +37,7 @@ __global__ void k_qed_tau0(float* tau, long long n_ids, uint32_t kind, uint32_t 
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < n_ids;
          id += (long long)gridDim.x * blockDim.x) {
         const U4 o = philox4x32_10(U4{(uint32_t)id, 0u, kind, 0u}, k0, k1);
-        tau[id] = (float)(-log(u01d(o.x)));
+        tau[id] = neg_log_u01(o.x);
     }
 }
 
@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256) k_qed_bw32(BwArgs A) {
         Q.tau[id] = t;
         if (t > 0.0f) continue;
         const U4 o = philox4x32_10(U4{(uint32_t)id, Q.step, 1u, 0u}, Q.k0, Q.k1);
-        const float r = fminf((float)u01d(o.x), 0.99999994f);
+        const float r = u01f(o.x);
         const float eta = bw_eta(A.T, chi, r);
         const float w = p.w[i];
         const int je = atomicAdd(A.el_n, 1), jp = atomicAdd(A.po_n, 1);

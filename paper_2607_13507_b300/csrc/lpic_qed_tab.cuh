@@ -33,7 +33,17 @@ __host__ __device__ inline U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
 }
 
 // uniform in (0, 1) from 32 bits: (x + 1/2) 2^-32
-__device__ inline double u01d(uint32_t x) { return ((double)x + 0.5) * 2.3283064365386963e-10; }
+// (x + 1/2) 2^-32 in single precision, kept below 1
+__device__ __forceinline__ float u01f(uint32_t x) { return fminf(((float)x + 0.5f) * 0x1p-32f, 0.99999994f); }
+
+// -ln u for u = (x + 1/2) 2^-32, in single precision (the FP64 units of this
+// part are slow): below 1/2 from u itself, above it as -log1p(-(1 - u)) with
+// 1 - u = ((2^32 - 1 - x) + 1/2) 2^-32 formed without cancellation, so the
+// relative error stays at float rounding for every x
+__device__ __forceinline__ float neg_log_u01(uint32_t x) {
+    if (x < 0x80000000u) return -logf(((float)x + 0.5f) * 0x1p-32f);
+    return -log1pf(-(((float)(0xFFFFFFFFu - x) + 0.5f) * 0x1p-32f));
+}
 
 // --------------------------------------------------------------- the tables
 struct QedTab {
@@ -62,16 +72,11 @@ __device__ inline float qed_map(float y, float top) {
     return top < 1.0f ? top * y3 : y3 * (10.0f + y * (-15.0f + 6.0f * y));
 }
 
-// xi of cumulative probability r in table row i: bisection for the interval
-// of the cumulative holding r, then xi^{1/3} linear in the probability (the
-// cumulative grows like xi^{1/3} at small xi).
-__device__ inline float qed_row_xi(const QedTab& T, int i, float r) {
+// xi of cumulative probability r in table row i, given the interval
+// [lo, hi] of the row's cumulative that holds r: xi^{1/3} linear in the
+// probability (the cumulative grows like xi^{1/3} at small xi).
+__device__ __forceinline__ float qed_row_xi_at(const QedTab& T, int i, int lo, int hi, float r) {
     const float* P = T.cdf + (long long)i * T.ny;
-    int lo = 0, hi = T.ny - 1;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (P[mid] <= r) lo = mid; else hi = mid;
-    }
     const float pa = P[lo], pb = P[hi];
     const float f = pb > pa ? fminf((r - pa) / (pb - pa), 1.0f) : 0.0f;
     const float dy = 1.0f / (float)(T.ny - 1);
@@ -81,15 +86,36 @@ __device__ inline float qed_row_xi(const QedTab& T, int i, float r) {
     return z * z * z;
 }
 
+// The intervals holding r in rows i0 and i1, by bisections of both rows in
+// one loop (their loads are independent, so the two chains of dependent
+// loads overlap).
+__device__ __forceinline__ void qed_bisect2(const QedTab& T, int i0, int i1, float r, int& lo0, int& hi0,
+                                            int& lo1, int& hi1) {
+    const float* P0 = T.cdf + (long long)i0 * T.ny;
+    const float* P1 = T.cdf + (long long)i1 * T.ny;
+    lo0 = 0; hi0 = T.ny - 1; lo1 = 0; hi1 = T.ny - 1;
+    while (hi0 - lo0 > 1 || hi1 - lo1 > 1) {
+        const int m0 = (lo0 + hi0) >> 1, m1 = (lo1 + hi1) >> 1;
+        const float p0 = P0[m0], p1 = P1[m1];
+        if (hi0 - lo0 > 1) { if (p0 <= r) lo0 = m0; else hi0 = m0; }
+        if (hi1 - lo1 > 1) { if (p1 <= r) lo1 = m1; else hi1 = m1; }
+    }
+}
+
 // xi(chi, r): rows interpolated in (ln chi, ln xi) (exact in the classical
 // limit, where xi is proportional to chi); clamped to the last row.
 __device__ inline float qed_xi(const QedTab& T, float chi, float r) {
-    if (chi <= T.chi0) return qed_row_xi(T, 0, r) * (chi / T.chi0);
+    int lo0, hi0, lo1, hi1;
+    if (chi <= T.chi0) {
+        qed_bisect2(T, 0, 0, r, lo0, hi0, lo1, hi1);
+        return qed_row_xi_at(T, 0, lo0, hi0, r) * (chi / T.chi0);
+    }
     float u = (logf(chi) - T.lchi0) * T.inv_dl;
     u = fminf(u, (float)(T.nchi - 1));
     const int i = min((int)u, T.nchi - 2);
     const float f = u - (float)i;
-    const float a = qed_row_xi(T, i, r), b = qed_row_xi(T, i + 1, r);
+    qed_bisect2(T, i, i + 1, r, lo0, hi0, lo1, hi1);
+    const float a = qed_row_xi_at(T, i, lo0, hi0, r), b = qed_row_xi_at(T, i + 1, lo1, hi1, r);
     if (!(a > 0.0f) || !(b > 0.0f)) return a + f * (b - a);
     return expf(logf(a) + f * (logf(b) - logf(a)));
 }
