@@ -485,6 +485,13 @@ lpic_status lpic_qed_pair_eval(lpic_grid_t grid, const double *chi, const double
 lpic_status lpic_qed_eval(lpic_grid_t grid, const double *chi, const double *r, long long n, double *h,
                           double *xi, cudaStream_t stream);
 
+/* Fault injection for tests: from this call on, the nth device allocation
+ * the library makes (counted over all grids, species, ensembles and tables)
+ * fails as if the device were out of memory; the call that made it unwinds
+ * what it had allocated and returns LPIC_ENOMEM.  nth = 0 turns injection
+ * off.  Not thread-safe; for tests only. */
+lpic_status lpic_debug_fail_alloc(long long nth);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char *lpic_last_error(void);
 

@@ -2,6 +2,7 @@
 // Descriptor checks, scratch ownership, the fixed-point shift, and the
 // launches of the Maxwell, sort, particle and diagnostic kernels.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -50,6 +51,23 @@ lpic_status fail(lpic_status s, const char* fmt, ...) {
         cudaError_t e_ = cudaGetLastError();                                              \
         if (e_ != cudaSuccess) return fail(LPIC_ECUDA, "launch %s: %s", what, cudaGetErrorString(e_)); \
     } while (0)
+
+// Every device allocation of the library goes through dev_alloc, so that
+// a test can make the n-th one fail as if the device were out of memory
+// (lpic_debug_fail_alloc) and check that each call unwinds and reports
+// LPIC_ENOMEM.
+std::atomic<long long> g_alloc_fail_at{0};    // 0: off
+std::atomic<long long> g_alloc_seen{0};
+
+template <class T>
+cudaError_t dev_alloc(T** p, size_t bytes) {
+    const long long k = g_alloc_fail_at.load();
+    if (k > 0 && g_alloc_seen.fetch_add(1) + 1 == k) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
 
 struct Species {
     double q = 0, m = 1;
@@ -625,14 +643,14 @@ lpic_status lpic_create_grid(const lpic_grid_desc* desc, lpic_grid_t* out) {
     }
     const size_t fbytes = (d.precision == LPIC_FP64 || d.maxwell_fp64) ? 8 : 4;
     const int plane = d.ny * nz;
-    if (cudaMalloc(&g->d_status, 64) != cudaSuccess ||
-        cudaMalloc(&g->d_clock, 64) != cudaSuccess ||
-        cudaMalloc(&g->d_acc, 64) != cudaSuccess ||
-        cudaMalloc(&g->d_cnt, 64) != cudaSuccess ||
-        (d.absorb_x == 1 && cudaMalloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess) ||
-        (g->cpml && cudaMalloc(&g->d_psi, fbytes * 4 * plane * (2 * d.pml_cells + 2)) != cudaSuccess) ||
-        (g->cpml && cudaMalloc(&g->d_pcoef, fbytes * 6 * fx) != cudaSuccess) ||
-        (g->laser.on && cudaMalloc(&g->d_lprof, sizeof(double) * plane) != cudaSuccess)) {
+    if (dev_alloc(&g->d_status, 64) != cudaSuccess ||
+        dev_alloc(&g->d_clock, 64) != cudaSuccess ||
+        dev_alloc(&g->d_acc, 64) != cudaSuccess ||
+        dev_alloc(&g->d_cnt, 64) != cudaSuccess ||
+        (d.absorb_x == 1 && dev_alloc(&g->d_mur, fbytes * 8 * plane) != cudaSuccess) ||
+        (g->cpml && dev_alloc(&g->d_psi, fbytes * 4 * plane * (2 * d.pml_cells + 2)) != cudaSuccess) ||
+        (g->cpml && dev_alloc(&g->d_pcoef, fbytes * 6 * fx) != cudaSuccess) ||
+        (g->laser.on && dev_alloc(&g->d_lprof, sizeof(double) * plane) != cudaSuccess)) {
         lpic_destroy_grid(g);
         return fail(LPIC_ENOMEM, "scratch allocation failed");
     }
@@ -742,15 +760,15 @@ lpic_status lpic_add_species(lpic_grid_t g, const lpic_species_desc* desc, cudaS
     s.buf[0] = d.buffers[0]; s.buf[1] = d.buffers[1];
     const int nt = (int)g->ntiles;
     s.item_cap = nt + (d.capacity + g->P - 1) / g->P + 1;
-    if (cudaMalloc(&s.d_n, sizeof(int) * 4) != cudaSuccess ||
-        cudaMalloc(&s.d_count, sizeof(int) * (nt + 1)) != cudaSuccess ||
-        cudaMalloc(&s.d_start, sizeof(int) * (nt + 2)) != cudaSuccess ||
-        cudaMalloc(&s.d_cursor, sizeof(int) * (nt + 1)) != cudaSuccess ||
-        cudaMalloc(&s.d_coff, sizeof(int) * (nt + 1)) != cudaSuccess ||
-        cudaMalloc(&s.d_items, sizeof(int2) * s.item_cap) != cudaSuccess ||
-        cudaMalloc(&s.d_nitems, sizeof(int) * 4) != cudaSuccess ||
-        cudaMalloc(&s.d_esc, sizeof(int) * d.capacity) != cudaSuccess ||
-        cudaMalloc(&s.d_nesc, sizeof(int) * 4) != cudaSuccess) {
+    if (dev_alloc(&s.d_n, sizeof(int) * 4) != cudaSuccess ||
+        dev_alloc(&s.d_count, sizeof(int) * (nt + 1)) != cudaSuccess ||
+        dev_alloc(&s.d_start, sizeof(int) * (nt + 2)) != cudaSuccess ||
+        dev_alloc(&s.d_cursor, sizeof(int) * (nt + 1)) != cudaSuccess ||
+        dev_alloc(&s.d_coff, sizeof(int) * (nt + 1)) != cudaSuccess ||
+        dev_alloc(&s.d_items, sizeof(int2) * s.item_cap) != cudaSuccess ||
+        dev_alloc(&s.d_nitems, sizeof(int) * 4) != cudaSuccess ||
+        dev_alloc(&s.d_esc, sizeof(int) * d.capacity) != cudaSuccess ||
+        dev_alloc(&s.d_nesc, sizeof(int) * 4) != cudaSuccess) {
         cudaFree(s.d_n); cudaFree(s.d_count); cudaFree(s.d_start); cudaFree(s.d_cursor);
         cudaFree(s.d_coff); cudaFree(s.d_items); cudaFree(s.d_nitems);
         cudaFree(s.d_esc); cudaFree(s.d_nesc);
@@ -1420,14 +1438,14 @@ lpic_status lpic_create_ensemble(lpic_grid_t* grids, int n, lpic_ensemble_t* out
     for (int i = 0; i < e->nslots; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return density[a] > density[b]; });
     auto cleanup = [&](lpic_status st, const char* msg) { lpic_destroy_ensemble(e); return fail(st, "%s", msg); };
-    if (cudaMalloc(&e->d_fields, sizeof(EnsField) * n) != cudaSuccess ||
-        cudaMalloc(&e->d_sort, sizeof(EnsSort) * e->nslots) != cudaSuccess ||
-        cudaMalloc(&e->d_args[0], sizeof(GpdArgs) * e->nslots) != cudaSuccess ||
-        cudaMalloc(&e->d_args[1], sizeof(GpdArgs) * e->nslots) != cudaSuccess ||
-        cudaMalloc(&e->d_order, sizeof(int) * e->nslots) != cudaSuccess ||
-        cudaMalloc(&e->d_prefix, sizeof(int) * (e->nslots + 1)) != cudaSuccess ||
-        cudaMalloc(&e->d_head, 64) != cudaSuccess ||
-        cudaMalloc(&e->d_status, 64) != cudaSuccess)
+    if (dev_alloc(&e->d_fields, sizeof(EnsField) * n) != cudaSuccess ||
+        dev_alloc(&e->d_sort, sizeof(EnsSort) * e->nslots) != cudaSuccess ||
+        dev_alloc(&e->d_args[0], sizeof(GpdArgs) * e->nslots) != cudaSuccess ||
+        dev_alloc(&e->d_args[1], sizeof(GpdArgs) * e->nslots) != cudaSuccess ||
+        dev_alloc(&e->d_order, sizeof(int) * e->nslots) != cudaSuccess ||
+        dev_alloc(&e->d_prefix, sizeof(int) * (e->nslots + 1)) != cudaSuccess ||
+        dev_alloc(&e->d_head, 64) != cudaSuccess ||
+        dev_alloc(&e->d_status, 64) != cudaSuccess)
         return cleanup(LPIC_ENOMEM, "ensemble table allocation failed");
     if (cudaMemcpy(e->d_fields, hf.data(), sizeof(EnsField) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(e->d_sort, hs.data(), sizeof(EnsSort) * e->nslots, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1539,7 +1557,7 @@ lpic_status lpic_qed_init(lpic_grid_t g, double eps_ref, uint64_t seed, cudaStre
         const QedHostTables H = qed_build_tables(1e-4, 1e3, 32, 513);
         const size_t n = H.logh.size() + H.top.size() + H.cdf.size();
         float* d = nullptr;
-        if (cudaMalloc(&d, n * sizeof(float)) != cudaSuccess) return fail(LPIC_ENOMEM, "QED table allocation failed");
+        if (dev_alloc(&d, n * sizeof(float)) != cudaSuccess) return fail(LPIC_ENOMEM, "QED table allocation failed");
         g->d_qtab = d;
         LPIC_CUDA(cudaMemcpyAsync(d, H.logh.data(), H.logh.size() * 4, cudaMemcpyHostToDevice, st));
         LPIC_CUDA(cudaMemcpyAsync(d + H.nchi, H.top.data(), H.top.size() * 4, cudaMemcpyHostToDevice, st));
@@ -1554,7 +1572,7 @@ lpic_status lpic_qed_init(lpic_grid_t g, double eps_ref, uint64_t seed, cudaStre
         const BwHostTables H = bw_build_tables(1e-2, 1e3, 32, 513);
         const size_t n = H.g.size() + H.cdf.size();
         float* d = nullptr;
-        if (cudaMalloc(&d, n * sizeof(float)) != cudaSuccess) return fail(LPIC_ENOMEM, "QED table allocation failed");
+        if (dev_alloc(&d, n * sizeof(float)) != cudaSuccess) return fail(LPIC_ENOMEM, "QED table allocation failed");
         g->d_btab = d;
         LPIC_CUDA(cudaMemcpyAsync(d, H.g.data(), H.g.size() * 4, cudaMemcpyHostToDevice, st));
         LPIC_CUDA(cudaMemcpyAsync(d + H.nchi, H.cdf.data(), H.cdf.size() * 4, cudaMemcpyHostToDevice, st));
@@ -1657,7 +1675,7 @@ lpic_status lpic_qed_fuse(lpic_grid_t g, int sid_e, int sid_ph, float* tau, long
         e.q_ph = -1;
         return LPIC_OK;
     }
-    if (!g->d_qstep && cudaMalloc(&g->d_qstep, 64) != cudaSuccess)
+    if (!g->d_qstep && dev_alloc(&g->d_qstep, 64) != cudaSuccess)
         return fail(LPIC_ENOMEM, "step counter allocation failed");
     e.q_ph = sid_ph;
     e.q_tau = tau;
@@ -1675,6 +1693,13 @@ lpic_status lpic_qed_set_step(lpic_grid_t g, long long step, cudaStream_t st) {
     if (step < 0 || step > 0xffffffffLL) return fail(LPIC_EINVAL, "step must fit 32 bits");
     k_set_uint<<<1, 32, 0, st>>>(g->d_qstep, (unsigned)step);
     LPIC_LAUNCHED("k_set_uint");
+    return LPIC_OK;
+}
+
+lpic_status lpic_debug_fail_alloc(long long nth) {
+    if (nth < 0) return fail(LPIC_EINVAL, "nth must be >= 0");
+    g_alloc_seen.store(0);
+    g_alloc_fail_at.store(nth);
     return LPIC_OK;
 }
 

@@ -33,7 +33,7 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
            "lpic_ensemble_launches", "lpic_qed_init", "lpic_qed_initial_tau", "lpic_qed_compton",
            "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval", "lpic_species_set_next_id",
-           "lpic_qed_fuse", "lpic_qed_set_step"]
+           "lpic_qed_fuse", "lpic_qed_set_step", "lpic_debug_fail_alloc"]
 
 
 class LpicError(RuntimeError):
@@ -140,6 +140,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_species_set_next_id.argtypes = [vp, i, ctypes.c_longlong, st]
     lib.lpic_qed_fuse.argtypes = [vp, i, i, vp, ctypes.c_longlong, vp, ctypes.c_longlong, ctypes.c_longlong, st]
     lib.lpic_qed_set_step.argtypes = [vp, ctypes.c_longlong, st]
+    lib.lpic_debug_fail_alloc.argtypes = [ctypes.c_longlong]
     lib.lpic_last_error.restype = ctypes.c_char_p
     lib.lpic_last_error.argtypes = []
     for name in EXPORTS:
@@ -545,6 +546,11 @@ class Ensemble:
         n = ctypes.c_longlong()
         _check(load().lpic_ensemble_launches(self.h_, ctypes.byref(n)))
         return n.value
+
+
+def debug_fail_alloc(nth: int):
+    """Tests: make the library's nth device allocation from now fail (0: off)."""
+    _check(load().lpic_debug_fail_alloc(int(nth)))
 
 
 def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, sort_interval=0,
