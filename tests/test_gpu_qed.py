@@ -16,7 +16,7 @@ import pytest
 from oracle import oracle as O
 from paper_2607_13507_b300 import workloads as W
 
-from pic_cases import gpu_case, match_particles, oracle_case, rel_l2, run_gpu, run_oracle
+from pic_cases import field_bound, gpu_case, match_particles, oracle_case, rel_l2, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -306,7 +306,7 @@ def test_photons_stream_at_c_among_plasma_steps(order, absorb):
     Jg = G.current()
     for c in range(3):
         assert rel_l2(Jg[c].cpu().numpy(), g.J[c]) < 1e-4, ("J", c)
-        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < 1e-4 * steps, ("E", c)
+        assert rel_l2(G.E[c].cpu().numpy(), g.E[c]) < field_bound(1e-4, steps), ("E", c)
     G.sort()            # compact the particles removed in the last step
     for k, sg in enumerate(G.species):
         xg, xo, ug, uo = match_particles(G, sg, sps[k], wl)
