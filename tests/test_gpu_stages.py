@@ -2,7 +2,9 @@
 stages between the particle-update steps, and its Sec. 6.1 application).
 
 * Gathering the fields into a per-particle array and pushing/depositing with
-  them gives bit-identical fields, currents and particles to the fused kernel.
+  them gives bit-identical fields, currents and particles to the fused kernel,
+  and the gathered fields match the oracle's interpolation at the particles'
+  half-step positions.
 * A stage hook that adds a uniform B_z to the gathered fields matches the fused
   path on a grid whose B_z carries the same uniform field (to float32 rounding
   of the interpolation, which sums the shape weights).
@@ -72,6 +74,51 @@ def test_unfused_stages_match_fused(case):
         a, b = _by_id(sa), _by_id(sb)
         for k in a:
             assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("case", ["thermal2d_tsc", "laser2d", "thermal3d_tsc"])
+def test_gather_stage_matches_the_oracle_gather(case):
+    """Stage 1's per-particle fields against the oracle's interpolation at
+    the particles' half-step positions (x^{n+1/2}, stored cell + offsets), in
+    the GPU's own fields after a few steps, to float rounding of the
+    interpolation sums (1e-5 of the component's largest value)."""
+    from paper_2607_13507_b300 import lpic
+    if case == "thermal2d_tsc":
+        wl = W.thermal2d(n=40, ppc=6, vth=0.2, order=2, precision="fp32")
+    elif case == "laser2d":
+        wl = W.laser2d(nx=128, ny=32, ppc=2, precision="fp32")
+    else:
+        wl = W.thermal3d(n=12, ppc=3, vth=0.2, order=2, precision="fp32")
+    parts = W.load_all(wl)
+    G = gpu_case(wl, parts, lpic.FP32_FIXED)
+    steps = 30 if case == "laser2d" else 4
+    for s in range(steps):
+        G.step(s * wl.dt)
+    t = steps * wl.dt
+    G.maxwell_half(0, t)
+    g = O.Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, absorb_x=wl.absorb_x)
+    h = np.array(wl.h)
+    rng = np.random.Generator(np.random.Philox(3))
+    for sid, sp in enumerate(G.species):
+        f = G.gather_fields(sid)
+        torch.cuda.synchronize()
+        assert G.check_status() == 0
+        for c in range(3):
+            g.E[c][...] = G.E[c].cpu().numpy().astype(np.float64)
+            g.B[c][...] = G.B[c].cpu().numpy().astype(np.float64)
+        st = sp.state()
+        fg = f.cpu().numpy()
+        n = st["cell"].shape[0]
+        cell = st["cell"].astype(np.int64)
+        coords = [cell % wl.n[0], (cell // wl.n[0]) % wl.n[1]] + ([cell // (wl.n[0] * wl.n[1])] if wl.dim == 3 else [])
+        x = (np.stack(coords).astype(np.float64) + st["off"].astype(np.float64)) * h[:, None]
+        pick = rng.choice(n, size=min(n, 3000), replace=False)
+        scale = [max(float(torch.max(torch.abs(a)).item()), 1e-30) for a in list(G.E) + list(G.B)]
+        for i in pick:
+            E, B = O.gather(g, x[:, i])
+            ref = np.concatenate([E, B])
+            for c in range(6):
+                assert abs(fg[c, i] - ref[c]) <= 1e-5 * scale[c], (sid, i, c, fg[c, i], ref[c])
 
 
 def test_stage_hook_external_field():
