@@ -194,6 +194,15 @@ lpic_status lpic_add_species(lpic_grid_t grid, const lpic_species_desc *desc,
 lpic_status lpic_species_query(lpic_grid_t grid, int species_id, cudaStream_t stream,
                                int *current_buffer, long long *count);
 
+/* What a checkpoint needs besides the caller-owned buffers: the weight bound
+ * the species was registered with (max |w| at add time, or max_weight if
+ * larger; it sets the fixed-point shift, so a restored grid given the same
+ * bounds and capacities gets the same shift and can take the saved integer
+ * current as it is) and the id its next created particle will get.
+ * Synchronises `stream`. */
+lpic_status lpic_species_checkpoint_info(lpic_grid_t grid, int species_id, cudaStream_t stream,
+                                         double *max_weight, long long *next_id);
+
 /* Sort a species by cell tile (Algorithm 1 "sort particles by cell index"):
  * counting sort (histogram, scan, scatter) from the current buffer into the
  * other one, dropping removed particles; then the buffers flip.  Within a

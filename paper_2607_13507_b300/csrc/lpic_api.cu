@@ -1783,6 +1783,18 @@ lpic_status lpic_qed_pair_eval(lpic_grid_t g, const double* chi, const double* r
 }
 
 
+lpic_status lpic_species_checkpoint_info(lpic_grid_t g, int sid, cudaStream_t st, double* max_weight,
+                                         long long* next_id) {
+    if (lpic_status r = check_species(g, sid)) return r;
+    if (!max_weight || !next_id) return fail(LPIC_EINVAL, "NULL output");
+    int n2[2] = {0, 0};
+    LPIC_CUDA(cudaMemcpyAsync(n2, g->sp[sid].d_n, sizeof(n2), cudaMemcpyDeviceToHost, st));
+    LPIC_CUDA(cudaStreamSynchronize(st));
+    *max_weight = g->sp[sid].wmax;
+    *next_id = n2[1];
+    return LPIC_OK;
+}
+
 lpic_status lpic_species_set_next_id(lpic_grid_t g, int sid, long long next_id, cudaStream_t st) {
     if (lpic_status r = check_species(g, sid)) return r;
     if (next_id < 0 || next_id >= (1LL << 31)) return fail(LPIC_EINVAL, "next_id %lld outside [0, 2^31)", next_id);

@@ -33,7 +33,7 @@ EXPORTS = ["lpic_species_bytes", "lpic_create_grid", "lpic_destroy_grid", "lpic_
            "lpic_ensemble_step", "lpic_ensemble_graph_steps", "lpic_ensemble_check_status",
            "lpic_ensemble_launches", "lpic_qed_init", "lpic_qed_initial_tau", "lpic_qed_compton",
            "lpic_qed_eval", "lpic_qed_breit_wheeler", "lpic_qed_pair_eval", "lpic_species_set_next_id",
-           "lpic_qed_fuse", "lpic_qed_set_step", "lpic_debug_fail_alloc"]
+           "lpic_qed_fuse", "lpic_qed_set_step", "lpic_debug_fail_alloc", "lpic_species_checkpoint_info"]
 
 
 class LpicError(RuntimeError):
@@ -138,6 +138,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.lpic_qed_breit_wheeler.argtypes = [vp, i, i, i, vp, ctypes.c_longlong, ctypes.c_longlong, st]
     lib.lpic_qed_pair_eval.argtypes = [vp, vp, vp, ctypes.c_longlong, vp, vp, st]
     lib.lpic_species_set_next_id.argtypes = [vp, i, ctypes.c_longlong, st]
+    lib.lpic_species_checkpoint_info.argtypes = [vp, i, st, ctypes.POINTER(ctypes.c_double),
+                                                 ctypes.POINTER(ctypes.c_longlong)]
     lib.lpic_qed_fuse.argtypes = [vp, i, i, vp, ctypes.c_longlong, vp, ctypes.c_longlong, ctypes.c_longlong, st]
     lib.lpic_qed_set_step.argtypes = [vp, ctypes.c_longlong, st]
     lib.lpic_debug_fail_alloc.argtypes = [ctypes.c_longlong]
@@ -306,6 +308,7 @@ class Grid:
         if pml is not None and not absorb_x:
             raise ValueError("CPML layers need absorbing x")
         mode = 0 if not absorb_x else (2 if pml is not None else 1)
+        self.cpml = mode == 2
         P = pml or PmlSpec(cells=0)
         smax = 0.8 * (P.m + 1.0) / self.h[0] if P.sigma_max is None else float(P.sigma_max)
         desc = GridDesc(dim, self.n[0], self.n[1], nz, self.h[0], self.h[1], self.h[2], self.dt,
@@ -349,6 +352,71 @@ class Grid:
         return sp
 
     # -- nonlinear Compton emission
+    # -- checkpoint / resume: all state is caller-owned tensors plus the
+    # species' weight bounds and id counters; a grid created with the same
+    # description restores it and continues bit for bit (FP32 path; the FP64
+    # path's double atomics add in a varying order)
+    def checkpoint(self, stream=None) -> dict:
+        """Host copy of the state: fields, current, fixed-point shift and, per
+        species, its charge, mass, capacity, weight bound, next created id
+        and the alive particles (leapfrog-staggered)."""
+        if self.cpml:
+            # the layers' convolution memory lives in the library's scratch
+            raise ValueError("checkpoints do not cover the CPML layers' memory")
+        torch.cuda.synchronize(self.device)
+        out = {"dim": self.dim, "precision": self.precision, "n": list(self.n[:self.dim]),
+               "E": [t.cpu().numpy() for t in self.E], "B": [t.cpu().numpy() for t in self.B],
+               "J": [t.cpu().numpy() for t in self.J], "species": []}
+        if self.precision == FP32_FIXED:
+            out["fixed_shift"] = self.info().fixed_shift
+        for sp in self.species:
+            wmax, nid = ctypes.c_double(), ctypes.c_longlong()
+            _check(load().lpic_species_checkpoint_info(self.h_, sp.id, _stream(stream), ctypes.byref(wmax),
+                                                       ctypes.byref(nid)))
+            st = sp.state(stream)
+            key = "cell" if self.precision == FP32_FIXED else "x"
+            alive = st[key] >= 0 if key == "cell" else np.ones(st["id"].shape[0], bool)
+            parts = {k: (v[..., alive] if v.ndim > 1 else v[alive]) for k, v in st.items()}
+            out["species"].append({"q": sp.q, "m": sp.m, "cap": sp.cap, "max_weight": wmax.value,
+                                   "next_id": nid.value, "particles": parts})
+        return out
+
+    def restore(self, ckpt: dict, stream=None):
+        """Load a checkpoint into this grid, created with the same description
+        and holding no species yet."""
+        from .workloads import Particles
+        if self.species:
+            raise ValueError("restore needs a grid without species")
+        if ckpt["dim"] != self.dim or ckpt["precision"] != self.precision or \
+                list(ckpt["n"]) != list(self.n[:self.dim]):
+            raise ValueError("checkpoint of another grid description")
+        nx, ny = self.n[0], self.n[1]
+        for rec in ckpt["species"]:
+            st = rec["particles"]
+            n = st["id"].shape[0]
+            if self.precision == FP32_FIXED:
+                c = st["cell"].astype(np.int64)
+                coords = [c % nx, (c // nx) % ny] + ([c // (nx * ny)] if self.dim == 3 else [])
+                cell, off = np.stack(coords).astype(np.int32), st["off"]
+            else:
+                cell, off = np.zeros((self.dim, n), np.int32), np.zeros((self.dim, n))
+            p = Particles(q=rec["q"], m=rec["m"], cell=cell, off=off, u=st["u"], w=st["w"], id=st["id"])
+            sp = Species(self, rec["q"], rec["m"], rec["cap"])
+            sp.upload(p, True, stream, rec["max_weight"])
+            if self.precision == FP64:
+                # the positions themselves, not rebuilt from cell + offset
+                v = sp._views(0)
+                for d in range(self.dim):
+                    v["x"][d][:n] = torch.from_numpy(st["x"][d]).to(self.device)
+            self.species.append(sp)
+            sp.set_next_id(rec["next_id"], stream)
+        if self.precision == FP32_FIXED and self.info().fixed_shift != ckpt["fixed_shift"]:
+            raise ValueError("restored species give another fixed-point shift (capacities differ)")
+        for name in ("E", "B", "J"):
+            for dst, src in zip(getattr(self, name), ckpt[name]):
+                dst.copy_(torch.from_numpy(src).to(self.device))
+        torch.cuda.synchronize(self.device)
+
     def qed_init(self, eps_ref, seed, stream=None):
         """Build the emission tables; eps_ref = hbar omega / (m c^2) of the unit frequency."""
         _check(load().lpic_qed_init(self.h_, float(eps_ref), int(seed) & (2**64 - 1), _stream(stream)))
@@ -567,3 +635,34 @@ def grid_for(wl, precision=None, tile=None, device="cuda", block_particles=0, so
     pml = PmlSpec() if getattr(wl, "boundary", "mur") == "cpml" else None
     return Grid(wl.dim, wl.n, wl.h, wl.dt, wl.order, prec, wl.absorb_x, laser, tile, device,
                 block_particles, sort_interval, pml, maxwell_fp64)
+
+
+def save_checkpoint(G: Grid, path, stream=None):
+    """Grid.checkpoint() written to an .npz file."""
+    ck = G.checkpoint(stream)
+    flat = {"meta": np.array([ck["dim"], ck["precision"], ck.get("fixed_shift", 0), len(ck["species"])]),
+            "n": np.array(ck["n"])}
+    for name in ("E", "B", "J"):
+        for c, a in enumerate(ck[name]):
+            flat[f"{name}{c}"] = a
+    for k, rec in enumerate(ck["species"]):
+        flat[f"s{k}_scalars"] = np.array([rec["q"], rec["m"], rec["cap"], rec["max_weight"], rec["next_id"]],
+                                         dtype=np.float64)
+        for key, a in rec["particles"].items():
+            flat[f"s{k}_{key}"] = a
+    np.savez(path, **flat)
+
+
+def load_checkpoint(G: Grid, path, stream=None):
+    """Restore an .npz written by save_checkpoint into a fresh grid G."""
+    z = np.load(path)
+    dim, prec, fshift, ns = (int(v) for v in z["meta"])
+    ck = {"dim": dim, "precision": prec, "fixed_shift": fshift, "n": list(z["n"]),
+          "E": [z[f"E{c}"] for c in range(3)], "B": [z[f"B{c}"] for c in range(3)],
+          "J": [z[f"J{c}"] for c in range(3)], "species": []}
+    keys = ("cell", "off", "u", "w", "id") if prec == FP32_FIXED else ("x", "u", "w", "id")
+    for k in range(ns):
+        q, m, cap, wmax, nid = z[f"s{k}_scalars"]
+        ck["species"].append({"q": q, "m": m, "cap": int(cap), "max_weight": wmax, "next_id": int(nid),
+                              "particles": {key: z[f"s{k}_{key}"] for key in keys}})
+    G.restore(ck, stream)
