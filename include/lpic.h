@@ -81,6 +81,9 @@ typedef enum {
 #define LPIC_ST_NAN       0x4u  /* non-finite momentum */
 #define LPIC_ST_OUTSIDE   0x8u  /* a deposit or gather reached past an absorbing edge */
 #define LPIC_ST_OVERFLOW  0x10u /* a fixed-point value exceeded its bound */
+#define LPIC_ST_BOUNDS    0x20u /* checked build (liblpic_check.so, LPIC_CHECK=1) only:
+                                   a shared-memory index of the gather or the current
+                                   box fell outside its box; the access was skipped */
 
 enum { LPIC_FP64 = 0, LPIC_FP32_FIXED = 1 };
 

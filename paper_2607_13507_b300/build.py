@@ -1,6 +1,9 @@
-"""Build liblpic.so (CUDA for sm_103a) in-tree with nvcc.
+"""Build liblpic.so (CUDA for sm_103a) in-tree with nvcc, and on request the
+checked library liblpic_check.so (LPIC_CHECK=1: bounds tests on the
+data-dependent shared-memory indices of the tile kernels, which raise
+LPIC_ST_BOUNDS instead of accessing).
 
-    python -m paper_2607_13507_b300.build
+    python -m paper_2607_13507_b300.build [--checked]
 """
 from __future__ import annotations
 
@@ -13,6 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_lib", "liblpic.so")
+OUT_CHECK = os.path.join(PKG, "_lib", "liblpic_check.so")
 SOURCES = sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -33,12 +37,16 @@ def _deps():
     return files
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    if not force and os.path.exists(OUT):
-        t = os.path.getmtime(OUT)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          checked: bool = False) -> str:
+    out = OUT_CHECK if checked else OUT
+    if checked:
+        extra = list(extra or []) + ["-DLPIC_CHECK=1"]
+    if not force and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(f) <= t for f in _deps()):
-            return OUT
-    os.makedirs(os.path.dirname(OUT), exist_ok=True)
+            return out
+    os.makedirs(os.path.dirname(out), exist_ok=True)
     tag = f"tmp{os.getpid()}"
     objdir = os.path.join(os.path.dirname(OUT), "obj." + tag)
     os.makedirs(objdir, exist_ok=True)
@@ -57,18 +65,18 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         failed = [src for src, p in procs if p.wait() != 0]
         if failed:
             raise subprocess.CalledProcessError(1, "nvcc " + " ".join(os.path.basename(f) for f in failed))
-        tmp = OUT + "." + tag
+        tmp = out + "." + tag
         cmd = [nvcc(), *ARCH, "--shared", "-o", tmp, *objs]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
-        os.replace(tmp, OUT)
+        os.replace(tmp, out)
     finally:
         shutil.rmtree(objdir, ignore_errors=True)
-    return OUT
+    return out
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     x = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else None
-    print(build(force=True, verbose=v, extra=x))
+    print(build(force=True, verbose=v, extra=x, checked="--checked" in sys.argv))

@@ -36,6 +36,14 @@
 #include "lpic_common.cuh"
 #include "lpic_qed_tab.cuh"
 
+// Checked build (compiled into a library of its own): every data-dependent
+// shared-memory index of the gather and of the current box is tested against
+// its box; an index outside it raises LPIC_ST_BOUNDS and the access is
+// skipped.  Off in the product library.
+#ifndef LPIC_CHECK
+#define LPIC_CHECK 0
+#endif
+
 namespace lpic {
 
 struct P32 {
@@ -162,7 +170,12 @@ __device__ __forceinline__ void place32(float (&S)[ORDER + 2], const W& w, int o
 template <bool SKIP_ZERO>
 struct Acc32 {
     int* sJ;
+    int lim = 0;                 // checked build: words in the box
+    unsigned* st = nullptr;
     __device__ __forceinline__ void operator()(int idx, int v) const {
+#if LPIC_CHECK
+        if ((unsigned)idx >= (unsigned)lim) { set_status(st, LPIC_ST_BOUNDS); return; }
+#endif
         if constexpr (SKIP_ZERO) {
             const unsigned a = (unsigned)__cvta_generic_to_shared(sJ + idx);
             asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.s32 q, %1, 0;\n\t@q red.shared.add.s32 [%0], %1;\n\t}"
@@ -659,8 +672,13 @@ template <int DIM>
 struct LoadShared {
     const float* sF;
     int fsz, G0, G1;
+    unsigned* st = nullptr;      // checked build: status word
     __device__ inline float operator()(int comp, int x, int y, int z) const {
-        return sF[comp * fsz + ((DIM == 3 ? z + 1 : 0) * G1 + (y + 1)) * G0 + (x + 1)];
+        const int idx = comp * fsz + ((DIM == 3 ? z + 1 : 0) * G1 + (y + 1)) * G0 + (x + 1);
+#if LPIC_CHECK
+        if ((unsigned)idx >= (unsigned)(6 * fsz)) { set_status(st, LPIC_ST_BOUNDS); return 0.0f; }
+#endif
+        return sF[idx];
     }
 };
 
@@ -970,7 +988,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
     auto deposit_ring = [&](int slot) -> unsigned {
         Move<DIM> mv;
         mv.read(sRing + (slot & (kRing - 1)), kRing);
-        deposit3d<ORDER>(Acc32<false>{sR}, jsz, H0, H1, mv.lc, mv.f, mv.ce, mv.fe, mv.s);
+        deposit3d<ORDER>(Acc32<false>{sR, 3 * jsz, st}, jsz, H0, H1, mv.lc, mv.f, mv.ce, mv.fe, mv.s);
         return mv.template bound<ORDER>();
     };
 
@@ -1061,7 +1079,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
 #pragma unroll
                     for (int c = 0; c < 6; ++c) fld[c] = A.fields[c * A.fcap + i];
                 } else {
-                    gather32<DIM, ORDER>(LoadShared<DIM>{sF, fsz, G0, G1}, nx_, ny_, nz_, hx_, hy_, hz_, fld);
+                    gather32<DIM, ORDER>(LoadShared<DIM>{sF, fsz, G0, G1, st}, nx_, ny_, nz_, hx_, hy_, hz_, fld);
                 }
                 if constexpr (MODE == kGpdGather) {
 #pragma unroll
@@ -1128,7 +1146,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                         const NodeW<ORDER> ex(mv.ce[0], mv.fe[0]), ey(mv.ce[1], mv.fe[1]), ez(mv.ce[2], mv.fe[2]);
                         mv.same = ex.base == nx_.base && ey.base == ny_.base && (DIM == 2 || ez.base == nz_.base);
                         if constexpr (DIM == 2) {
-                            const Acc32<true> acc{sR};
+                            const Acc32<true> acc{sR, 3 * jsz, st};
                             // the stencil-sized window when every converged lane allows it
                             if (__all_sync(__activemask(), mv.same))
                                 deposit2d_w<ORDER, true>(acc, jsz, H0, nx_, ny_, ex, ey, mv.s, mv.vz);
@@ -1137,7 +1155,7 @@ __device__ __forceinline__ void gpd_item(const GpdArgs& A, int item_index, float
                         } else {
                             if (mv.same) {
                                 bnd = mv.template bound<ORDER>();
-                                deposit3d_w<ORDER>(Acc32<false>{sR}, jsz, H0, H1, nx_, ny_, nz_, ex, ey, ez, mv.s);
+                                deposit3d_w<ORDER>(Acc32<false>{sR, 3 * jsz, st}, jsz, H0, H1, nx_, ny_, nz_, ex, ey, ez, mv.s);
                             } else {
                                 // staged: deposited with the other general-form moves
                                 const int to = atomicAdd(sCnt + kCntRing, 1) & (kRing - 1);

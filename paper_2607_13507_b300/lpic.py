@@ -14,10 +14,12 @@ import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "liblpic.so")
+# LPIC_LIBRARY selects another build of the same ABI (the checked library
+# liblpic_check.so in the bounds tests)
+LIB_PATH = os.environ.get("LPIC_LIBRARY") or os.path.join(_PKG, "_lib", "liblpic.so")
 
 FP64, FP32_FIXED = 0, 1
-ST_CFL, ST_HALO, ST_NAN, ST_OUTSIDE, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
+ST_CFL, ST_HALO, ST_NAN, ST_OUTSIDE, ST_OVERFLOW, ST_BOUNDS = 0x1, 0x2, 0x4, 0x8, 0x10, 0x20
 
 STATUS = {0: "LPIC_OK", 1: "LPIC_EINVAL", 2: "LPIC_ENOMEM", 3: "LPIC_ECUDA", 4: "LPIC_EDEVICE",
           5: "LPIC_EUNSUPPORTED"}
